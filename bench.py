@@ -1,0 +1,354 @@
+"""Throughput of the batched Generals.io environment step on GB300.
+
+One benchmark step = one frame of every game of the workload: the fused
+step kernel (moves, combat, capture, growth, termination, reward, auto-reset,
+fog, observations, mask, scoreboard) plus the benchmark random-legal policy
+that produces the next frame's actions, in one launch.  Default workload:
+65,536 1v1 games on 24x24 boards (20% mountains, 12 castles of 40-50),
+auto-reset on, synthetic and seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank steps its own
+games (global ids offset by rank) with no collective on the data path.
+``--impl reference`` times the CPU oracle (the only other implementation of
+these rules) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "1v1-65536x24x24"
+METRIC = "frames/s per GB300 (bit-exact vs oracle)"
+UNIT = "frames/s"
+POLICY_SEED = 2
+MAP_SEED = 1
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel
+# from one ncu capture, valid only for the kernel source with this hash.
+NCU_TRAFFIC = {"kernel_sha1": None, "bytes_per_launch": None}
+
+
+def kernel_sha1() -> str:
+    p = os.path.join(ROOT, "paper_2606_23348_gb300", "csrc", "gk_kernels.cu")
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+def algorithmic_bytes(env) -> int:
+    """Bytes one step launch must move at minimum, from the library's layout:
+    state read + write (int16 army, int8 owner, int8 terrain per cell),
+    five per-player planes (int16 + 4 x int8) and the mask written, actions
+    read and next actions written, reward / scoreboard / done written, game
+    scalars read + written, game table read."""
+    npad = env.npad.astype(np.int64)
+    P = env.P.astype(np.int64)
+    per_game = 2 * 4 * npad + 6 * P * npad + 4 * P + 4 * P + 4 * P + 8 * P + 1 + 2 * 32 + 32
+    return int(per_game.sum())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        busy = [x for x in sm if mx and x > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_throughput(budget_s: float = 12.0, games: int = 1024):
+    """The oracle as it stands, single-threaded, on the first `games` games of
+    the workload for as many frames as fit in the time budget."""
+    from oracle import OracleEnv
+    from paper_2606_23348_gb300.workloads import workload
+    H, W, mode, P, gen, _ = workload(WORKLOAD, G=games)
+    orc = OracleEnv(H, W, mode, P, seed=MAP_SEED, **gen)
+    frames = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.step(orc.policy(POLICY_SEED))
+        frames += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return games * frames / el, {"games": games, "frames": frames, "seconds": round(el, 2)}
+
+
+def run_reference(args, rank, world):
+    """The oracle, single-threaded on the host: one step = one frame of the
+    first 256 games of the workload (the same maps, policy and rules)."""
+    if rank != 0:
+        return
+    from oracle import OracleEnv
+    from paper_2606_23348_gb300.workloads import workload
+    games = 256
+    H, W, mode, P, gen, _ = workload(WORKLOAD, G=games)
+    orc = OracleEnv(H, W, mode, P, seed=MAP_SEED, **gen)
+    for _ in range(args.warmup):
+        orc.step(orc.policy(POLICY_SEED))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step(orc.policy(POLICY_SEED))
+    el = time.perf_counter() - t0
+    value = games * args.steps / el
+    sample = f"first {games} games of the workload, one frame per step, single thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
+        "data": "synthetic (seeded counter-hash maps and policy)",
+        "config": {"workload": WORKLOAD, "sample": sample, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU path
+def run_e2e(env, acts, args, world):
+    """The same step through gen_step_host: pinned host actions copied in,
+    every output and the next actions copied back, inside the timed region."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import Outputs
+    h_out = Outputs(env.layout, pin_host=True)
+    h_act = acts.cpu().pin_memory()
+    h_next = torch.empty_like(h_act).pin_memory()
+    Ke = max(3, min(args.steps, args.e2e_steps))
+    for _ in range(2):
+        env.step_host(h_act, h_out, POLICY_SEED, h_next)
+        h_act.copy_(h_next)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        env.step_host(h_act, h_out, POLICY_SEED, h_next)
+        h_act.copy_(h_next)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    value = sum_over_ranks(float(env.G * Ke), world) / e2e_s
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h_act.numel() * 4,
+            "d2h_bytes_per_step": h_out.nbytes() + h_next.numel() * 4, "steps": Ke,
+            "path": "gen_step_host (pinned host buffers, fused policy)"}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv, copy_peak_gbps
+    from paper_2606_23348_gb300.workloads import workload
+
+    torch.cuda.set_device(local)
+    H, W, mode, P, gen, _ = workload(WORKLOAD)
+    G = int(H.shape[0])
+    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=rank * G, **gen)
+    if args.warps:
+        env.set_launch(args.warps)
+    out = env.new_outputs()
+    acts = env.new_actions()
+    stream = torch.cuda.current_stream()
+    env.policy(POLICY_SEED, acts)
+    for _ in range(args.warmup):
+        env.step_policy(acts, out, POLICY_SEED, acts)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        t_all[0].record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            env.step_policy(acts, out, POLICY_SEED, acts)
+            ev[k][1].record(stream)
+        t_all[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    elapsed_ms = t_all[0].elapsed_time(t_all[1])
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    frames_total = sum_over_ranks(float(G * K), world)
+    value = frames_total / (elapsed_ms * 1e-3)
+
+    # e2e: the same step through the host-buffer entry point, copies timed
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(env, acts, args, world)
+
+    nbytes = algorithmic_bytes(env)
+    peak, peak_kind = peaks()
+    achieved = nbytes / (launch_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_sha1"] == kernel_sha1() else None
+    own_peak = copy_peak_gbps(1 << 30, 5) if (rank == 0 and not args.no_copy_peak) else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = oracle_throughput(budget_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {sample['games']} games of the workload x {sample['frames']} frames "
+                         f"({sample['seconds']} s), one thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int16",
+            "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
+            "config": {"workload": WORKLOAD, "games_per_gpu": G, "board": "24x24", "mode": "1v1",
+                       "cities": 12, "mountains": 0.2, "policy": "uniform legal, split p=0.2",
+                       "parallelism": f"replicas x{world} (disjoint game ids)",
+                       "l2": "inputs larger than L2 (state 151 MB + outputs 529 MB per step)",
+                       "launch": f"{args.warps or 8} games (warps) per CTA"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "own_copy_kernel_gbps": own_peak, "algorithmic_bytes_per_launch": nbytes,
+                         "launch_ms": launch_ms, "kernel": "k_generals (fused step + policy)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": K,
+            "clocks": clk.summary(),
+            "kernel_sha1": kernel_sha1(),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--warps", type=int, default=0, help="games per CTA (0 = library default)")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-copy-peak", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        from paper_2606_23348_gb300.build import build_library
+        if rank == 0:
+            build_library()
+        barrier(world)
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * libgenerals: batched Generals.io environment step on GB300 (sm_103a).
+ *
+ * One call advances every game of an environment by one turn: action
+ * validation and application, combat and capture, general capture with land
+ * transfer, army growth, termination and reward, auto-reset through the
+ * seeded map generator, then per-player fog-of-war observations, the public
+ * scoreboard and the legal-action mask (paper, Section IV; fixed H x W x 9
+ * action space of Section IV-G; reward of Section III).
+ *
+ * Conventions shared by every entry point
+ *  - Return 0 on success or a negative GEN_ERR_* code; gen_last_error()
+ *    gives a one-line reason.  Illegal or out-of-range actions are not
+ *    errors: they act as a pass and are counted per game.
+ *  - Device pointers ("d_") must be 16-byte aligned device memory of the
+ *    sizes stated; host pointers ("h_") are ordinary (preferably pinned)
+ *    host memory.  The library never frees caller memory.
+ *  - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls are stream-ordered and do not synchronise the device,
+ *    except where a call is documented as synchronous.
+ *  - The environment owns the game state (device arenas) until
+ *    gen_destroy().  An environment must not be used from two host threads
+ *    at once.
+ *
+ * Layout (ragged batches allowed: each game g has its own H_g x W_g board,
+ * N_g = H_g * W_g cells, P_g players):
+ *  - Npad_g = N_g rounded up to a multiple of 16.
+ *  - Per-player planes (obs_army int16, obs_owner int8, obs_terrain int8,
+ *    obs_vis uint8, mask uint8) hold, for game g and player p, Npad_g cells
+ *    in row-major order starting at plane_off[g] + p * Npad_g.  Cells
+ *    N_g .. Npad_g-1 are padding and read 0 (army), -2 (owner), 4 (terrain),
+ *    0 (vis, mask).  A uniform batch is the array [G][P][Npad].
+ *  - Per-player slots (actions, reward, scoreboard) of game g are
+ *    player_off[g] + p.  A uniform batch is [G][P].
+ *  - Codes: terrain 0 plain, 1 mountain, 2 castle, 3 general; observed
+ *    terrain 4 = fog, 5 = fogged mountain or castle; owner -1 neutral,
+ *    0..P-1 player, -2 hidden.  Mask byte: bit d (0 up, 1 down, 2 left,
+ *    3 right) = all-but-one move legal, bit 4+d = half move legal; pass is
+ *    always legal and not in the mask.
+ *  - Action of a player: flat index a = cell * 9 + k into the H x W x 9
+ *    action space; k = 0 pass, 1..4 all-but-one up/down/left/right, 5..8
+ *    half up/down/left/right.
+ */
+#ifndef GENERALS_H
+#define GENERALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GEN_OK 0
+#define GEN_ERR_BAD_ARG (-1)
+#define GEN_ERR_OOM (-2)
+#define GEN_ERR_CUDA (-3)
+#define GEN_ERR_TIMEOUT (-4)
+#define GEN_ERR_STATE (-5)
+
+#define GEN_MODE_1V1 0
+#define GEN_MODE_2V2 1
+#define GEN_MODE_FFA 2
+
+#define GEN_MAX_PLAYERS 8
+#define GEN_MAX_SIDE 64
+
+typedef struct gen_env gen_env;
+
+/* Generator and episode parameters (Section IV-A map generation). */
+typedef struct gen_params {
+    uint64_t seed;             /* map seed of the counter hash */
+    uint64_t game_id_base;     /* global id of local game 0 (sharding) */
+    uint32_t mountain_thresh;  /* P(mountain) = thresh / 2^32; 858993459 = 20% */
+    int32_t n_cities;          /* >= 0: neutral castles per map; < 0: use city_per_mille */
+    int32_t city_per_mille;    /* castles = floor(N * per_mille / 1000) when n_cities < 0 */
+    int32_t city_army_min;     /* castle army, inclusive range (40..50 in the paper) */
+    int32_t city_army_max;
+    int32_t min_general_dist;  /* Manhattan spacing of generals; <= 0: floor((H+W)/3) */
+    int32_t max_turns;         /* 0 = no truncation; else done code 2 at this turn */
+    int32_t auto_reset;        /* 1: a finished game is regenerated inside gen_step */
+} gen_params;
+
+/* Caller-provided device output buffers (sizes from gen_layout). */
+typedef struct gen_outputs {
+    int16_t *obs_army;    /* [plane_cells] army if visible else 0 */
+    int8_t *obs_owner;    /* [plane_cells] owner if visible else -2 */
+    int8_t *obs_terrain;  /* [plane_cells] terrain if visible else 4 / 5 */
+    uint8_t *obs_vis;     /* [plane_cells] 1 if visible */
+    uint8_t *mask;        /* [plane_cells] legal-move bits */
+    float *reward;        /* [player_slots] reward of this step */
+    int32_t *scoreboard;  /* [player_slots][2] land, army (public) */
+    uint8_t *done;        /* [n_games] 0 running, 1 terminal, 2 truncated */
+} gen_outputs;
+
+typedef struct gen_layout_info {
+    int32_t n_games;
+    int32_t player_slots;  /* sum of P_g */
+    int64_t plane_cells;   /* sum of P_g * Npad_g: elements of each per-player plane */
+    int64_t state_cells;   /* sum of Npad_g */
+    int32_t max_players;
+    int32_t max_cells;     /* max N_g */
+} gen_layout_info;
+
+/* Fill *p with the defaults: seed 1, 20% mountains, 8 castles of 40..50,
+ * spacing floor((H+W)/3), no truncation, auto-reset on. */
+int gen_default_params(gen_params *p);
+
+/* Create a uniform batch of `batch` games of H x W in `mode` (0 1v1, 1 2v2,
+ * 2 FFA with 8 players) with default parameters and the given seed.  Runs
+ * the generator for every game (epoch 0).  Synchronous. */
+int gen_create(gen_env **out, int batch, int H, int W, int mode, uint64_t seed);
+
+/* Create a ragged batch: per-game host arrays h_H, h_W, h_mode and
+ * h_n_players (players for FFA; ignored for 1v1 / 2v2), each of `batch`
+ * entries; 1 <= H, W <= 64, P <= N.  Synchronous. */
+int gen_create_ex(gen_env **out, const gen_params *p, int batch, const int32_t *h_H, const int32_t *h_W,
+                  const int32_t *h_mode, const int32_t *h_n_players);
+
+/* Layout sizes and, when the arrays are non-NULL, the per-game host offsets
+ * (h_plane_off[g], h_player_off[g], h_npad[g], each [n_games]). */
+int gen_layout(const gen_env *env, gen_layout_info *info, int64_t *h_plane_off, int32_t *h_player_off,
+               int32_t *h_npad);
+
+/* Regenerate games (next epoch, new map, turn 0; the frame counter runs on)
+ * and write their observations, masks and scoreboard into `out` (reward 0,
+ * done 0).  d_game_ids: device int32 [n] of distinct local game ids (ids
+ * outside [0, n_games) are skipped), or NULL for all games.  Section IV-A. */
+int gen_reset(gen_env *env, const int32_t *d_game_ids, int n, const gen_outputs *out, void *stream);
+
+/* Write the current observations, masks and scoreboard of every game into
+ * `out` without advancing (reward 0, done 0). */
+int gen_observe(gen_env *env, const gen_outputs *out, void *stream);
+
+/* Advance every game by one turn.  d_actions: device int32 [player_slots].
+ * Writes every field of `out`.  Section IV-B..IV-E. */
+int gen_step(gen_env *env, const int32_t *d_actions, const gen_outputs *out, void *stream);
+
+/* gen_step, then the benchmark policy for the next step computed from the
+ * new masks in the same launch: d_next_actions [player_slots] receives, per
+ * player, a uniformly drawn legal (cell, direction) pair (row-major cells,
+ * then up, down, left, right; pass when none) sent whole, or halved with
+ * probability 0.2, keyed by (policy_seed, global game id, frame, player).
+ * d_next_actions may equal d_actions. */
+int gen_step_policy(gen_env *env, const int32_t *d_actions, const gen_outputs *out, uint64_t policy_seed,
+                    int32_t *d_next_actions, void *stream);
+
+/* The benchmark policy alone, from the current state of every game. */
+int gen_policy(gen_env *env, uint64_t policy_seed, int32_t *d_actions, void *stream);
+
+/* gen_step with host buffers: copies h_actions [player_slots] to the device,
+ * steps, copies every non-NULL output of `h_out` back into host memory (same
+ * sizes as the device outputs) and synchronises the stream.  When
+ * h_next_actions is non-NULL the benchmark policy of gen_step_policy runs in
+ * the same launch and its actions are copied back too. */
+int gen_step_host(gen_env *env, const int32_t *h_actions, const gen_outputs *h_out, uint64_t policy_seed,
+                  int32_t *h_next_actions, void *stream);
+
+/* Copy the whole game state to host memory: h_army [state_cells] int16,
+ * h_owner / h_terrain [state_cells] int8 (game g at its state offset,
+ * sum of Npad of earlier games), h_scalars [n_games][8] uint32 = turn,
+ * frame, epoch, alive bits, finished, invalid actions, saturations, error.
+ * Synchronous on `stream`. */
+int gen_read_state(gen_env *env, int16_t *h_army, int8_t *h_owner, int8_t *h_terrain, uint32_t *h_scalars,
+                   void *stream);
+
+/* Overwrite the whole game state from host memory (same layout as
+ * gen_read_state; the error word is ignored).  Synchronous on `stream`. */
+int gen_write_state(gen_env *env, const int16_t *h_army, const int8_t *h_owner, const int8_t *h_terrain,
+                    const uint32_t *h_scalars, void *stream);
+
+/* Launch shape of this environment's step kernel: games (warps) per CTA,
+ * one of 1, 2, 4, 8 that fits the shared-memory limit.  Used by the
+ * autotuner; results do not depend on it. */
+int gen_set_launch(gen_env *env, int warps_per_cta);
+
+/* Measure copy bandwidth of this GPU with the library's own 128-bit copy
+ * kernel over `bytes` (rounded down to 16 B), best of `reps`; returns GB/s
+ * counting read + write bytes in *gbps.  Synchronous. */
+int gen_copy_peak(size_t bytes, int reps, double *gbps);
+
+/* Reason for the last failure on this thread (never NULL). */
+const char *gen_last_error(void);
+
+void gen_destroy(gen_env *env);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENERALS_H */

@@ -1,0 +1,87 @@
+// Internal structures shared by the kernels and the C-ABI layer of
+// libgenerals.  Not part of the public interface (include/generals.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace gk {
+
+constexpr int kMaxPlayers = 8;
+constexpr int kMaxSide = 64;
+constexpr int kGenAttempts = 64;  // rejection attempts per level (generator)
+
+enum Op : int32_t {
+    OP_CREATE = 0,   // epoch 0 map, counters cleared, outputs
+    OP_RESET = 1,    // next epoch map, outputs
+    OP_OBSERVE = 2,  // outputs only
+    OP_STEP = 3,     // full step, outputs
+    OP_POLICY = 4,   // benchmark policy only
+};
+
+// Read-only description of one game (32 bytes).
+struct alignas(16) GameInfo {
+    int64_t plane_off;   // first cell of player 0's plane in every per-player output plane
+    int32_t cell_off;    // first cell in the state arenas
+    int32_t player_off;  // first per-player slot (actions, reward, scoreboard)
+    int16_t H, W;
+    int16_t N, Npad;     // cells, cells rounded up to 16
+    int8_t mode, P;
+    int16_t n_cities;
+    int16_t dmin;        // Manhattan spacing of generals
+    int16_t pad;
+};
+static_assert(sizeof(GameInfo) == 32, "GameInfo is 32 bytes");
+
+// Mutable per-game scalars (32 bytes), one row of gen_read_state's h_scalars.
+struct alignas(16) GameScalars {
+    uint32_t turn, frame, epoch, alive, finished, invalid, saturated, err;
+};
+static_assert(sizeof(GameScalars) == 32, "GameScalars is 32 bytes");
+
+struct KArgs {
+    const GameInfo* info;
+    const int32_t* list;  // optional list of local game ids, else item i = game i
+    int32_t n_items;
+    int32_t n_games;    // list entries outside [0, n_games) are skipped
+    int32_t op;
+    int16_t* army;
+    int8_t* owner;
+    int8_t* terrain;
+    GameScalars* scal;
+    const int32_t* actions;
+    int16_t* obs_army;
+    int8_t* obs_owner;
+    int8_t* obs_terrain;
+    uint8_t* obs_vis;
+    uint8_t* mask;
+    float* reward;
+    int32_t* scoreboard;
+    uint8_t* done;
+    int32_t* next_actions;  // non-null: fused benchmark policy
+    uint64_t policy_seed;
+    uint64_t seed;
+    uint64_t game_id_base;
+    uint32_t mtn_thresh;
+    int32_t city_min, city_span;
+    int32_t max_turns;
+    int32_t auto_reset;
+    int32_t do_outputs;
+    // shared-memory carve of one warp (one game)
+    int32_t npad_max;   // cells
+    int32_t nw_stride;  // 32-bit words per bitset
+    int32_t pmax;
+    int32_t warp_smem;  // bytes per warp
+};
+
+// Bytes of shared memory one warp needs for games up to npad_max cells and
+// pmax players; also returns the bitset stride in words.
+int warp_smem_bytes(int npad_max, int pmax, int* nw_stride);
+
+// Launch the step kernel with `warps_per_cta` games per CTA on `stream`.
+// Returns a cudaError_t value.
+int launch_step(const KArgs& a, int warps_per_cta, void* stream);
+
+// 128-bit copy kernel used to measure the HBM roofline denominator.
+int launch_copy(const void* src, void* dst, size_t n16, int blocks, void* stream);
+
+}  // namespace gk

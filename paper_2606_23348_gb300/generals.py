@@ -1,0 +1,266 @@
+"""Python binding of libgenerals (include/generals.h) — argument marshalling only.
+
+Every step of the environment runs in the library's CUDA kernels; this module
+allocates torch tensors for the outputs, passes their device pointers and
+the current CUDA stream through ctypes, and raises when a call fails.  There
+is no CPU fallback: without the compiled library and a GPU nothing here runs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libgenerals.so")
+_lock = threading.Lock()
+_lib = None
+
+GEN_MAX_PLAYERS = 8
+
+
+class GenParams(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64),
+        ("game_id_base", C.c_uint64),
+        ("mountain_thresh", C.c_uint32),
+        ("n_cities", C.c_int32),
+        ("city_per_mille", C.c_int32),
+        ("city_army_min", C.c_int32),
+        ("city_army_max", C.c_int32),
+        ("min_general_dist", C.c_int32),
+        ("max_turns", C.c_int32),
+        ("auto_reset", C.c_int32),
+    ]
+
+
+class GenOutputs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in
+                ("obs_army", "obs_owner", "obs_terrain", "obs_vis", "mask", "reward", "scoreboard", "done")]
+
+
+class GenLayoutInfo(C.Structure):
+    _fields_ = [
+        ("n_games", C.c_int32),
+        ("player_slots", C.c_int32),
+        ("plane_cells", C.c_int64),
+        ("state_cells", C.c_int64),
+        ("max_players", C.c_int32),
+        ("max_cells", C.c_int32),
+    ]
+
+
+EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "gen_reset", "gen_observe",
+           "gen_step", "gen_step_policy", "gen_policy", "gen_step_host", "gen_read_state", "gen_write_state",
+           "gen_set_launch", "gen_copy_peak", "gen_last_error", "gen_destroy")
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgenerals.so; raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgenerals.so is not built ({path}); run __graft_entry__.build() or "
+                               "python -m paper_2606_23348_gb300.build")
+        lib = C.CDLL(path)
+        vp, i32, u64 = C.c_void_p, C.c_int32, C.c_uint64
+        sig = {
+            "gen_default_params": (C.c_int, [C.POINTER(GenParams)]),
+            "gen_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, u64]),
+            "gen_create_ex": (C.c_int, [C.POINTER(vp), C.POINTER(GenParams), C.c_int, vp, vp, vp, vp]),
+            "gen_layout": (C.c_int, [vp, C.POINTER(GenLayoutInfo), vp, vp, vp]),
+            "gen_reset": (C.c_int, [vp, vp, C.c_int, C.POINTER(GenOutputs), vp]),
+            "gen_observe": (C.c_int, [vp, C.POINTER(GenOutputs), vp]),
+            "gen_step": (C.c_int, [vp, vp, C.POINTER(GenOutputs), vp]),
+            "gen_step_policy": (C.c_int, [vp, vp, C.POINTER(GenOutputs), u64, vp, vp]),
+            "gen_policy": (C.c_int, [vp, u64, vp, vp]),
+            "gen_step_host": (C.c_int, [vp, vp, C.POINTER(GenOutputs), u64, vp, vp]),
+            "gen_read_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+            "gen_write_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+            "gen_set_launch": (C.c_int, [vp, C.c_int]),
+            "gen_copy_peak": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
+            "gen_last_error": (C.c_char_p, []),
+            "gen_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+class GeneralsError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise GeneralsError(f"{what} failed ({rc}): {load_library().gen_last_error().decode()}")
+
+
+def default_params(**kw) -> GenParams:
+    p = GenParams()
+    _check(load_library().gen_default_params(C.byref(p)), "gen_default_params")
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def copy_peak_gbps(nbytes: int = 1 << 30, reps: int = 10) -> float:
+    """HBM copy bandwidth (read + write bytes) measured by the library's own copy kernel."""
+    out = C.c_double()
+    _check(load_library().gen_copy_peak(nbytes, reps, C.byref(out)), "gen_copy_peak")
+    return float(out.value)
+
+
+def _cur_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Outputs:
+    """Device output tensors of one environment (torch, on cuda)."""
+
+    def __init__(self, layout: GenLayoutInfo, device="cuda", pin_host: bool = False):
+        import torch
+        pc, ps, G = int(layout.plane_cells), int(layout.player_slots), int(layout.n_games)
+        kw = dict(device=device) if not pin_host else dict(pin_memory=True)
+        self.obs_army = torch.empty(pc, dtype=torch.int16, **kw)
+        self.obs_owner = torch.empty(pc, dtype=torch.int8, **kw)
+        self.obs_terrain = torch.empty(pc, dtype=torch.int8, **kw)
+        self.obs_vis = torch.empty(pc, dtype=torch.uint8, **kw)
+        self.mask = torch.empty(pc, dtype=torch.uint8, **kw)
+        self.reward = torch.empty(ps, dtype=torch.float32, **kw)
+        self.scoreboard = torch.empty((ps, 2), dtype=torch.int32, **kw)
+        self.done = torch.empty(G, dtype=torch.uint8, **kw)
+        self.struct = GenOutputs(*[t.data_ptr() for t in self.tensors()])
+
+    def tensors(self):
+        return (self.obs_army, self.obs_owner, self.obs_terrain, self.obs_vis, self.mask, self.reward,
+                self.scoreboard, self.done)
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.tensors())
+
+
+class GeneralsEnv:
+    """A batch of games held on the GPU by libgenerals.
+
+    ``H``, ``W``, ``mode`` and ``n_players`` are per-game sequences (ragged
+    batches allowed) or scalars with ``batch``.
+    """
+
+    def __init__(self, H, W, mode=0, n_players=8, batch=None, **params):
+        lib = load_library()
+        if batch is not None:
+            H, W = np.full(batch, H), np.full(batch, W)
+            mode, n_players = np.full(batch, mode), np.full(batch, n_players)
+        self.H = np.ascontiguousarray(H, np.int32)
+        self.W = np.ascontiguousarray(W, np.int32)
+        self.mode = np.ascontiguousarray(np.broadcast_to(mode, self.H.shape), np.int32)
+        self.n_players = np.ascontiguousarray(np.broadcast_to(n_players, self.H.shape), np.int32)
+        self.params = default_params(**params)
+        h = C.c_void_p()
+        _check(lib.gen_create_ex(C.byref(h), C.byref(self.params), int(self.H.shape[0]),
+                                 self.H.ctypes.data, self.W.ctypes.data, self.mode.ctypes.data,
+                                 self.n_players.ctypes.data), "gen_create_ex")
+        self.h = h
+        self.lib = lib
+        info = GenLayoutInfo()
+        G = int(self.H.shape[0])
+        self.plane_off = np.zeros(G, np.int64)
+        self.player_off = np.zeros(G, np.int32)
+        self.npad = np.zeros(G, np.int32)
+        _check(lib.gen_layout(h, C.byref(info), self.plane_off.ctypes.data, self.player_off.ctypes.data,
+                              self.npad.ctypes.data), "gen_layout")
+        self.layout = info
+        self.G = G
+        self.P = np.where(self.mode == 0, 2, np.where(self.mode == 1, 4, self.n_players)).astype(np.int32)
+        self.N = (self.H * self.W).astype(np.int64)
+        self.state_off = np.concatenate([[0], np.cumsum(self.npad)[:-1]]).astype(np.int64)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gen_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- buffers --------------------------------------------------------
+    def new_outputs(self) -> Outputs:
+        return Outputs(self.layout)
+
+    def new_actions(self):
+        import torch
+        return torch.zeros(int(self.layout.player_slots), dtype=torch.int32, device="cuda")
+
+    # ---- calls ----------------------------------------------------------
+    def observe(self, out: Outputs, stream=None):
+        _check(self.lib.gen_observe(self.h, C.byref(out.struct), stream or _cur_stream()), "gen_observe")
+
+    def reset(self, out: Outputs, game_ids=None, stream=None):
+        if game_ids is None:
+            _check(self.lib.gen_reset(self.h, None, 0, C.byref(out.struct), stream or _cur_stream()), "gen_reset")
+        else:
+            _check(self.lib.gen_reset(self.h, C.c_void_p(game_ids.data_ptr()), int(game_ids.numel()),
+                                      C.byref(out.struct), stream or _cur_stream()), "gen_reset")
+
+    def step(self, actions, out: Outputs, stream=None):
+        _check(self.lib.gen_step(self.h, C.c_void_p(actions.data_ptr()), C.byref(out.struct),
+                                 stream or _cur_stream()), "gen_step")
+
+    def step_policy(self, actions, out: Outputs, policy_seed: int, next_actions, stream=None):
+        _check(self.lib.gen_step_policy(self.h, C.c_void_p(actions.data_ptr()), C.byref(out.struct),
+                                        int(policy_seed), C.c_void_p(next_actions.data_ptr()),
+                                        stream or _cur_stream()), "gen_step_policy")
+
+    def policy(self, policy_seed: int, actions, stream=None):
+        _check(self.lib.gen_policy(self.h, int(policy_seed), C.c_void_p(actions.data_ptr()),
+                                   stream or _cur_stream()), "gen_policy")
+
+    def step_host(self, h_actions, h_out: Outputs, policy_seed: int = 0, h_next_actions=None, stream=None):
+        """Host-buffer step: h_actions, h_out (and h_next_actions) are CPU (pinned) tensors."""
+        nxt = C.c_void_p(h_next_actions.data_ptr()) if h_next_actions is not None else None
+        _check(self.lib.gen_step_host(self.h, C.c_void_p(h_actions.data_ptr()), C.byref(h_out.struct),
+                                      int(policy_seed), nxt, stream or _cur_stream()), "gen_step_host")
+
+    def set_launch(self, warps_per_cta: int):
+        _check(self.lib.gen_set_launch(self.h, int(warps_per_cta)), "gen_set_launch")
+
+    def read_state(self):
+        n = int(self.layout.state_cells)
+        army = np.zeros(n, np.int16)
+        owner = np.zeros(n, np.int8)
+        terrain = np.zeros(n, np.int8)
+        scal = np.zeros((self.G, 8), np.uint32)
+        _check(self.lib.gen_read_state(self.h, army.ctypes.data, owner.ctypes.data, terrain.ctypes.data,
+                                       scal.ctypes.data, _cur_stream()), "gen_read_state")
+        return army, owner, terrain, scal
+
+    def write_state(self, army, owner, terrain, scal):
+        army = np.ascontiguousarray(army, np.int16)
+        owner = np.ascontiguousarray(owner, np.int8)
+        terrain = np.ascontiguousarray(terrain, np.int8)
+        scal = np.ascontiguousarray(scal, np.uint32)
+        _check(self.lib.gen_write_state(self.h, army.ctypes.data, owner.ctypes.data, terrain.ctypes.data,
+                                        scal.ctypes.data, _cur_stream()), "gen_write_state")
+
+    # ---- views ----------------------------------------------------------
+    def board(self, state, g: int):
+        """(army, owner, terrain) of game g from a read_state() tuple, padding removed."""
+        o, n = int(self.state_off[g]), int(self.N[g])
+        return state[0][o:o + n], state[1][o:o + n], state[2][o:o + n]
+
+    def plane(self, t, g: int, p: int):
+        """Player p's plane of game g from a flat per-player output tensor (padding removed)."""
+        o = int(self.plane_off[g]) + p * int(self.npad[g])
+        return t[o:o + int(self.N[g])]
