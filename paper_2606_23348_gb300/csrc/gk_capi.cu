@@ -411,6 +411,9 @@ int gen_read_state(gen_env* e, int16_t* h_army, int8_t* h_owner, int8_t* h_terra
         CUDA_TRY(cudaMemcpyAsync(h_scalars, e->d_scal, sizeof(GameScalars) * (size_t)e->G, cudaMemcpyDeviceToHost, s),
                  "read scalars");
     CUDA_TRY(cudaStreamSynchronize(s), "read_state sync");
+    // the device keeps per-map passable-neighbour bits above the cell type
+    if (h_terrain)
+        for (size_t i = 0; i < n; ++i) h_terrain[i] = (int8_t)(h_terrain[i] & 3);
     return GEN_OK;
 }
 
@@ -443,6 +446,9 @@ int gen_write_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, co
     CUDA_TRY(cudaMemcpyAsync(e->d_terrain, h_terrain, n, cudaMemcpyHostToDevice, s), "write terrain");
     CUDA_TRY(cudaMemcpyAsync(e->d_scal, sc.data(), sizeof(GameScalars) * (size_t)e->G, cudaMemcpyHostToDevice, s),
              "write scalars");
+    KArgs a = base_args(e, gk::OP_DERIVE);
+    int rc = launch(e, a, stream, "derive launch");
+    if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(s), "write_state sync");
     return GEN_OK;
 }

@@ -16,6 +16,7 @@ enum Op : int32_t {
     OP_OBSERVE = 2,  // outputs only
     OP_STEP = 3,     // full step, outputs
     OP_POLICY = 4,   // benchmark policy only
+    OP_DERIVE = 5,   // recompute cached per-map bits after a state upload
 };
 
 // Read-only description of one game (32 bytes).

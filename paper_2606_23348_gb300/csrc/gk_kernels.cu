@@ -1,16 +1,29 @@
 // Device code of libgenerals: one warp advances one Generals.io game.
 //
-// Per game and step (paper Section IV): the warp stages the board (int16
-// armies, int8 owners, int8 terrain) in shared memory, lane 0 resolves the
-// players' moves one after another (Sec. IV-D/IV-E), the warp applies
-// growth (Sec. IV-C) while it turns the board into 32-cell bitsets with
-// __ballot_sync (ownership per player, army >= 2, passable neighbour per
-// direction, edge columns), decides termination and reward (Sec. III),
-// regenerates finished games (Sec. IV-A), dilates ownership bitsets into
-// fog-of-war visibility with word shifts (Sec. IV-B), and expands bitsets
-// and board bytes into 16-cell observation and mask chunks written with
-// 128-bit streaming stores.  Optionally the benchmark policy picks the next
-// actions from the same bitsets (popc counts, a warp scan, a bit walk).
+// Per game and step (paper Section IV) the warp
+//   1. stages the board (int16 armies, int8 owners, int8 terrain) in shared
+//      memory with 128-bit loads;
+//   2. resolves the players' moves one after another on lane 0 (Sec. IV-D,
+//      IV-E), with a warp-wide pass for the land transfer of a captured
+//      general;
+//   3. applies growth (Sec. IV-C) while __ballot_sync turns the board into
+//      32-cell bitsets (ownership per player, army >= 2) and
+//      __reduce_add_sync totals the armies;
+//   4. decides termination and reward (Sec. III) and regenerates finished
+//      games (Sec. IV-A);
+//   5. dilates the (team) ownership bitsets into fog-of-war visibility with
+//      word shifts (Sec. IV-B);
+//   6. expands bitsets and board bytes into 16-cell observation and mask
+//      chunks written with 128-bit streaming stores;
+//   7. optionally picks the next actions with the benchmark policy: legal
+//      (cell, direction) counts per chunk, a warp scan to find the chunk, a
+//      16-lane scan to find the cell.
+//
+// Terrain bytes carry the cell type in bits 0-1 and, in bits 2-5, whether
+// the neighbour up / down / left / right exists and is not a mountain.  The
+// generator sets these bits once per map (mountains never change), so move
+// validation and the mask read them instead of the neighbours.  The public
+// state (gen_read_state) shows bits 0-1 only.
 //
 // No floating point decides anything: all game arithmetic is integer.
 #include <cuda_runtime.h>
@@ -46,15 +59,15 @@ __device__ __forceinline__ int uniform_below(uint32_t u, uint32_t n) { return (i
 struct Smem {
     int16_t* army;
     int8_t* owner;
-    int8_t* terrain;
-    uint32_t* own;   // [pmax][stride]
-    uint32_t* big;   // army >= 2
-    uint32_t* dp;    // [4][stride]: neighbour in direction d exists and is not a mountain
-    uint32_t* col0;  // first column
-    uint32_t* colL;  // last column
-    uint32_t* vis;   // [pmax][stride]
+    uint8_t* terrain;  // type | passable-neighbour bits << 2
+    uint32_t* own;     // [pmax][stride]
+    uint32_t* big;     // army >= 2
+    uint32_t* col0;    // first column
+    uint32_t* colL;    // last column
+    uint32_t* vis;     // [pmax][stride]
     uint32_t* tmp;
-    int32_t* misc;   // [0..7] general cells, [8..15] land, [16..23] army
+    uint16_t* cnt;     // [pmax][chunks]: legal (cell, direction) pairs per 16-cell chunk
+    int32_t* misc;     // [0..7] general cells, [8..15] land, [16..23] army
     int stride;
 };
 
@@ -63,14 +76,12 @@ __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
     const int np = a.npad_max, st = a.nw_stride, pm = a.pmax;
     s.army = reinterpret_cast<int16_t*>(base);
     s.owner = reinterpret_cast<int8_t*>(base + 2 * np);
-    s.terrain = reinterpret_cast<int8_t*>(base + 3 * np);
+    s.terrain = reinterpret_cast<uint8_t*>(base + 3 * np);
     uint32_t* w = reinterpret_cast<uint32_t*>(base + 4 * np);
     s.own = w;
     w += pm * st;
     s.big = w;
     w += st;
-    s.dp = w;
-    w += 4 * st;
     s.col0 = w;
     w += st;
     s.colL = w;
@@ -79,13 +90,16 @@ __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
     w += pm * st;
     s.tmp = w;
     w += st;
+    s.cnt = reinterpret_cast<uint16_t*>(w);
+    const int cnt_words = (pm * (np >> 4) + 1) / 2;
+    w += (cnt_words + 3) & ~3;
     s.misc = reinterpret_cast<int32_t*>(w);
     s.stride = st;
     return s;
 }
 
 struct Game {
-    int H, W, N, Npad, P, mode, nw;
+    int H, W, N, Npad, nch, P, mode, nw;
     int64_t plane_off;
     int cell_off, player_off, n_cities, dmin;
 };
@@ -96,6 +110,7 @@ __device__ __forceinline__ Game load_game(const GameInfo* gi) {
     g.W = gi->W;
     g.N = gi->N;
     g.Npad = gi->Npad;
+    g.nch = gi->Npad >> 4;
     g.P = gi->P;
     g.mode = gi->mode;
     g.nw = (gi->N + 31) >> 5;
@@ -112,6 +127,29 @@ __device__ __forceinline__ uint32_t valid_bits(int N, int w) {
     if (rem >= 32) return kFull;
     if (rem <= 0) return 0u;
     return (1u << rem) - 1u;
+}
+
+// passable-neighbour bits of every cell (bits 2..5 of the terrain byte),
+// from a mountain bitset so that no lane reads a byte another lane writes
+__device__ void derive_passable(const Game& g, const Smem& s, int lane) {
+    const int N = g.N, W = g.W, H = g.H;
+    for (int w = 0; w < g.nw; ++w) {
+        const int c = 32 * w + lane;
+        const unsigned m = __ballot_sync(kFull, c < N && (s.terrain[c] & 3) == kMountain);
+        if (lane == 0) s.tmp[w] = m;
+    }
+    __syncwarp();
+    for (int c = lane; c < N; c += 32) {
+        const int r = c / W, col = c - r * W;
+        auto mtn = [&](int x) { return (s.tmp[x >> 5] >> (x & 31)) & 1u; };
+        uint32_t b = 0;
+        if (r > 0 && !mtn(c - W)) b |= 1u;
+        if (r < H - 1 && !mtn(c + W)) b |= 2u;
+        if (col > 0 && !mtn(c - 1)) b |= 4u;
+        if (col < W - 1 && !mtn(c + 1)) b |= 8u;
+        s.terrain[c] = (uint8_t)((s.terrain[c] & 3) | (b << 2));
+    }
+    __syncwarp();
 }
 
 // ---- map generator (Sec. IV-A) ----------------------------------------------
@@ -228,6 +266,7 @@ __device__ void generate(const KArgs& a, const Game& g, const Smem& s, uint64_t 
             j += kGenAttempts;
         }
     }
+    derive_passable(g, s, lane);
 }
 
 // ---- one move on lane 0 (Sec. IV-D, IV-E) ----------------------------------
@@ -235,31 +274,21 @@ __device__ void generate(const KArgs& a, const Game& g, const Smem& s, uint64_t 
 // bits 16..19 (+1), or 0 when no general fell.
 __device__ int resolve_move(const Game& g, const Smem& s, int p, int32_t act, uint32_t& alive, uint32_t& invalid,
                             uint32_t& sat) {
-    const int N = g.N, W = g.W, H = g.H;
-    if (act < 0 || act >= 9 * N) {
+    if (act < 0 || act >= 9 * g.N) {
         invalid += 1;
         return 0;
     }
     const int c = act / 9, k = act - 9 * c;
     if (k == 0) return 0;
     const int d = (k - 1) & 3;
-    const bool half = k >= 5;
-    int r = c / W, col = c - r * W;
-    if (d == 0) r -= 1;
-    if (d == 1) r += 1;
-    if (d == 2) col -= 1;
-    if (d == 3) col += 1;
     const int av = s.army[c];
-    if (s.owner[c] != p || av < 2 || r < 0 || r >= H || col < 0 || col >= W) {
+    // bit 2+d: the neighbour towards d exists and is not a mountain
+    if (s.owner[c] != p || av < 2 || !((s.terrain[c] >> (2 + d)) & 1u)) {
         invalid += 1;
         return 0;
     }
-    const int dst = r * W + col;
-    if (s.terrain[dst] == kMountain) {
-        invalid += 1;
-        return 0;
-    }
-    const int moved = half ? (av >> 1) : (av - 1);
+    const int dst = c + (d == 0 ? -g.W : d == 1 ? g.W : d == 2 ? -1 : 1);
+    const int moved = (k >= 5) ? (av >> 1) : (av - 1);
     s.army[c] = (int16_t)(av - moved);
     const int o = s.owner[dst];
     const int def = s.army[dst];
@@ -270,14 +299,14 @@ __device__ int resolve_move(const Game& g, const Smem& s, int p, int32_t act, ui
             sat += 1;
         }
         s.army[dst] = (int16_t)sum;
-        if (o != p && s.terrain[dst] != kGeneral) s.owner[dst] = (int8_t)p;
+        if (o != p && (s.terrain[dst] & 3) != kGeneral) s.owner[dst] = (int8_t)p;
         return 0;
     }
     if (moved > def) {
         s.owner[dst] = (int8_t)p;
         s.army[dst] = (int16_t)(moved - def);
-        if (s.terrain[dst] == kGeneral && o >= 0) {
-            s.terrain[dst] = kCastle;
+        if ((s.terrain[dst] & 3) == kGeneral && o >= 0) {
+            s.terrain[dst] = (uint8_t)((s.terrain[dst] & ~3u) | kCastle);
             alive &= ~(1u << o);
             return dst | ((o + 1) << 16);
         }
@@ -289,104 +318,165 @@ __device__ int resolve_move(const Game& g, const Smem& s, int p, int32_t act, ui
     return 0;
 }
 
-// ---- growth + bitsets + scoreboard (one cell per lane per word) ------------
-__device__ uint32_t cell_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, int lane) {
-    const int N = g.N, W = g.W, H = g.H, P = g.P, nw = g.nw;
-    const int q32 = 32 / W, r32 = 32 - q32 * W;
-    int r = lane / W, col = lane - (lane / W) * W;
+// ---- growth + bitsets + army totals, 16 cells per lane ---------------------
+// Bytes are compared four at a time inside 32-bit words: zero_bytes(x) has
+// 0x80 in every byte of x that is zero (exact, no carries between bytes).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
+    const uint32_t t = (x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+    return ~(t | x) & 0x80808080u;
+}
+// bits 7, 15, 23, 31 of x -> bits 0..3
+__device__ __forceinline__ uint32_t gather4(uint32_t x80) { return (x80 * 0x00204081u) >> 28; }
+
+template <int PT>
+__device__ uint32_t chunk_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, int lane) {
+    const int P = g.P, nch = g.nch, st2 = 2 * s.stride;
+    const bool grow = grow_s || grow_p;
     uint32_t sat = 0;
-    int land[kMaxPlayers], arm[kMaxPlayers];
+    int arm[PT];
 #pragma unroll
-    for (int p = 0; p < kMaxPlayers; ++p) land[p] = arm[p] = 0;
-    for (int w = 0; w < nw; ++w) {
-        const int c = 32 * w + lane;
-        const bool valid = c < N;
-        int t = kMountain, o = -1, av = 0;
-        if (valid) {
-            t = s.terrain[c];
-            o = s.owner[c];
-            av = s.army[c];
-            if (o >= 0 && ((grow_s && (t == kGeneral || t == kCastle)) || (grow_p && t == kPlain))) {
-                av += 1;
-                if (av > kArmyMax) {
-                    av = kArmyMax;
-                    sat += 1;
+    for (int p = 0; p < PT; ++p) arm[p] = 0;
+    uint16_t* own16 = reinterpret_cast<uint16_t*>(s.own);
+    uint16_t* big16 = reinterpret_cast<uint16_t*>(s.big);
+    for (int ch = lane; ch < nch; ch += 32) {
+        const int c0 = ch << 4;
+        const uint4 O = *reinterpret_cast<const uint4*>(s.owner + c0);
+        const uint4 A0 = *reinterpret_cast<const uint4*>(s.army + c0);
+        const uint4 A1 = *reinterpret_cast<const uint4*>(s.army + c0 + 8);
+        const uint32_t ow[4] = {O.x, O.y, O.z, O.w};
+        uint32_t aw[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+        if (grow) {
+            // owned generals / castles (+1 on even turns), owned plain (+1 every 50)
+            const uint4 T = *reinterpret_cast<const uint4*>(s.terrain + c0);
+            const uint32_t tw[4] = {T.x, T.y, T.z, T.w};
+            bool changed = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t owned = ~zero_bytes(~ow[k]) & 0x80808080u;
+                const uint32_t structure = (tw[k] << 6) & 0x80808080u;       // type bit 1
+                const uint32_t plain = zero_bytes(tw[k] & 0x03030303u);
+                const uint32_t g80 = owned & ((grow_s ? structure : 0u) | (grow_p ? plain : 0u));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t inc = (__byte_perm(g80, 0, h ? 0x3322 : 0x1100) >> 15) & 0x00010001u;
+                    uint32_t v = aw[2 * k + h] + inc;
+                    const uint32_t ov = v & 0x80008000u;  // 32767 + 1
+                    sat += __popc(ov);
+                    v -= ov >> 15;
+                    changed |= (inc != 0u);
+                    aw[2 * k + h] = v;
                 }
-                s.army[c] = (int16_t)av;
+            }
+            if (changed) {
+                *reinterpret_cast<uint4*>(s.army + c0) = make_uint4(aw[0], aw[1], aw[2], aw[3]);
+                *reinterpret_cast<uint4*>(s.army + c0 + 8) = make_uint4(aw[4], aw[5], aw[6], aw[7]);
             }
         }
-        const bool up = valid && r > 0 && s.terrain[c - W] != kMountain;
-        const bool dn = valid && r < H - 1 && s.terrain[c + W] != kMountain;
-        const bool lf = valid && col > 0 && s.terrain[c - 1] != kMountain;
-        const bool rt = valid && col < W - 1 && s.terrain[c + 1] != kMountain;
-        const unsigned b_big = __ballot_sync(kFull, valid && av >= 2);
-        const unsigned b_up = __ballot_sync(kFull, up);
-        const unsigned b_dn = __ballot_sync(kFull, dn);
-        const unsigned b_lf = __ballot_sync(kFull, lf);
-        const unsigned b_rt = __ballot_sync(kFull, rt);
-        const unsigned b_c0 = __ballot_sync(kFull, valid && col == 0);
-        const unsigned b_cl = __ballot_sync(kFull, valid && col == W - 1);
-        if (lane == 0) {
-            s.big[w] = b_big;
-            s.dp[0 * s.stride + w] = b_up;
-            s.dp[1 * s.stride + w] = b_dn;
-            s.dp[2 * s.stride + w] = b_lf;
-            s.dp[3 * s.stride + w] = b_rt;
-            s.col0[w] = b_c0;
-            s.colL[w] = b_cl;
+        // army >= 2: bit 15 / 31 of army + 0x7FFE per halfword
+        uint32_t big = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t y0 = aw[2 * k] + 0x7FFE7FFEu, y1 = aw[2 * k + 1] + 0x7FFE7FFEu;
+            big |= gather4(__byte_perm(y0, y1, 0x7531) & 0x80808080u) << (4 * k);
+        }
+        big16[ch] = (uint16_t)big;
+        // army totals: low and high bytes of 4 armies dotted with 0/1 owner bytes
+        uint32_t lo4[4], hi4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            lo4[k] = __byte_perm(aw[2 * k], aw[2 * k + 1], 0x6420);
+            hi4[k] = __byte_perm(aw[2 * k], aw[2 * k + 1], 0x7531);
         }
 #pragma unroll
-        for (int p = 0; p < kMaxPlayers; ++p) {
+        for (int p = 0; p < PT; ++p) {
             if (p < P) {
-                const unsigned b_own = __ballot_sync(kFull, o == p);
-                if (lane == 0) s.own[p * s.stride + w] = b_own;
-                land[p] += __popc(b_own);
-                arm[p] += __reduce_add_sync(kFull, (unsigned)(o == p ? av : 0));
+                uint32_t own = 0, slo = 0, shi = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t z = zero_bytes(ow[k] ^ (0x01010101u * (uint32_t)p));
+                    own |= gather4(z) << (4 * k);
+                    const uint32_t m = z >> 7;
+                    slo = __dp4a(lo4[k], m, slo);
+                    shi = __dp4a(hi4[k], m, shi);
+                }
+                arm[p] += (int)(slo + 256u * shi);
+                own16[p * st2 + ch] = (uint16_t)own;
             }
         }
-        col += r32;
-        r += q32;
-        if (col >= W) {
-            col -= W;
-            r += 1;
+        if ((nch & 1) && ch == nch - 1) {  // unused upper half of the last word
+            big16[nch] = 0;
+#pragma unroll
+            for (int p = 0; p < PT; ++p)
+                if (p < P) own16[p * st2 + nch] = 0;
         }
     }
     if (lane == 0) {
 #pragma unroll
-        for (int p = 0; p < kMaxPlayers; ++p) {
-            s.misc[8 + p] = land[p];
-            s.misc[16 + p] = arm[p];
+        for (int p = 0; p < kMaxPlayers; ++p) s.misc[16 + p] = 0;
+    }
+#pragma unroll
+    for (int p = 0; p < PT; ++p) {
+        if (p < P) {
+            const int tot = (int)__reduce_add_sync(kFull, (unsigned)arm[p]);
+            if (lane == 0) s.misc[16 + p] = tot;
         }
     }
     __syncwarp();
     return __reduce_add_sync(kFull, sat);
 }
 
+__device__ __forceinline__ uint32_t cell_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, int lane) {
+    if (g.P <= 2) return chunk_pass<2>(g, s, grow_s, grow_p, lane);
+    if (g.P <= 4) return chunk_pass<4>(g, s, grow_s, grow_p, lane);
+    return chunk_pass<8>(g, s, grow_s, grow_p, lane);
+}
+
+// ---- board geometry: first and last column bitsets -------------------------
+__device__ void column_pass(const Game& g, const Smem& s, int lane) {
+    const int N = g.N, W = g.W, nw = g.nw;
+    for (int w = lane; w < nw; w += 32) {
+        const int base = 32 * w;
+        uint32_t c0 = 0, cl = 0;
+        for (int c = ((base + W - 1) / W) * W; c < base + 32; c += W) c0 |= 1u << (c - base);
+        for (int c = ((base + W) / W) * W - 1; c < base + 32; c += W) cl |= 1u << (c - base);
+        const uint32_t v = valid_bits(N, w);
+        s.col0[w] = c0 & v;
+        s.colL[w] = cl & v;
+    }
+    __syncwarp();
+}
+
 // ---- fog: 3x3 dilation of the (team) ownership bitset (Sec. IV-B) ----------
+// Also counts each player's land for the scoreboard.
 __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane) {
     const int N = g.N, W = g.W, nw = g.nw, st = s.stride;
     const int q = W >> 5, sh = W & 31;
+    const bool team = g.mode == 1;
     for (int p = 0; p < g.P; ++p) {
-        const bool team = g.mode == 1;
         const uint32_t* own = s.own + p * st;
         const uint32_t* ally = s.own + (p ^ 1) * st;
+        int land = 0;
         for (int w = lane; w < nw; w += 32) {
-            uint32_t T = own[w] | (team ? ally[w] : 0u);
-            uint32_t Tm = (w > 0) ? (own[w - 1] | (team ? ally[w - 1] : 0u)) : 0u;
-            uint32_t Tp = (w + 1 < nw) ? (own[w + 1] | (team ? ally[w + 1] : 0u)) : 0u;
-            uint32_t L = (T << 1) | (Tm >> 31);  // bit c <- cell c-1
-            uint32_t R = (T >> 1) | (Tp << 31);  // bit c <- cell c+1
+            const uint32_t mine = own[w];
+            land += __popc(mine);
+            const uint32_t T = mine | (team ? ally[w] : 0u);
+            const uint32_t Tm = (w > 0) ? (own[w - 1] | (team ? ally[w - 1] : 0u)) : 0u;
+            const uint32_t Tp = (w + 1 < nw) ? (own[w + 1] | (team ? ally[w + 1] : 0u)) : 0u;
+            const uint32_t L = (T << 1) | (Tm >> 31);  // bit c <- cell c-1
+            const uint32_t R = (T >> 1) | (Tp << 31);  // bit c <- cell c+1
             s.tmp[w] = (T | (L & ~s.col0[w]) | (R & ~s.colL[w])) & valid_bits(N, w);
         }
+        land = (int)__reduce_add_sync(kFull, (unsigned)land);
+        if (lane == 0) s.misc[8 + p] = land;
         __syncwarp();
         const bool seeing = (alive >> p) & 1u;
         for (int w = lane; w < nw; w += 32) {
             const uint32_t h = s.tmp[w];
             // bit c <- cell c - W (row above) and cell c + W (row below)
-            int wa = w - q;
+            const int wa = w - q;
             uint32_t up = (wa >= 0 ? s.tmp[wa] << sh : 0u);
             if (sh && wa - 1 >= 0) up |= s.tmp[wa - 1] >> (32 - sh);
-            int wb = w + q;
+            const int wb = w + q;
             uint32_t dn = (wb < nw ? s.tmp[wb] >> sh : 0u);
             if (sh && wb + 1 < nw) dn |= s.tmp[wb + 1] << (32 - sh);
             s.vis[p * st + w] = seeing ? ((h | up | dn) & valid_bits(N, w)) : 0u;
@@ -399,115 +489,134 @@ __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane)
 __device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
 
 // ---- observation + mask chunks of 16 cells (Sec. IV-B, App. A, Sec. IV-G) --
+// WRITE: store the planes; COUNT: legal (cell, direction) pairs per chunk.
+template <bool WRITE, bool COUNT>
 __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished, int lane) {
-    const int nch = g.Npad >> 4, st = s.stride;
-    const int items = g.P * nch;
-    for (int it = lane; it < items; it += 32) {
-        const int p = it / nch;
-        const int c0 = (it - p * nch) << 4;
+    const int nch = g.nch, st = s.stride, P = g.P;
+    int p = 0, ch = lane;
+    while (p < P && ch >= nch) {
+        ch -= nch;
+        ++p;
+    }
+    while (p < P) {
+        const int c0 = ch << 4;
         const int wi = c0 >> 5, sh = c0 & 16;
-        const uint32_t vis16 = (s.vis[p * st + wi] >> sh) & 0xFFFFu;
         uint32_t mv = 0;
         if (!finished && ((alive >> p) & 1u)) mv = ((s.own[p * st + wi] & s.big[wi]) >> sh) & 0xFFFFu;
-        const uint32_t mU = mv & (s.dp[0 * st + wi] >> sh);
-        const uint32_t mD = mv & (s.dp[1 * st + wi] >> sh);
-        const uint32_t mL = mv & (s.dp[2 * st + wi] >> sh);
-        const uint32_t mR = mv & (s.dp[3 * st + wi] >> sh);
-        const uint4 A0 = *reinterpret_cast<const uint4*>(s.army + c0);
-        const uint4 A1 = *reinterpret_cast<const uint4*>(s.army + c0 + 8);
-        const uint4 O = *reinterpret_cast<const uint4*>(s.owner + c0);
         const uint4 T = *reinterpret_cast<const uint4*>(s.terrain + c0);
-        const uint32_t aw[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
-        const uint32_t ow[4] = {O.x, O.y, O.z, O.w};
         const uint32_t tw[4] = {T.x, T.y, T.z, T.w};
-        uint32_t oa[8], oo[4], ot[4], ov[4], om[4];
+        uint32_t om[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint32_t v1 = spread4((vis16 >> (4 * k)) & 15u);
-            const uint32_t bm = v1 * 0xFFu;
-            oo[k] = (ow[k] & bm) | (0xFEFEFEFEu & ~bm);
-            const uint32_t fogc = ((tw[k] ^ (tw[k] >> 1)) & 0x01010101u) | 0x04040404u;
-            ot[k] = (tw[k] & bm) | (fogc & ~bm);
-            ov[k] = v1;
-            oa[2 * k] = aw[2 * k] & __byte_perm(bm, 0, 0x1100);
-            oa[2 * k + 1] = aw[2 * k + 1] & __byte_perm(bm, 0, 0x3322);
-            const uint32_t m = spread4((mU >> (4 * k)) & 15u) | (spread4((mD >> (4 * k)) & 15u) << 1) |
-                               (spread4((mL >> (4 * k)) & 15u) << 2) | (spread4((mR >> (4 * k)) & 15u) << 3);
-            om[k] = m * 0x11u;
+            const uint32_t dpb = ((tw[k] >> 2) & 0x0F0F0F0Fu) * 0x11u;
+            om[k] = dpb & (spread4((mv >> (4 * k)) & 15u) * 0xFFu);
         }
-        const int64_t off = g.plane_off + (int64_t)p * g.Npad + c0;
-        uint4* pa = reinterpret_cast<uint4*>(a.obs_army + off);
-        __stcs(pa, make_uint4(oa[0], oa[1], oa[2], oa[3]));
-        __stcs(pa + 1, make_uint4(oa[4], oa[5], oa[6], oa[7]));
-        __stcs(reinterpret_cast<uint4*>(a.obs_owner + off), make_uint4(oo[0], oo[1], oo[2], oo[3]));
-        __stcs(reinterpret_cast<uint4*>(a.obs_terrain + off), make_uint4(ot[0], ot[1], ot[2], ot[3]));
-        __stcs(reinterpret_cast<uint4*>(a.obs_vis + off), make_uint4(ov[0], ov[1], ov[2], ov[3]));
-        __stcs(reinterpret_cast<uint4*>(a.mask + off), make_uint4(om[0], om[1], om[2], om[3]));
+        if (COUNT) {
+            const uint32_t n = __popc(om[0] & 0x0F0F0F0Fu) + __popc(om[1] & 0x0F0F0F0Fu) +
+                               __popc(om[2] & 0x0F0F0F0Fu) + __popc(om[3] & 0x0F0F0F0Fu);
+            s.cnt[p * nch + ch] = (uint16_t)n;
+        }
+        if (WRITE) {
+            const uint32_t vis16 = (s.vis[p * st + wi] >> sh) & 0xFFFFu;
+            const uint4 A0 = *reinterpret_cast<const uint4*>(s.army + c0);
+            const uint4 A1 = *reinterpret_cast<const uint4*>(s.army + c0 + 8);
+            const uint4 O = *reinterpret_cast<const uint4*>(s.owner + c0);
+            const uint32_t aw[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+            const uint32_t ow[4] = {O.x, O.y, O.z, O.w};
+            uint32_t oa[8], oo[4], ot[4], ov[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t v1 = spread4((vis16 >> (4 * k)) & 15u);
+                const uint32_t bm = v1 * 0xFFu;
+                oo[k] = (ow[k] & bm) | (0xFEFEFEFEu & ~bm);
+                const uint32_t tt = tw[k] & 0x03030303u;
+                const uint32_t fogc = ((tt ^ (tt >> 1)) & 0x01010101u) | 0x04040404u;
+                ot[k] = (tt & bm) | (fogc & ~bm);
+                ov[k] = v1;
+                oa[2 * k] = aw[2 * k] & __byte_perm(bm, 0, 0x1100);
+                oa[2 * k + 1] = aw[2 * k + 1] & __byte_perm(bm, 0, 0x3322);
+            }
+            const int64_t off = g.plane_off + (int64_t)p * g.Npad + c0;
+            uint4* pa = reinterpret_cast<uint4*>(a.obs_army + off);
+            __stcs(pa, make_uint4(oa[0], oa[1], oa[2], oa[3]));
+            __stcs(pa + 1, make_uint4(oa[4], oa[5], oa[6], oa[7]));
+            __stcs(reinterpret_cast<uint4*>(a.obs_owner + off), make_uint4(oo[0], oo[1], oo[2], oo[3]));
+            __stcs(reinterpret_cast<uint4*>(a.obs_terrain + off), make_uint4(ot[0], ot[1], ot[2], ot[3]));
+            __stcs(reinterpret_cast<uint4*>(a.obs_vis + off), make_uint4(ov[0], ov[1], ov[2], ov[3]));
+            __stcs(reinterpret_cast<uint4*>(a.mask + off), make_uint4(om[0], om[1], om[2], om[3]));
+        }
+        ch += 32;
+        while (p < P && ch >= nch) {
+            ch -= nch;
+            ++p;
+        }
     }
+    __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
 }
 
 // ---- benchmark policy: uniform legal (cell, direction), split p = 0.2 -------
+// Needs the chunk counts of output_pass<*, true>.
 __device__ void policy_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished,
                             uint32_t frame, uint64_t gid, int lane) {
-    const int nw = g.nw, st = s.stride;
-    const int wpl = (nw + 31) >> 5;
-    const int w0 = lane * wpl;
+    const int nch = g.nch;
+    const int cpl = (nch + 31) >> 5;  // consecutive chunks per lane
+    const int c_lo = lane * cpl;
+    // lane p hashes player p's two draws
+    uint32_t u1 = 0, u2 = 0;
+    if (lane < g.P) {
+        const uint64_t K = hkey(a.policy_seed, gid, frame, (uint64_t)lane);
+        u1 = hdraw(K, 0);
+        u2 = hdraw(K, 1);
+    }
     for (int p = 0; p < g.P; ++p) {
-        const bool on = !finished && ((alive >> p) & 1u);
-        uint32_t cnt = 0;
-        if (on) {
-            for (int w = w0; w < w0 + wpl && w < nw; ++w) {
-                const uint32_t mv = s.own[p * st + w] & s.big[w];
-                cnt += __popc(mv & s.dp[w]) + __popc(mv & s.dp[st + w]) + __popc(mv & s.dp[2 * st + w]) +
-                       __popc(mv & s.dp[3 * st + w]);
-            }
-        }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
+        const uint16_t* cnt = s.cnt + p * nch;
+        uint32_t mine = 0;
+        for (int c = c_lo; c < c_lo + cpl && c < nch; ++c) mine += cnt[c];
+        const uint32_t incl = warp_incl_scan(mine, lane);
         const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint32_t pu1 = __shfl_sync(kFull, u1, p);
+        const uint32_t pu2 = __shfl_sync(kFull, u2, p);
         int32_t action = 0;
-        if (total > 0) {
-            const uint64_t K = hkey(a.policy_seed, gid, frame, (uint64_t)p);
-            const uint32_t j = (uint32_t)uniform_below(hdraw(K, 0), total);
-            const bool split = hdraw(K, 1) < kSplitThresh;
-            const unsigned b = __ballot_sync(kFull, incl > j);
-            const int L = __ffs(b) - 1;
-            int32_t found = 0;
+        if (total > 0 && !finished && ((alive >> p) & 1u)) {
+            const uint32_t j = (uint32_t)uniform_below(pu1, total);
+            const int L = __ffs(__ballot_sync(kFull, incl > j)) - 1;
+            // chunk holding pair j, and j's rank inside it (lane L walks its chunks)
+            uint32_t jj = j - __shfl_sync(kFull, incl - mine, L);
+            int chs = 0;
             if (lane == L) {
-                uint32_t jj = j - (incl - cnt);
-                for (int w = w0; w < w0 + wpl && w < nw; ++w) {
-                    const uint32_t mv = s.own[p * st + w] & s.big[w];
-                    const uint32_t u = mv & s.dp[w], dn = mv & s.dp[st + w], l = mv & s.dp[2 * st + w],
-                                   r = mv & s.dp[3 * st + w];
-                    const uint32_t cw = __popc(u) + __popc(dn) + __popc(l) + __popc(r);
-                    if (jj >= cw) {
-                        jj -= cw;
-                        continue;
-                    }
-                    uint32_t m = u | dn | l | r;
-                    while (m) {
-                        const int bit = __ffs(m) - 1;
-                        const uint32_t dirs = ((u >> bit) & 1u) | (((dn >> bit) & 1u) << 1) |
-                                              (((l >> bit) & 1u) << 2) | (((r >> bit) & 1u) << 3);
-                        const uint32_t cb = __popc(dirs);
-                        if (jj < cb) {
-                            uint32_t dd = dirs;
-                            for (uint32_t z = 0; z < jj; ++z) dd &= dd - 1;
-                            const int d = __ffs(dd) - 1;
-                            found = (32 * w + bit) * 9 + (split ? 5 + d : 1 + d);
-                            break;
-                        }
-                        jj -= cb;
-                        m &= m - 1;
-                    }
-                    break;
+                chs = c_lo;
+                while (jj >= cnt[chs]) {
+                    jj -= cnt[chs];
+                    ++chs;
                 }
             }
-            action = __shfl_sync(kFull, found, L);
+            chs = __shfl_sync(kFull, chs, L);
+            jj = __shfl_sync(kFull, jj, L);
+            // lanes 0..15 take the 16 cells of the chunk
+            const int c = chs * 16 + (lane & 15);
+            uint32_t dirs = 0;
+            if (lane < 16 && s.owner[c] == p && s.army[c] >= 2) dirs = (s.terrain[c] >> 2) & 15u;
+            const uint32_t nd = __popc(dirs);
+            const uint32_t ic = warp_incl_scan(nd, lane);
+            const int B = __ffs(__ballot_sync(kFull, ic > jj)) - 1;
+            int32_t found = 0;
+            if (lane == B) {
+                const uint32_t r = jj - (ic - nd);
+                uint32_t dd = dirs;
+                for (uint32_t z = 0; z < r; ++z) dd &= dd - 1;
+                const int d = __ffs(dd) - 1;
+                found = c * 9 + ((pu2 < kSplitThresh) ? 5 + d : 1 + d);
+            }
+            action = __shfl_sync(kFull, found, B);
         }
         if (lane == 0) a.next_actions[g.player_off + p] = action;
     }
@@ -546,7 +655,7 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_generals(const KArgs a) {
+__global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
     extern __shared__ __align__(16) char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -559,17 +668,18 @@ __global__ void __launch_bounds__(256) k_generals(const KArgs a) {
     const uint64_t gid = a.game_id_base + (uint64_t)gidx;
     GameScalars* sc = a.scal + gidx;
 
-    uint32_t turn, frame, epoch, alive, finished, invalid, saturated;
-    if (a.op == OP_CREATE) {
-        turn = frame = epoch = finished = invalid = saturated = 0;
-    } else {
-        turn = sc->turn;
-        frame = sc->frame;
-        epoch = sc->epoch;
-        alive = sc->alive;
-        finished = sc->finished;
-        invalid = sc->invalid;
-        saturated = sc->saturated;
+    uint32_t turn = 0, frame = 0, epoch = 0, alive = 0, finished = 0, invalid = 0, saturated = 0, err = 0;
+    if (a.op != OP_CREATE) {
+        const uint4 s0 = *reinterpret_cast<const uint4*>(sc);
+        const uint4 s1 = *(reinterpret_cast<const uint4*>(sc) + 1);
+        turn = s0.x;
+        frame = s0.y;
+        epoch = s0.z;
+        alive = s0.w;
+        finished = s1.x;
+        invalid = s1.y;
+        saturated = s1.z;
+        err = s1.w;
     }
     const uint32_t all_alive = (1u << g.P) - 1u;
     bool wrote_state = false;
@@ -586,103 +696,100 @@ __global__ void __launch_bounds__(256) k_generals(const KArgs a) {
         wrote_state = true;
     } else {
         load_board(a, g, s, lane);
-        if (a.op == OP_STEP) {
-            if (!finished) {
-                // moves in rotating priority, each checked when it runs (Q1)
-                const int32_t my_act = (lane < g.P) ? a.actions[g.player_off + lane] : 0;
-                uint32_t eliminated = 0;
-                uint32_t inv0 = 0, sat0 = 0;
-                for (int k = 0; k < g.P; ++k) {
-                    const int p = (int)((turn + (uint32_t)k) % (uint32_t)g.P);
-                    const int32_t act = __shfl_sync(kFull, my_act, p);
-                    int cap = 0;
-                    if (lane == 0 && ((alive >> p) & 1u)) cap = resolve_move(g, s, p, act, alive, inv0, sat0);
-                    cap = __shfl_sync(kFull, cap, 0);
-                    alive = __shfl_sync(kFull, alive, 0);
-                    __syncwarp();
-                    if (cap) {
-                        // land transfer: every other cell of the loser, army - army/2 (Q7)
-                        const int dst = cap & 0xFFFF, q = (cap >> 16) - 1;
-                        eliminated |= 1u << q;
-                        for (int c = lane; c < g.N; c += 32) {
-                            if (c != dst && s.owner[c] == q) {
-                                s.owner[c] = (int8_t)p;
-                                const int av = s.army[c];
-                                s.army[c] = (int16_t)(av - (av >> 1));
-                            }
+        if (a.op == OP_DERIVE) {
+            derive_passable(g, s, lane);
+            wrote_state = true;
+        } else if (a.op == OP_STEP && !finished) {
+            // moves in rotating priority, each checked when it runs (Q1)
+            const int32_t my_act = (lane < g.P) ? a.actions[g.player_off + lane] : 0;
+            uint32_t eliminated = 0;
+            uint32_t inv0 = 0, sat0 = 0;
+            for (int k = 0; k < g.P; ++k) {
+                const int p = (int)((turn + (uint32_t)k) % (uint32_t)g.P);
+                const int32_t act = __shfl_sync(kFull, my_act, p);
+                int cap = 0;
+                if (lane == 0 && ((alive >> p) & 1u)) cap = resolve_move(g, s, p, act, alive, inv0, sat0);
+                cap = __shfl_sync(kFull, cap, 0);
+                alive = __shfl_sync(kFull, alive, 0);
+                __syncwarp();
+                if (cap) {
+                    // land transfer: every other cell of the loser, army - army/2 (Q7)
+                    const int dst = cap & 0xFFFF, q = (cap >> 16) - 1;
+                    eliminated |= 1u << q;
+                    for (int c = lane; c < g.N; c += 32) {
+                        if (c != dst && s.owner[c] == q) {
+                            s.owner[c] = (int8_t)p;
+                            const int av = s.army[c];
+                            s.army[c] = (int16_t)(av - (av >> 1));
                         }
-                        __syncwarp();
                     }
+                    __syncwarp();
                 }
-                invalid += __shfl_sync(kFull, inv0, 0);
-                saturated += __shfl_sync(kFull, sat0, 0);
-                turn += 1;
-                saturated += cell_pass(g, s, (turn % 2u) == 0u, (turn % 50u) == 0u, lane);
-                // termination and reward (Sec. III, IV-D, IV-E; Q17, Q21)
-                if (g.mode == 1) {
-                    const bool dead0 = (alive & 0x3u) == 0u, dead1 = (alive & 0xCu) == 0u;
-                    if (dead0 || dead1) {
-                        done = 1;
-                        const bool mine_dead = ((lane >> 1) == 0) ? dead0 : dead1;
-                        my_reward = mine_dead ? -1.0f : 1.0f;
-                    }
-                } else {
-                    if ((eliminated >> lane) & 1u) my_reward = -1.0f;
-                    if (__popc(alive) <= 1) {
-                        done = 1;
-                        if ((alive >> lane) & 1u) my_reward = 1.0f;
-                    }
-                }
-                if (!done && a.max_turns > 0 && turn >= (uint32_t)a.max_turns) done = 2;
-                if (done) {
-                    if (a.auto_reset) {
-                        epoch += 1;
-                        generate(a, g, s, gid, epoch, lane);
-                        turn = 0;
-                        alive = all_alive;
-                        cell_pass(g, s, false, false, lane);
-                    } else {
-                        finished = 1;
-                    }
-                }
-                wrote_state = true;
-            } else {
-                cell_pass(g, s, false, false, lane);  // frozen game: outputs only
             }
-            frame += 1;
+            invalid += __shfl_sync(kFull, inv0, 0);
+            saturated += __shfl_sync(kFull, sat0, 0);
+            turn += 1;
+            saturated += cell_pass(g, s, (turn % 2u) == 0u, (turn % 50u) == 0u, lane);
+            // termination and reward (Sec. III, IV-D, IV-E; Q17, Q21)
+            if (g.mode == 1) {
+                const bool dead0 = (alive & 0x3u) == 0u, dead1 = (alive & 0xCu) == 0u;
+                if (dead0 || dead1) {
+                    done = 1;
+                    const bool mine_dead = ((lane >> 1) == 0) ? dead0 : dead1;
+                    my_reward = mine_dead ? -1.0f : 1.0f;
+                }
+            } else {
+                if ((eliminated >> lane) & 1u) my_reward = -1.0f;
+                if (__popc(alive) <= 1) {
+                    done = 1;
+                    if ((alive >> lane) & 1u) my_reward = 1.0f;
+                }
+            }
+            if (!done && a.max_turns > 0 && turn >= (uint32_t)a.max_turns) done = 2;
+            if (done) {
+                if (a.auto_reset) {
+                    epoch += 1;
+                    generate(a, g, s, gid, epoch, lane);
+                    turn = 0;
+                    alive = all_alive;
+                    cell_pass(g, s, false, false, lane);
+                } else {
+                    finished = 1;
+                }
+            }
+            wrote_state = true;
         } else {
-            cell_pass(g, s, false, false, lane);
+            cell_pass(g, s, false, false, lane);  // observe, policy, or a frozen game
         }
+        if (a.op == OP_STEP) frame += 1;
     }
 
-    if (a.op != OP_POLICY) {
-        if (a.do_outputs) {
-            fog_pass(g, s, alive, lane);
-            output_pass(a, g, s, alive, finished != 0, lane);
-            if (lane < g.P) {
-                a.reward[g.player_off + lane] = my_reward;
-                a.scoreboard[2 * (g.player_off + lane) + 0] = s.misc[8 + lane];
-                a.scoreboard[2 * (g.player_off + lane) + 1] = s.misc[16 + lane];
-            }
-            if (lane == 0) a.done[gidx] = (uint8_t)done;
+    const bool fin = finished != 0;
+    if (a.do_outputs) {
+        column_pass(g, s, lane);
+        fog_pass(g, s, alive, lane);
+        if (a.next_actions)
+            output_pass<true, true>(a, g, s, alive, fin, lane);
+        else
+            output_pass<true, false>(a, g, s, alive, fin, lane);
+        if (lane < g.P) {
+            a.reward[g.player_off + lane] = my_reward;
+            a.scoreboard[2 * (g.player_off + lane) + 0] = s.misc[8 + lane];
+            a.scoreboard[2 * (g.player_off + lane) + 1] = s.misc[16 + lane];
         }
+        if (lane == 0) a.done[gidx] = (uint8_t)done;
+    } else if (a.next_actions) {
+        output_pass<false, true>(a, g, s, alive, fin, lane);
     }
-    if (a.next_actions) policy_pass(a, g, s, alive, finished != 0, frame, gid, lane);
+    if (a.next_actions) policy_pass(a, g, s, alive, fin, frame, gid, lane);
     if (wrote_state) {
         __syncwarp();
         store_board(a, g, s, lane);
     }
     if (lane == 0 && a.op != OP_OBSERVE && a.op != OP_POLICY) {
-        GameScalars o;
-        o.turn = turn;
-        o.frame = frame;
-        o.epoch = epoch;
-        o.alive = alive;
-        o.finished = finished;
-        o.invalid = invalid;
-        o.saturated = saturated;
-        o.err = (a.op == OP_CREATE) ? 0u : sc->err;
-        *sc = o;
+        uint4* dst = reinterpret_cast<uint4*>(sc);
+        dst[0] = make_uint4(turn, frame, epoch, alive);
+        dst[1] = make_uint4(finished, invalid, saturated, a.op == OP_CREATE ? 0u : err);
     }
 }
 
@@ -696,7 +803,9 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
     int nw = (npad_max + 31) / 32;
     nw = (nw + 3) & ~3;
     if (nw_stride) *nw_stride = nw;
-    return 4 * npad_max + 4 * nw * (2 * pmax + 8) + 4 * 24;
+    const int cnt_words = (pmax * (npad_max >> 4) + 1) / 2;
+    const int cnt_pad = (cnt_words + 3) & ~3;
+    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + 4 * cnt_pad + 4 * 24;
 }
 
 int launch_step(const KArgs& a, int warps_per_cta, void* stream) {
