@@ -145,6 +145,24 @@ int gen_step(gen_env *env, const int32_t *d_actions, const gen_outputs *out, voi
 int gen_step_policy(gen_env *env, const int32_t *d_actions, const gen_outputs *out, uint64_t policy_seed,
                     int32_t *d_next_actions, void *stream);
 
+/* Rollout forms of gen_rollout. */
+#define GEN_ROLLOUT_RESIDENT 0 /* one launch; each game's state stays in shared memory for all K frames */
+#define GEN_ROLLOUT_GRAPH 1    /* K step launches replayed from a captured CUDA graph */
+#define GEN_ROLLOUT_LAUNCHES 2 /* K step launches issued one by one */
+
+/* K frames of every game, the benchmark policy choosing every action (see
+ * gen_step_policy).  Every array of `out` holds K consecutive frames: frame
+ * f of a per-player plane starts at f * plane_cells, of reward at
+ * f * player_slots, of scoreboard at 2 * f * player_slots, of done at
+ * f * n_games.  d_actions [player_slots]: in, the first frame's actions;
+ * out, the actions for the frame after the rollout.  d_action_log
+ * [K][player_slots] (may be NULL) receives the actions each frame consumed.
+ * All forms give identical results.  GEN_ROLLOUT_GRAPH captures on first use
+ * and replays while K, the seed and every buffer stay the same; its first
+ * call must not happen inside another stream capture. */
+int gen_rollout(gen_env *env, int K, uint64_t policy_seed, int32_t *d_actions, const gen_outputs *out,
+                int32_t *d_action_log, int form, void *stream);
+
 /* The benchmark policy alone, from the current state of every game. */
 int gen_policy(gen_env *env, uint64_t policy_seed, int32_t *d_actions, void *stream);
 
@@ -173,6 +191,17 @@ int gen_write_state(gen_env *env, const int16_t *h_army, const int8_t *h_owner, 
  * one of 1, 2, 4, 8 that fits the shared-memory limit.  Used by the
  * autotuner; results do not depend on it. */
 int gen_set_launch(gen_env *env, int warps_per_cta);
+
+/* Pick each size bucket's launch shape (games per CTA among 2, 4, 8) by
+ * timing `steps` step launches of a scratch batch with the bucket's board
+ * shapes (the environment's own games do not advance).  Results are cached
+ * per (padded board size class, player class, SM count) for the process.
+ * A one-line-per-bucket report goes to `report` when non-NULL.
+ * Synchronous.  Buckets: games are grouped by padded cells (<= 256, 512,
+ * 768, 1024, 1536, 2048, 3072, 4096) and players (<= 2, 4, 8); each bucket
+ * launches with its own shared-memory size, largest first, on forked
+ * streams. */
+int gen_autotune(gen_env *env, int steps, char *report, size_t report_cap);
 
 /* Measure copy bandwidth of this GPU with the library's own 128-bit copy
  * kernel over `bytes` (rounded down to 16 B), best of `reps`; returns GB/s

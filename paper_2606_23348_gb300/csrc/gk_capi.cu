@@ -1,12 +1,17 @@
 // C-ABI of libgenerals (declared in include/generals.h): argument checks,
-// device arenas, per-game layout, launches.  All game work runs in the
-// kernels of gk_kernels.cu; this file never computes a rule.
+// device arenas, per-game layout, size buckets, launches, rollouts (plain,
+// resident, CUDA graph) and the launch-shape autotuner.  All game work runs
+// in the kernels of gk_kernels.cu; this file never computes a rule.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "generals.h"
@@ -32,15 +37,32 @@ int cuda_fail(cudaError_t e, const char* what) {
     return fail(GEN_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(expr, what)                  \
-    do {                                      \
-        cudaError_t e_ = (expr);              \
+#define CUDA_TRY(expr, what)                               \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
 constexpr int kMaxSmemPerCta = 227 * 1024;
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// A group of games of similar size launched together with its own
+// shared-memory carve and launch shape.
+struct Bucket {
+    int offset = 0;   // first entry in the env's game order
+    int n = 0;        // games
+    int npad_max = 0;
+    int pmax = 0;
+    int nw_stride = 0;
+    int warp_smem = 0;
+    int warps = 8;    // games (warps) per CTA
+    int max_ctas = 0;
+};
+
+// process-wide cache of autotuned launch shapes: (cell class, player class, SMs) -> warps
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
 
 }  // namespace
 
@@ -54,9 +76,12 @@ struct gen_env {
     int pmax = 0;
     int npad_max = 0;
     int nmax = 0;
-    int nw_stride = 0;
-    int warp_smem = 0;
-    int warps_per_cta = 8;
+    Bucket all;                      // every game, largest carve (used for game-id lists)
+    std::vector<Bucket> buckets;     // size buckets covering every game once
+    int32_t* d_order = nullptr;      // games sorted by bucket (NULL: identity, one bucket)
+    std::vector<cudaStream_t> side;  // one per bucket beyond the first
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     GameInfo* d_info = nullptr;
     GameScalars* d_scal = nullptr;
     int16_t* d_army = nullptr;
@@ -66,12 +91,20 @@ struct gen_env {
     int32_t* d_actions = nullptr;
     gen_outputs d_out{};
     bool have_out = false;
+    // cached rollout graph
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> graph_key;
 };
 
 namespace {
 
 void free_env(gen_env* e) {
     if (!e) return;
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    for (auto s : e->side) cudaStreamDestroy(s);
+    for (auto v : e->join) cudaEventDestroy(v);
+    if (e->fork) cudaEventDestroy(e->fork);
+    cudaFree(e->d_order);
     cudaFree(e->d_info);
     cudaFree(e->d_scal);
     cudaFree(e->d_army);
@@ -102,7 +135,7 @@ int check_params(const gen_params* p) {
     return GEN_OK;
 }
 
-int check_outputs(const gen_env* e, const gen_outputs* o) {
+int check_outputs(const gen_outputs* o) {
     if (!o) return fail(GEN_ERR_BAD_ARG, "outputs is NULL");
     const void* ptrs[8] = {o->obs_army, o->obs_owner, o->obs_terrain, o->obs_vis,
                            o->mask,     o->reward,    o->scoreboard,  o->done};
@@ -110,16 +143,33 @@ int check_outputs(const gen_env* e, const gen_outputs* o) {
         if (!ptrs[i]) return fail(GEN_ERR_BAD_ARG, "output field %d is NULL", i);
         if (i < 5 && !aligned16(ptrs[i])) return fail(GEN_ERR_BAD_ARG, "output plane %d not 16-byte aligned", i);
     }
-    (void)e;
     return GEN_OK;
 }
 
-KArgs base_args(const gen_env* e, int op) {
+int choose_warps(int warp_smem) {
+    for (int w : {8, 4, 2, 1})
+        if (w * warp_smem <= kMaxSmemPerCta) return w;
+    return 0;
+}
+
+// fill a bucket's carve and launch shape; 0 or a GEN_ERR code
+int shape_bucket(Bucket& b) {
+    b.warp_smem = gk::warp_smem_bytes(b.npad_max, b.pmax, &b.nw_stride);
+    if (b.warps == 0 || b.warps * b.warp_smem > kMaxSmemPerCta) b.warps = choose_warps(b.warp_smem);
+    if (b.warps == 0)
+        return fail(GEN_ERR_BAD_ARG, "a %d-cell board needs %d bytes of shared memory per game", b.npad_max,
+                    b.warp_smem);
+    const int rc = gk::max_resident_ctas(b.warps, b.warps * b.warp_smem, &b.max_ctas);
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "occupancy query");
+    return GEN_OK;
+}
+
+KArgs base_args(const gen_env* e, const Bucket& b, int op) {
     KArgs a;
     memset(&a, 0, sizeof(a));
     a.info = e->d_info;
-    a.list = nullptr;
-    a.n_items = e->G;
+    a.list = (&b == &e->all || !e->d_order) ? nullptr : e->d_order + b.offset;
+    a.n_items = b.n;
     a.n_games = e->G;
     a.op = op;
     a.army = e->d_army;
@@ -133,10 +183,14 @@ KArgs base_args(const gen_env* e, int op) {
     a.city_span = e->prm.city_army_max - e->prm.city_army_min + 1;
     a.max_turns = e->prm.max_turns;
     a.auto_reset = e->prm.auto_reset;
-    a.npad_max = e->npad_max;
-    a.nw_stride = e->nw_stride;
-    a.pmax = e->pmax;
-    a.warp_smem = e->warp_smem;
+    a.frames = 1;
+    a.plane_stride = e->plane_cells;
+    a.slot_stride = e->player_slots;
+    a.game_stride = e->G;
+    a.npad_max = b.npad_max;
+    a.nw_stride = b.nw_stride;
+    a.pmax = b.pmax;
+    a.warp_smem = b.warp_smem;
     return a;
 }
 
@@ -152,9 +206,36 @@ void set_outputs(KArgs& a, const gen_outputs* o) {
     a.do_outputs = 1;
 }
 
-int launch(const gen_env* e, const KArgs& a, void* stream, const char* what) {
-    int rc = gk::launch_step(a, e->warps_per_cta, stream);
+int launch_one(const Bucket& b, const KArgs& a, void* stream, const char* what) {
+    const int rc = gk::launch_step(a, b.warps, b.max_ctas, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, what);
+    return GEN_OK;
+}
+
+// Every game, one launch per size bucket; buckets after the first run on
+// side streams forked from and joined back into `stream`.
+template <class Fill>
+int launch_buckets(gen_env* e, int op, Fill fill, void* stream, const char* what) {
+    const size_t nb = e->buckets.size();
+    if (nb == 1) {
+        KArgs a = base_args(e, e->buckets[0], op);
+        fill(a);
+        return launch_one(e->buckets[0], a, stream, what);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaEventRecord(e->fork, s), "fork record");
+    for (size_t i = 0; i < nb; ++i) {
+        cudaStream_t si = i == 0 ? s : e->side[i - 1];
+        if (i > 0) CUDA_TRY(cudaStreamWaitEvent(si, e->fork, 0), "fork wait");
+        KArgs a = base_args(e, e->buckets[i], op);
+        fill(a);
+        int rc = launch_one(e->buckets[i], a, si, what);
+        if (rc) return rc;
+        if (i > 0) {
+            CUDA_TRY(cudaEventRecord(e->join[i - 1], si), "join record");
+            CUDA_TRY(cudaStreamWaitEvent(s, e->join[i - 1], 0), "join wait");
+        }
+    }
     return GEN_OK;
 }
 
@@ -162,12 +243,6 @@ int players_for(int mode, int n_players) {
     if (mode == GEN_MODE_1V1) return 2;
     if (mode == GEN_MODE_2V2) return 4;
     return n_players;
-}
-
-int choose_warps(int warp_smem) {
-    for (int w : {8, 4, 2, 1})
-        if (w * warp_smem <= kMaxSmemPerCta) return w;
-    return 0;
 }
 
 int ensure_internal_outputs(gen_env* e) {
@@ -184,6 +259,59 @@ int ensure_internal_outputs(gen_env* e) {
     CUDA_TRY(cudaMalloc(&o.done, (size_t)e->G), "cudaMalloc done");
     CUDA_TRY(cudaMalloc(&e->d_actions, ps * 4), "cudaMalloc actions");
     e->have_out = true;
+    return GEN_OK;
+}
+
+// Size class of a game: padded cells rounded up to a class edge, players
+// rounded up to 2, 4 or 8.  Games of one class share a carve.
+int cell_class(int npad) {
+    for (int edge : {256, 512, 768, 1024, 1536, 2048, 3072, 4096})
+        if (npad <= edge) return edge;
+    return 4096;
+}
+int player_class(int P) { return P <= 2 ? 2 : (P <= 4 ? 4 : 8); }
+
+std::pair<int, int> game_class(const GameInfo& gi) { return std::make_pair(cell_class(gi.Npad), player_class(gi.P)); }
+
+int build_buckets(gen_env* e) {
+    std::vector<int> order((size_t)e->G);
+    for (int g = 0; g < e->G; ++g) order[(size_t)g] = g;
+    auto key = [&](int g) { return game_class(e->h_info[(size_t)g]); };
+    // largest class first (it finishes last), then game id
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) > key(y); });
+    e->buckets.clear();
+    for (int i = 0; i < e->G;) {
+        const auto k = key(order[(size_t)i]);
+        int j = i;
+        Bucket b;
+        b.offset = i;
+        while (j < e->G && key(order[(size_t)j]) == k) {
+            const GameInfo& gi = e->h_info[(size_t)order[(size_t)j]];
+            b.npad_max = std::max(b.npad_max, (int)gi.Npad);
+            b.pmax = std::max(b.pmax, (int)gi.P);
+            ++j;
+        }
+        b.n = j - i;
+        b.warps = 8;
+        int rc = shape_bucket(b);
+        if (rc) return rc;
+        e->buckets.push_back(b);
+        i = j;
+    }
+    if (e->buckets.size() > 1) {
+        CUDA_TRY(cudaMalloc(&e->d_order, sizeof(int32_t) * (size_t)e->G), "cudaMalloc order");
+        CUDA_TRY(cudaMemcpy(e->d_order, order.data(), sizeof(int32_t) * (size_t)e->G, cudaMemcpyHostToDevice),
+                 "upload order");
+        CUDA_TRY(cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming), "event");
+        for (size_t i = 1; i < e->buckets.size(); ++i) {
+            cudaStream_t s;
+            cudaEvent_t v;
+            CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+            e->side.push_back(s);
+            CUDA_TRY(cudaEventCreateWithFlags(&v, cudaEventDisableTiming), "event");
+            e->join.push_back(v);
+        }
+    }
     return GEN_OK;
 }
 
@@ -254,16 +382,21 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
         e->pmax = std::max(e->pmax, P);
         e->npad_max = std::max(e->npad_max, Npad);
         e->nmax = std::max(e->nmax, N);
-    }
-    if (cell > INT32_MAX) {
-        free_env(e);
-        return fail(GEN_ERR_BAD_ARG, "batch too large: %lld state cells", (long long)cell);
+        if (cell > INT32_MAX) {
+            free_env(e);
+            return fail(GEN_ERR_BAD_ARG, "batch too large: more than 2^31 state cells");
+        }
     }
     e->state_cells = cell;
     e->plane_cells = plane;
     e->player_slots = slot;
-    e->warp_smem = gk::warp_smem_bytes(e->npad_max, e->pmax, &e->nw_stride);
-    e->warps_per_cta = choose_warps(e->warp_smem);
+    e->all.n = batch;
+    e->all.npad_max = e->npad_max;
+    e->all.pmax = e->pmax;
+    if ((rc = shape_bucket(e->all)) != GEN_OK || (rc = build_buckets(e)) != GEN_OK) {
+        free_env(e);
+        return rc;
+    }
 
     cudaError_t ce;
     if ((ce = cudaMalloc(&e->d_info, sizeof(GameInfo) * (size_t)batch)) != cudaSuccess ||
@@ -281,8 +414,7 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
         free_env(e);
         return cuda_fail(ce, "upload game table");
     }
-    KArgs a = base_args(e, gk::OP_CREATE);
-    rc = launch(e, a, nullptr, "create launch");
+    rc = launch_buckets(e, gk::OP_CREATE, [](KArgs&) {}, nullptr, "create launch");
     if (rc == GEN_OK && (ce = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_fail(ce, "create kernel");
     if (rc) {
         free_env(e);
@@ -322,39 +454,39 @@ int gen_layout(const gen_env* e, gen_layout_info* info, int64_t* h_plane_off, in
 
 int gen_reset(gen_env* e, const int32_t* d_game_ids, int n, const gen_outputs* out, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    int rc = check_outputs(e, out);
+    int rc = check_outputs(out);
     if (rc) return rc;
-    KArgs a = base_args(e, gk::OP_RESET);
-    if (d_game_ids) {
-        if (n < 0 || n > e->G) return fail(GEN_ERR_BAD_ARG, "reset count %d outside [0, %d]", n, e->G);
-        a.list = d_game_ids;
-        a.n_items = n;
-    }
+    if (!d_game_ids)
+        return launch_buckets(e, gk::OP_RESET, [&](KArgs& a) { set_outputs(a, out); }, stream, "reset launch");
+    if (n < 0 || n > e->G) return fail(GEN_ERR_BAD_ARG, "reset count %d outside [0, %d]", n, e->G);
+    KArgs a = base_args(e, e->all, gk::OP_RESET);
+    a.list = d_game_ids;
+    a.n_items = n;
     set_outputs(a, out);
-    return launch(e, a, stream, "reset launch");
+    return launch_one(e->all, a, stream, "reset launch");
 }
 
 int gen_observe(gen_env* e, const gen_outputs* out, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    int rc = check_outputs(e, out);
+    int rc = check_outputs(out);
     if (rc) return rc;
-    KArgs a = base_args(e, gk::OP_OBSERVE);
-    set_outputs(a, out);
-    return launch(e, a, stream, "observe launch");
+    return launch_buckets(e, gk::OP_OBSERVE, [&](KArgs& a) { set_outputs(a, out); }, stream, "observe launch");
 }
 
 int gen_step_policy(gen_env* e, const int32_t* d_actions, const gen_outputs* out, uint64_t policy_seed,
                     int32_t* d_next_actions, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
-    int rc = check_outputs(e, out);
+    int rc = check_outputs(out);
     if (rc) return rc;
-    KArgs a = base_args(e, gk::OP_STEP);
-    a.actions = d_actions;
-    set_outputs(a, out);
-    a.next_actions = d_next_actions;
-    a.policy_seed = policy_seed;
-    return launch(e, a, stream, "step launch");
+    return launch_buckets(e, gk::OP_STEP,
+                          [&](KArgs& a) {
+                              a.actions = d_actions;
+                              set_outputs(a, out);
+                              a.next_actions = d_next_actions;
+                              a.policy_seed = policy_seed;
+                          },
+                          stream, "step launch");
 }
 
 int gen_step(gen_env* e, const int32_t* d_actions, const gen_outputs* out, void* stream) {
@@ -364,10 +496,99 @@ int gen_step(gen_env* e, const int32_t* d_actions, const gen_outputs* out, void*
 int gen_policy(gen_env* e, uint64_t policy_seed, int32_t* d_actions, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
-    KArgs a = base_args(e, gk::OP_POLICY);
-    a.next_actions = d_actions;
-    a.policy_seed = policy_seed;
-    return launch(e, a, stream, "policy launch");
+    return launch_buckets(e, gk::OP_POLICY,
+                          [&](KArgs& a) {
+                              a.next_actions = d_actions;
+                              a.policy_seed = policy_seed;
+                          },
+                          stream, "policy launch");
+}
+
+int gen_rollout(gen_env* e, int K, uint64_t policy_seed, int32_t* d_actions, const gen_outputs* out,
+                int32_t* d_action_log, int impl, void* stream) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (K < 1) return fail(GEN_ERR_BAD_ARG, "K = %d < 1", K);
+    if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
+    int rc = check_outputs(out);
+    if (rc) return rc;
+    if (impl == GEN_ROLLOUT_RESIDENT) {
+        return launch_buckets(e, gk::OP_STEP,
+                              [&](KArgs& a) {
+                                  a.actions = d_actions;
+                                  set_outputs(a, out);
+                                  a.next_actions = d_actions;
+                                  a.policy_seed = policy_seed;
+                                  a.frames = K;
+                                  a.action_log = d_action_log;
+                              },
+                              stream, "rollout launch");
+    }
+    if (impl != GEN_ROLLOUT_GRAPH && impl != GEN_ROLLOUT_LAUNCHES)
+        return fail(GEN_ERR_BAD_ARG, "unknown rollout form %d", impl);
+    // K single-frame launches; launch k writes frame k of every output
+    auto enqueue = [&](cudaStream_t s) -> int {
+        for (int k = 0; k < K; ++k) {
+            const int64_t pk = (int64_t)k * e->plane_cells, sk = (int64_t)k * e->player_slots;
+            int r = launch_buckets(e, gk::OP_STEP,
+                                   [&](KArgs& a) {
+                                       a.actions = d_actions;
+                                       set_outputs(a, out);
+                                       a.obs_army += pk;
+                                       a.obs_owner += pk;
+                                       a.obs_terrain += pk;
+                                       a.obs_vis += pk;
+                                       a.mask += pk;
+                                       a.reward += sk;
+                                       a.scoreboard += 2 * sk;
+                                       a.done += (int64_t)k * e->G;
+                                       a.next_actions = d_actions;
+                                       a.policy_seed = policy_seed;
+                                       a.action_log = d_action_log ? d_action_log + sk : nullptr;
+                                   },
+                                   s, "rollout launch");
+            if (r) return r;
+        }
+        return GEN_OK;
+    };
+    if (impl == GEN_ROLLOUT_LAUNCHES) return enqueue((cudaStream_t)stream);
+    // CUDA graph of the K launches, captured once per (K, buffers, seed)
+    const std::vector<const void*> key = {(const void*)(intptr_t)K, (const void*)(uintptr_t)policy_seed,
+                                          d_actions,                d_action_log,
+                                          out->obs_army,            out->obs_owner,
+                                          out->obs_terrain,         out->obs_vis,
+                                          out->mask,                out->reward,
+                                          out->scoreboard,          out->done};
+    if (!e->graph || e->graph_key != key) {
+        if (e->graph) {
+            cudaGraphExecDestroy(e->graph);
+            e->graph = nullptr;
+        }
+        cudaStream_t cap;
+        CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t gr = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            rc = enqueue(cap);
+            cudaError_t ce2 = cudaStreamEndCapture(cap, &gr);
+            if (rc == GEN_OK && ce2 != cudaSuccess) rc = cuda_fail(ce2, "end capture");
+        } else {
+            rc = cuda_fail(ce, "begin capture");
+        }
+        cudaStreamDestroy(cap);
+        if (rc) {
+            if (gr) cudaGraphDestroy(gr);
+            return rc;
+        }
+        ce = cudaGraphInstantiate(&e->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ce != cudaSuccess) {
+            e->graph = nullptr;
+            return cuda_fail(ce, "graph instantiate");
+        }
+        e->graph_key = key;
+    }
+    CUDA_TRY(cudaGraphLaunch(e->graph, (cudaStream_t)stream), "graph launch");
+    return GEN_OK;
 }
 
 int gen_step_host(gen_env* e, const int32_t* h_actions, const gen_outputs* h_out, uint64_t policy_seed,
@@ -446,8 +667,7 @@ int gen_write_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, co
     CUDA_TRY(cudaMemcpyAsync(e->d_terrain, h_terrain, n, cudaMemcpyHostToDevice, s), "write terrain");
     CUDA_TRY(cudaMemcpyAsync(e->d_scal, sc.data(), sizeof(GameScalars) * (size_t)e->G, cudaMemcpyHostToDevice, s),
              "write scalars");
-    KArgs a = base_args(e, gk::OP_DERIVE);
-    int rc = launch(e, a, stream, "derive launch");
+    int rc = launch_buckets(e, gk::OP_DERIVE, [](KArgs&) {}, stream, "derive launch");
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(s), "write_state sync");
     return GEN_OK;
@@ -457,10 +677,108 @@ int gen_set_launch(gen_env* e, int warps_per_cta) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)
         return fail(GEN_ERR_BAD_ARG, "warps_per_cta %d not in {1, 2, 4, 8}", warps_per_cta);
-    if (warps_per_cta * e->warp_smem > kMaxSmemPerCta)
-        return fail(GEN_ERR_BAD_ARG, "%d warps need %d bytes of shared memory", warps_per_cta,
-                    warps_per_cta * e->warp_smem);
-    e->warps_per_cta = warps_per_cta;
+    for (auto& b : e->buckets)
+        if (warps_per_cta * b.warp_smem > kMaxSmemPerCta)
+            return fail(GEN_ERR_BAD_ARG, "%d warps need %d bytes of shared memory", warps_per_cta,
+                        warps_per_cta * b.warp_smem);
+    for (auto& b : e->buckets) {
+        b.warps = warps_per_cta;
+        int rc = shape_bucket(b);
+        if (rc) return rc;
+    }
+    return GEN_OK;
+}
+
+int gen_autotune(gen_env* e, int steps, char* report, size_t report_cap) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (steps < 1) return fail(GEN_ERR_BAD_ARG, "steps < 1");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::string rep;
+    char line[256];
+    for (size_t bi = 0; bi < e->buckets.size(); ++bi) {
+        Bucket& b = e->buckets[bi];
+        const auto cls = std::make_pair(cell_class(b.npad_max), player_class(b.pmax));
+        const auto key = std::make_tuple(cls.first, cls.second, sms);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                b.warps = it->second;
+                int rc = shape_bucket(b);
+                if (rc) return rc;
+                snprintf(line, sizeof(line), "bucket %zu (%d games, <=%d cells, <=%d players): %d warps/CTA (cached)\n",
+                         bi, b.n, b.npad_max, b.pmax, b.warps);
+                rep += line;
+                continue;
+            }
+        }
+        // a scratch batch of this bucket's shapes: same parameters, its own state
+        std::vector<int32_t> hh, ww, mm, pp;
+        for (int g = 0; g < e->G; ++g) {
+            const GameInfo& gi = e->h_info[(size_t)g];
+            if (game_class(gi) != cls) continue;
+            hh.push_back(gi.H);
+            ww.push_back(gi.W);
+            mm.push_back(gi.mode);
+            pp.push_back(gi.P);
+        }
+        gen_env* t = nullptr;
+        int rc = gen_create_ex(&t, &e->prm, (int)hh.size(), hh.data(), ww.data(), mm.data(), pp.data());
+        if (rc) return rc;
+        rc = ensure_internal_outputs(t);
+        if (rc) {
+            free_env(t);
+            return rc;
+        }
+        cudaStream_t s;
+        cudaEvent_t t0, t1;
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        float best = 1e30f;
+        int best_w = b.warps;
+        std::string trials;
+        gen_policy(t, 1, t->d_actions, s);
+        for (int w : {2, 4, 8}) {
+            if (w * b.warp_smem > kMaxSmemPerCta) continue;
+            if (gen_set_launch(t, w) != GEN_OK) continue;
+            for (int k = 0; k < 3; ++k) gen_step_policy(t, t->d_actions, &t->d_out, 1, t->d_actions, s);
+            cudaEventRecord(t0, s);
+            for (int k = 0; k < steps; ++k) gen_step_policy(t, t->d_actions, &t->d_out, 1, t->d_actions, s);
+            cudaEventRecord(t1, s);
+            if (cudaEventSynchronize(t1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            snprintf(line, sizeof(line), " %dw=%.3fms", w, ms / steps);
+            trials += line;
+            if (ms < best) {
+                best = ms;
+                best_w = w;
+            }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        cudaStreamDestroy(s);
+        free_env(t);
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
+        b.warps = best_w;
+        if ((rc = shape_bucket(b)) != GEN_OK) return rc;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = best_w;
+        }
+        snprintf(line, sizeof(line), "bucket %zu (%d games, <=%d cells, <=%d players): %d warps/CTA;", bi, b.n,
+                 b.npad_max, b.pmax, best_w);
+        rep += line + trials + "\n";
+    }
+    if (report && report_cap) {
+        const size_t n = std::min(report_cap - 1, rep.size());
+        memcpy(report, rep.data(), n);
+        report[n] = 0;
+    }
     return GEN_OK;
 }
 

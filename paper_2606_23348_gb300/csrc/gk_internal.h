@@ -59,6 +59,12 @@ struct KArgs {
     int32_t* scoreboard;
     uint8_t* done;
     int32_t* next_actions;  // non-null: fused benchmark policy
+    // multi-frame rollouts: frame f writes its outputs at base + f * stride
+    int32_t frames;         // frames per launch (state stays in shared memory)
+    int64_t plane_stride;   // elements of one frame of a per-player plane
+    int32_t slot_stride;    // per-player slots of one frame (reward, actions log)
+    int32_t game_stride;    // games of one frame (done)
+    int32_t* action_log;    // optional [frames][slots]: actions each frame consumed
     uint64_t policy_seed;
     uint64_t seed;
     uint64_t game_id_base;
@@ -78,9 +84,13 @@ struct KArgs {
 // pmax players; also returns the bitset stride in words.
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride);
 
+// CTAs of the step kernel that fit on the whole GPU at once (raises the
+// kernel's shared-memory limit as a side effect).  Returns a cudaError_t.
+int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out);
+
 // Launch the step kernel with `warps_per_cta` games per CTA on `stream`.
 // Returns a cudaError_t value.
-int launch_step(const KArgs& a, int warps_per_cta, void* stream);
+int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream);
 
 // 128-bit copy kernel used to measure the HBM roofline denominator.
 int launch_copy(const void* src, void* dst, size_t n16, int blocks, void* stream);

@@ -491,7 +491,8 @@ __device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x0020
 // ---- observation + mask chunks of 16 cells (Sec. IV-B, App. A, Sec. IV-G) --
 // WRITE: store the planes; COUNT: legal (cell, direction) pairs per chunk.
 template <bool WRITE, bool COUNT>
-__device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished, int lane) {
+__device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished, int lane,
+                            int64_t frame_off) {
     const int nch = g.nch, st = s.stride, P = g.P;
     int p = 0, ch = lane;
     while (p < P && ch >= nch) {
@@ -536,7 +537,7 @@ __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32
                 oa[2 * k] = aw[2 * k] & __byte_perm(bm, 0, 0x1100);
                 oa[2 * k + 1] = aw[2 * k + 1] & __byte_perm(bm, 0, 0x3322);
             }
-            const int64_t off = g.plane_off + (int64_t)p * g.Npad + c0;
+            const int64_t off = frame_off + g.plane_off + (int64_t)p * g.Npad + c0;
             uint4* pa = reinterpret_cast<uint4*>(a.obs_army + off);
             __stcs(pa, make_uint4(oa[0], oa[1], oa[2], oa[3]));
             __stcs(pa + 1, make_uint4(oa[4], oa[5], oa[6], oa[7]));
@@ -565,8 +566,11 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 
 // ---- benchmark policy: uniform legal (cell, direction), split p = 0.2 -------
 // Needs the chunk counts of output_pass<*, true>.
-__device__ void policy_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished,
-                            uint32_t frame, uint64_t gid, int lane) {
+// Returns, on lane p < P, player p's action; DIRECT also stores it.
+template <bool DIRECT>
+__device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished,
+                               uint32_t frame, uint64_t gid, int lane) {
+    int32_t mine_action = 0;
     const int nch = g.nch;
     const int cpl = (nch + 31) >> 5;  // consecutive chunks per lane
     const int c_lo = lane * cpl;
@@ -618,8 +622,13 @@ __device__ void policy_pass(const KArgs& a, const Game& g, const Smem& s, uint32
             }
             action = __shfl_sync(kFull, found, B);
         }
-        if (lane == 0) a.next_actions[g.player_off + p] = action;
+        if (DIRECT) {
+            if (lane == 0) a.next_actions[g.player_off + p] = action;
+        } else if (lane == p) {
+            mine_action = action;
+        }
     }
+    return mine_action;
 }
 
 __device__ __forceinline__ void load_board(const KArgs& a, const Game& g, const Smem& s, int lane) {
@@ -655,16 +664,11 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
-    extern __shared__ __align__(16) char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int item = blockIdx.x * (blockDim.x >> 5) + wid;
-    if (item >= a.n_items) return;
-    const int gidx = a.list ? a.list[item] : item;
-    if (gidx < 0 || gidx >= a.n_games) return;
+namespace {
+
+template <bool MULTI>
+__device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const int gidx, const int lane) {
     const Game g = load_game(a.info + gidx);
-    const Smem s = carve(smem_raw + wid * a.warp_smem, a);
     const uint64_t gid = a.game_id_base + (uint64_t)gidx;
     GameScalars* sc = a.scal + gidx;
 
@@ -683,8 +687,6 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
     }
     const uint32_t all_alive = (1u << g.P) - 1u;
     bool wrote_state = false;
-    float my_reward = 0.0f;
-    uint32_t done = 0;
 
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
@@ -692,16 +694,25 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
         turn = 0;
         alive = all_alive;
         finished = 0;
-        saturated += cell_pass(g, s, false, false, lane);
         wrote_state = true;
     } else {
         load_board(a, g, s, lane);
         if (a.op == OP_DERIVE) {
             derive_passable(g, s, lane);
             wrote_state = true;
-        } else if (a.op == OP_STEP && !finished) {
+        }
+    }
+
+    // player `lane`'s action for the next step (frame 0: from the caller)
+    int32_t my_act = (a.op == OP_STEP && lane < g.P) ? a.actions[g.player_off + lane] : 0;
+    const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
+    for (int f = 0; f < frames; ++f) {
+        float my_reward = 0.0f;
+        uint32_t done = 0;
+        if (a.op == OP_STEP && !finished) {
+            if (MULTI && a.action_log && lane < g.P)
+                a.action_log[(int64_t)f * a.slot_stride + g.player_off + lane] = my_act;
             // moves in rotating priority, each checked when it runs (Q1)
-            const int32_t my_act = (lane < g.P) ? a.actions[g.player_off + lane] : 0;
             uint32_t eliminated = 0;
             uint32_t inv0 = 0, sat0 = 0;
             for (int k = 0; k < g.P; ++k) {
@@ -759,29 +770,33 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
             }
             wrote_state = true;
         } else {
-            cell_pass(g, s, false, false, lane);  // observe, policy, or a frozen game
+            // create, reset, observe, policy, or a frozen game
+            saturated += cell_pass(g, s, false, false, lane);
         }
         if (a.op == OP_STEP) frame += 1;
-    }
 
-    const bool fin = finished != 0;
-    if (a.do_outputs) {
-        column_pass(g, s, lane);
-        fog_pass(g, s, alive, lane);
-        if (a.next_actions)
-            output_pass<true, true>(a, g, s, alive, fin, lane);
-        else
-            output_pass<true, false>(a, g, s, alive, fin, lane);
-        if (lane < g.P) {
-            a.reward[g.player_off + lane] = my_reward;
-            a.scoreboard[2 * (g.player_off + lane) + 0] = s.misc[8 + lane];
-            a.scoreboard[2 * (g.player_off + lane) + 1] = s.misc[16 + lane];
+        const bool fin = finished != 0;
+        if (a.do_outputs) {
+            const int64_t poff = (int64_t)f * a.plane_stride;
+            const int64_t soff = (int64_t)f * a.slot_stride;
+            column_pass(g, s, lane);
+            fog_pass(g, s, alive, lane);
+            if (a.next_actions)
+                output_pass<true, true>(a, g, s, alive, fin, lane, poff);
+            else
+                output_pass<true, false>(a, g, s, alive, fin, lane, poff);
+            if (lane < g.P) {
+                a.reward[soff + g.player_off + lane] = my_reward;
+                a.scoreboard[2 * (soff + g.player_off + lane) + 0] = s.misc[8 + lane];
+                a.scoreboard[2 * (soff + g.player_off + lane) + 1] = s.misc[16 + lane];
+            }
+            if (lane == 0) a.done[(int64_t)f * a.game_stride + gidx] = (uint8_t)done;
+        } else if (a.next_actions) {
+            output_pass<false, true>(a, g, s, alive, fin, lane, 0);
         }
-        if (lane == 0) a.done[gidx] = (uint8_t)done;
-    } else if (a.next_actions) {
-        output_pass<false, true>(a, g, s, alive, fin, lane);
+        if (a.next_actions) my_act = policy_pass<!MULTI>(a, g, s, alive, fin, frame, gid, lane);
     }
-    if (a.next_actions) policy_pass(a, g, s, alive, fin, frame, gid, lane);
+    if (MULTI && a.next_actions && lane < g.P) a.next_actions[g.player_off + lane] = my_act;
     if (wrote_state) {
         __syncwarp();
         store_board(a, g, s, lane);
@@ -790,6 +805,34 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
         uint4* dst = reinterpret_cast<uint4*>(sc);
         dst[0] = make_uint4(turn, frame, epoch, alive);
         dst[1] = make_uint4(finished, invalid, saturated, a.op == OP_CREATE ? 0u : err);
+    }
+}
+
+
+}  // namespace
+
+// One warp per game; warps walk the item list with a grid stride.  MULTI:
+// several frames per launch (rollouts) with the board kept in shared memory.
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
+    extern __shared__ __align__(16) char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const Smem s = carve(smem_raw + wid * a.warp_smem, a);
+    if (!MULTI) {  // the grid covers every item
+        const int item = blockIdx.x * wpc + wid;
+        if (item >= a.n_items) return;
+        const int gidx = a.list ? a.list[item] : item;
+        if (gidx < 0 || gidx >= a.n_games) return;
+        run_game<MULTI>(a, s, gidx, lane);
+        return;
+    }
+    for (int item = blockIdx.x * wpc + wid; item < a.n_items; item += gridDim.x * wpc) {
+        const int gidx = a.list ? a.list[item] : item;
+        if (gidx < 0 || gidx >= a.n_games) continue;
+        __syncwarp();
+        run_game<MULTI>(a, s, gidx, lane);
     }
 }
 
@@ -808,17 +851,37 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
     return 4 * npad_max + 4 * nw * (2 * pmax + 4) + 4 * cnt_pad + 4 * 24;
 }
 
-int launch_step(const KArgs& a, int warps_per_cta, void* stream) {
+int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
+    static int configured = 48 * 1024;  // only ever raised, so every env's launches stay legal
+    cudaError_t e = cudaSuccess;
+    if (smem_bytes > configured) {
+        e = cudaFuncSetAttribute(k_generals<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_generals<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return (int)e;
+        configured = smem_bytes;
+    }
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false>, 32 * warps_per_cta,
+                                                           smem_bytes)) != cudaSuccess)
+        return (int)e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *out = per_sm * sms;
+    return 0;
+}
+
+int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     if (a.n_items <= 0) return 0;
     const int smem = a.warp_smem * warps_per_cta;
-    static int configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_generals, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return (int)e;
-        configured = smem;
-    }
-    const int blocks = (a.n_items + warps_per_cta - 1) / warps_per_cta;
-    k_generals<<<blocks, 32 * warps_per_cta, smem, (cudaStream_t)stream>>>(a);
+    int blocks = (a.n_items + warps_per_cta - 1) / warps_per_cta;
+    const bool multi = a.frames > 1 || a.action_log;
+    // multi-frame launches: a grid of many waves, warps stride over any items beyond it
+    if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
+    if (multi)
+        k_generals<true><<<blocks, 32 * warps_per_cta, smem, (cudaStream_t)stream>>>(a);
+    else
+        k_generals<false><<<blocks, 32 * warps_per_cta, smem, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 

@@ -53,8 +53,10 @@ class GenLayoutInfo(C.Structure):
 
 
 EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "gen_reset", "gen_observe",
-           "gen_step", "gen_step_policy", "gen_policy", "gen_step_host", "gen_read_state", "gen_write_state",
-           "gen_set_launch", "gen_copy_peak", "gen_last_error", "gen_destroy")
+           "gen_step", "gen_step_policy", "gen_policy", "gen_rollout", "gen_step_host", "gen_read_state",
+           "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy")
+
+ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
 
 def load_library(path: str = LIB_PATH):
@@ -78,6 +80,8 @@ def load_library(path: str = LIB_PATH):
             "gen_step": (C.c_int, [vp, vp, C.POINTER(GenOutputs), vp]),
             "gen_step_policy": (C.c_int, [vp, vp, C.POINTER(GenOutputs), u64, vp, vp]),
             "gen_policy": (C.c_int, [vp, u64, vp, vp]),
+            "gen_rollout": (C.c_int, [vp, C.c_int, u64, vp, C.POINTER(GenOutputs), vp, C.c_int, vp]),
+            "gen_autotune": (C.c_int, [vp, C.c_int, C.c_char_p, C.c_size_t]),
             "gen_step_host": (C.c_int, [vp, vp, C.POINTER(GenOutputs), u64, vp, vp]),
             "gen_read_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "gen_write_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -124,11 +128,13 @@ def _cur_stream():
 
 
 class Outputs:
-    """Device output tensors of one environment (torch, on cuda)."""
+    """Device output tensors of one environment (torch, on cuda); `frames`
+    consecutive frames for rollouts."""
 
-    def __init__(self, layout: GenLayoutInfo, device="cuda", pin_host: bool = False):
+    def __init__(self, layout: GenLayoutInfo, device="cuda", pin_host: bool = False, frames: int = 1):
         import torch
-        pc, ps, G = int(layout.plane_cells), int(layout.player_slots), int(layout.n_games)
+        pc, ps, G = (int(layout.plane_cells) * frames, int(layout.player_slots) * frames,
+                     int(layout.n_games) * frames)
         kw = dict(device=device) if not pin_host else dict(pin_memory=True)
         self.obs_army = torch.empty(pc, dtype=torch.int16, **kw)
         self.obs_owner = torch.empty(pc, dtype=torch.int8, **kw)
@@ -196,8 +202,8 @@ class GeneralsEnv:
             pass
 
     # ---- buffers --------------------------------------------------------
-    def new_outputs(self) -> Outputs:
-        return Outputs(self.layout)
+    def new_outputs(self, frames: int = 1) -> Outputs:
+        return Outputs(self.layout, frames=frames)
 
     def new_actions(self):
         import torch
@@ -226,6 +232,17 @@ class GeneralsEnv:
     def policy(self, policy_seed: int, actions, stream=None):
         _check(self.lib.gen_policy(self.h, int(policy_seed), C.c_void_p(actions.data_ptr()),
                                    stream or _cur_stream()), "gen_policy")
+
+    def rollout(self, K: int, policy_seed: int, actions, out: Outputs, action_log=None, form: int = 0,
+                stream=None):
+        log = C.c_void_p(action_log.data_ptr()) if action_log is not None else None
+        _check(self.lib.gen_rollout(self.h, int(K), int(policy_seed), C.c_void_p(actions.data_ptr()),
+                                    C.byref(out.struct), log, int(form), stream or _cur_stream()), "gen_rollout")
+
+    def autotune(self, steps: int = 5) -> str:
+        buf = C.create_string_buffer(4096)
+        _check(self.lib.gen_autotune(self.h, int(steps), buf, 4096), "gen_autotune")
+        return buf.value.decode()
 
     def step_host(self, h_actions, h_out: Outputs, policy_seed: int = 0, h_next_actions=None, stream=None):
         """Host-buffer step: h_actions, h_out (and h_next_actions) are CPU (pinned) tensors."""

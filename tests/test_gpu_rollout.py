@@ -1,0 +1,106 @@
+"""Multi-frame rollouts (resident, CUDA graph, plain launches) vs the oracle,
+and size-bucketed ragged batches, bit-exact frame by frame."""
+import types
+
+import numpy as np
+import pytest
+
+from gpu_helpers import PLANES, compare_frame, oracle_actions_flat
+from oracle import OracleEnv
+from paper_2606_23348_gb300.workloads import shapes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2606_23348_gb300.build import build_library
+    build_library()
+
+
+def frame_view(env, out, k):
+    """Frame k of a multi-frame Outputs as a one-frame object."""
+    pc, ps, G = int(env.layout.plane_cells), int(env.layout.player_slots), env.G
+    v = types.SimpleNamespace()
+    for name in PLANES:
+        setattr(v, name, getattr(out, name)[k * pc:(k + 1) * pc])
+    v.reward = out.reward[k * ps:(k + 1) * ps]
+    v.scoreboard = out.scoreboard[k * ps:(k + 1) * ps]
+    v.done = out.done[k * G:(k + 1) * G]
+    return v
+
+
+def make_pair(G=48, seed=3):
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    H, W, mode, P = shapes(G, (4, 20), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=seed)
+    P = np.where(mode == 2, np.minimum(P, H * W), P).astype(np.int32)
+    kw = dict(seed=seed, min_general_dist=1, n_cities=2, max_turns=40)
+    return GeneralsEnv(H, W, mode, P, **kw), OracleEnv(H, W, mode, P, **kw)
+
+
+@pytest.mark.parametrize("form", [0, 1, 2], ids=["resident", "graph", "launches"])
+def test_rollout_matches_oracle(form):
+    import torch
+    env, orc = make_pair()
+    assert len(set(zip(env.npad // 256, env.P))) > 1  # several size buckets
+    K = 9
+    out = env.new_outputs(frames=K)
+    acts = env.new_actions()
+    log = torch.zeros(K * int(env.layout.player_slots), dtype=torch.int32, device="cuda")
+    env.policy(5, acts)
+    for rep in range(3):  # the graph form replays from the second call on
+        env.rollout(K, 5, acts, out, log, form)
+        torch.cuda.synchronize()
+        logs = log.cpu().numpy().reshape(K, -1)
+        for k in range(K):
+            a = orc.policy(5)
+            np.testing.assert_array_equal(logs[k], oracle_actions_flat(env, a), err_msg=f"rep {rep} frame {k}")
+            orc.step(a)
+            if k < K - 1:
+                # state is only comparable at the end; outputs every frame
+                from gpu_helpers import oracle_flat_outputs
+                flat = oracle_flat_outputs(env, orc)
+                fv = frame_view(env, out, k)
+                for name in PLANES:
+                    np.testing.assert_array_equal(getattr(fv, name).cpu().numpy(), flat[name],
+                                                  err_msg=f"rep {rep} frame {k} {name}")
+        compare_frame(env, frame_view(env, out, K - 1), orc, f"rep {rep} last frame")
+        np.testing.assert_array_equal(acts.cpu().numpy(), oracle_actions_flat(env, orc.policy(5)))
+
+
+def test_rollout_forms_agree_on_full_workload_slice():
+    """The three forms give identical bytes on a ragged 15..30 batch."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    H, W, mode, P = shapes(4096, (15, 30), seed=7)
+    res = []
+    for form in (0, 1, 2):
+        env = GeneralsEnv(H, W, mode, P, seed=7, n_cities=-1, city_per_mille=20)
+        out = env.new_outputs(frames=4)
+        acts = env.new_actions()
+        env.policy(9, acts)
+        env.rollout(4, 9, acts, out, None, form)
+        env.rollout(4, 9, acts, out, None, form)
+        torch.cuda.synchronize()
+        res.append([t.cpu().numpy().copy() for t in out.tensors()] + [acts.cpu().numpy().copy()])
+    for other in res[1:]:
+        for x, y in zip(res[0], other):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_autotune_keeps_results():
+    import torch
+    env, orc = make_pair(G=40, seed=11)
+    rep = env.autotune(steps=2)
+    assert "bucket" in rep
+    out = env.new_outputs()
+    acts = env.new_actions()
+    env.policy(3, acts)
+    for f in range(10):
+        a = orc.policy(3)
+        env.step_policy(acts, out, 3, acts)
+        orc.step(a)
+    compare_frame(env, out, orc, "after autotune")
