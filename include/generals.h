@@ -174,6 +174,29 @@ int gen_policy(gen_env *env, uint64_t policy_seed, int32_t *d_actions, void *str
 int gen_step_host(gen_env *env, const int32_t *h_actions, const gen_outputs *h_out, uint64_t policy_seed,
                   int32_t *h_next_actions, void *stream);
 
+/* gen_step_host for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is an interface addition.  gen_step_host stages
+ * the actions and one frame of outputs in device buffers it cudaMallocs on
+ * its first call; some callers cannot allow that: an actor process whose
+ * device memory is already handed to a fixed-size pool, or a real-time loop
+ * that must not take cudaMalloc's implicit device synchronisation or risk an
+ * out-of-memory failure mid-rollout.  This entry point allocates nothing: it
+ * stages through a static device array of 32 MiB that every GPU loading the
+ * library holds until the process exits, with the same arguments, results
+ * and synchronisation as gen_step_host.
+ *  - A batch whose staging (actions, five planes, reward, scoreboard, done,
+ *    each rounded up to 256 bytes) exceeds 32 MiB is rejected with
+ *    GEN_ERR_BAD_ARG; use gen_step_host for it.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call, from any environment, shares the one array: calls whose
+ *    device work overlaps (other threads, other streams) race and must be
+ *    serialised by the caller.  Each call overwrites every staged byte it
+ *    reads, so no state carries over between calls. */
+int gen_step_host_static(gen_env *env, const int32_t *h_actions, const gen_outputs *h_out, uint64_t policy_seed,
+                         int32_t *h_next_actions, void *stream);
+
 /* Copy the whole game state to host memory: h_army [state_cells] int16,
  * h_owner / h_terrain [state_cells] int8 (game g at its state offset,
  * sum of Npad of earlier games), h_scalars [n_games][8] uint32 = turn,

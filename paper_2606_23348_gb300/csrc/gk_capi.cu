@@ -620,6 +620,97 @@ int gen_step_host(gen_env* e, const int32_t* h_actions, const gen_outputs* h_out
     return GEN_OK;
 }
 
+}  // extern "C"
+
+// ---- host-buffer step that allocates nothing --------------------------------
+// gen_step_host stages actions and outputs in device buffers it allocates on
+// its first call.  gen_step_host_static stages them instead in this
+// file-scope array, reserved when the library is loaded on a GPU and held by
+// every GPU that loads it until the process exits.  Host code must not use
+// the symbol as an address: the per-device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+namespace {
+
+constexpr size_t kStaticStageBytes = size_t(32) << 20;  // 32 MiB
+__device__ __align__(256) unsigned char g_static_stage[kStaticStageBytes];
+
+constexpr int kMaxStageDevices = 64;
+std::mutex g_stage_mu;
+unsigned char* g_stage_addr[kMaxStageDevices] = {};
+
+int static_stage(unsigned char** out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxStageDevices) return fail(GEN_ERR_BAD_ARG, "device %d beyond %d", dev, kMaxStageDevices);
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (!g_stage_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t ce = cudaGetSymbolAddress(&p, g_static_stage);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetSymbolAddress(static stage)");
+        g_stage_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_stage_addr[dev];
+    return GEN_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+int gen_step_host_static(gen_env* e, const int32_t* h_actions, const gen_outputs* h_out, uint64_t policy_seed,
+                         int32_t* h_next_actions, void* stream) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (!h_actions || !h_out) return fail(GEN_ERR_BAD_ARG, "host buffers are NULL");
+    const size_t pc = (size_t)e->plane_cells, ps = (size_t)e->player_slots, G = (size_t)e->G;
+    // stage layout: actions, five planes, reward, scoreboard, done (256-byte aligned each)
+    size_t off[9];
+    const size_t sizes[9] = {ps * 4, pc * 2, pc, pc, pc, pc, ps * 4, ps * 8, G};
+    size_t total = 0;
+    for (int i = 0; i < 9; ++i) {
+        off[i] = total;
+        total += align256(sizes[i]);
+    }
+    if (total > kStaticStageBytes)
+        return fail(GEN_ERR_BAD_ARG,
+                    "batch needs %zu bytes of staging; gen_step_host_static holds at most %zu (use gen_step_host)",
+                    total, kStaticStageBytes);
+    unsigned char* base = nullptr;
+    int rc = static_stage(&base);
+    if (rc) return rc;
+    int32_t* d_act = reinterpret_cast<int32_t*>(base + off[0]);
+    gen_outputs d;
+    d.obs_army = reinterpret_cast<int16_t*>(base + off[1]);
+    d.obs_owner = reinterpret_cast<int8_t*>(base + off[2]);
+    d.obs_terrain = reinterpret_cast<int8_t*>(base + off[3]);
+    d.obs_vis = base + off[4];
+    d.mask = base + off[5];
+    d.reward = reinterpret_cast<float*>(base + off[6]);
+    d.scoreboard = reinterpret_cast<int32_t*>(base + off[7]);
+    d.done = base + off[8];
+    // every staged byte the step reads is copied in first and every output it
+    // returns is written by the step, so nothing needs clearing between calls
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(d_act, h_actions, ps * 4, cudaMemcpyHostToDevice, s), "copy actions in");
+    rc = gen_step_policy(e, d_act, &d, policy_seed, h_next_actions ? d_act : nullptr, stream);
+    if (rc) return rc;
+    if (h_next_actions) CUDA_TRY(cudaMemcpyAsync(h_next_actions, d_act, ps * 4, cudaMemcpyDeviceToHost, s), "copy out");
+    const gen_outputs& h = *h_out;
+    if (h.obs_army) CUDA_TRY(cudaMemcpyAsync(h.obs_army, d.obs_army, pc * 2, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.obs_owner) CUDA_TRY(cudaMemcpyAsync(h.obs_owner, d.obs_owner, pc, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.obs_terrain)
+        CUDA_TRY(cudaMemcpyAsync(h.obs_terrain, d.obs_terrain, pc, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.obs_vis) CUDA_TRY(cudaMemcpyAsync(h.obs_vis, d.obs_vis, pc, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.mask) CUDA_TRY(cudaMemcpyAsync(h.mask, d.mask, pc, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.reward) CUDA_TRY(cudaMemcpyAsync(h.reward, d.reward, ps * 4, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.scoreboard)
+        CUDA_TRY(cudaMemcpyAsync(h.scoreboard, d.scoreboard, ps * 8, cudaMemcpyDeviceToHost, s), "copy out");
+    if (h.done) CUDA_TRY(cudaMemcpyAsync(h.done, d.done, G, cudaMemcpyDeviceToHost, s), "copy out");
+    CUDA_TRY(cudaStreamSynchronize(s), "step_host_static sync");
+    return GEN_OK;
+}
+
 int gen_read_state(gen_env* e, int16_t* h_army, int8_t* h_owner, int8_t* h_terrain, uint32_t* h_scalars,
                    void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");

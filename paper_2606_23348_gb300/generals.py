@@ -54,7 +54,8 @@ class GenLayoutInfo(C.Structure):
 
 EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "gen_reset", "gen_observe",
            "gen_step", "gen_step_policy", "gen_policy", "gen_rollout", "gen_step_host", "gen_read_state",
-           "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy")
+           "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
+           "gen_step_host_static")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH):
             "gen_rollout": (C.c_int, [vp, C.c_int, u64, vp, C.POINTER(GenOutputs), vp, C.c_int, vp]),
             "gen_autotune": (C.c_int, [vp, C.c_int, C.c_char_p, C.c_size_t]),
             "gen_step_host": (C.c_int, [vp, vp, C.POINTER(GenOutputs), u64, vp, vp]),
+            "gen_step_host_static": (C.c_int, [vp, vp, C.POINTER(GenOutputs), u64, vp, vp]),
             "gen_read_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "gen_write_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "gen_set_launch": (C.c_int, [vp, C.c_int]),
@@ -249,6 +251,14 @@ class GeneralsEnv:
         nxt = C.c_void_p(h_next_actions.data_ptr()) if h_next_actions is not None else None
         _check(self.lib.gen_step_host(self.h, C.c_void_p(h_actions.data_ptr()), C.byref(h_out.struct),
                                       int(policy_seed), nxt, stream or _cur_stream()), "gen_step_host")
+
+    def step_host_static(self, h_actions, h_out: Outputs, policy_seed: int = 0, h_next_actions=None,
+                         stream=None):
+        """step_host staged through the library's static device array (no device allocation)."""
+        nxt = C.c_void_p(h_next_actions.data_ptr()) if h_next_actions is not None else None
+        _check(self.lib.gen_step_host_static(self.h, C.c_void_p(h_actions.data_ptr()), C.byref(h_out.struct),
+                                             int(policy_seed), nxt, stream or _cur_stream()),
+               "gen_step_host_static")
 
     def set_launch(self, warps_per_cta: int):
         _check(self.lib.gen_set_launch(self.h, int(warps_per_cta)), "gen_set_launch")
