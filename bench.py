@@ -406,6 +406,61 @@ def run_rollout_workload(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_served(args, rank, world, local):
+    """256 closed-loop actor clients (exponential think time, mean 2 ms), each
+    holding 64..1024 mixed games with sides 15..40, opening and closing
+    sessions continuously, against an 80 GB admission budget; then the plain
+    bucketed step kernel on a batch of the same shapes."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.server import simulate
+    from paper_2606_23348_gb300.workloads import MOUNTAIN_THRESH_20PCT, shapes
+
+    torch.cuda.set_device(local)
+    params = dict(seed=MAP_SEED, mountain_thresh=MOUNTAIN_THRESH_20PCT, n_cities=-1, city_per_mille=30,
+                  city_army_min=40, city_army_max=50, min_general_dist=0)
+    sim = dict(clients=256, mean_interarrival_ms=2.0, min_games=64, max_games=1024, min_side=15, max_side=40,
+               frac_1v1=0.4, frac_2v2=0.3, min_steps=20, max_steps=200, seconds=args.served_seconds,
+               seed=11, policy_seed=POLICY_SEED, budget_bytes=80 << 30)
+    res = {}
+    for mode_name, host, copy in (("device_outputs", 0, 0), ("host_outputs", 1, 1)):
+        res[mode_name] = simulate(params, host_outputs=host, copy_outputs=copy, **sim)
+    # the plain fixed-size kernel on a batch with the same shape distribution
+    G = 256 * 544
+    H, W, mode, P = shapes(G, (15, 40), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=11)
+    env = GeneralsEnv(H, W, mode, P, **params)
+    out = env.new_outputs()
+    acts = env.new_actions()
+    env.policy(POLICY_SEED, acts)
+    for _ in range(args.warmup):
+        env.step_policy(acts, out, POLICY_SEED, acts)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    n = max(10, min(args.steps, 100))
+    for _ in range(n):
+        env.step_policy(acts, out, POLICY_SEED, acts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    plain = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "games": G}
+    dev = res["device_outputs"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": dev["frames_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": int(dev["requests"]), "warmup": args.warmup, "ms_per_step": dev["lat_mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
+            "data": "synthetic (simulated actor clients, seeded maps, random legal policy)",
+            "config": {"workload": "served-256-clients", **{k: v for k, v in sim.items() if k != "budget_bytes"},
+                       "budget_gb": 80},
+            "served": res, "plain_fixed_size_kernel": plain,
+            "latency_ms": {"p50": dev["lat_p50_ms"], "p99": dev["lat_p99_ms"]},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def len_buckets(env) -> int:
     """Size buckets of the batch (one launch each per frame)."""
     cls = set()
@@ -430,6 +485,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="workload name (paper_2606_23348_gb300.workloads)")
     ap.add_argument("--rollout", type=int, default=64, help="frames per rollout (ragged / mixed workloads)")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes first")
+    ap.add_argument("--served-seconds", type=float, default=10.0, help="measured window of the served workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
@@ -442,6 +498,8 @@ def main():
         barrier(world)
         if args.workload == WORKLOAD:
             run_ours(args, rank, world, local)
+        elif args.workload == "served-256-clients":
+            run_served(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

@@ -231,6 +231,90 @@ int gen_autotune(gen_env *env, int steps, char *report, size_t report_cap);
  * counting read + write bytes in *gbps.  Synchronous. */
 int gen_copy_peak(size_t bytes, int reps, double *gbps);
 
+/* ---- env server: continuous batching of many clients' steps ------------
+ * The games of every client session stay on the device.  A scheduler
+ * thread folds all step requests waiting at a given moment into one tick
+ * (one set of size-bucketed step launches over all their games, with the
+ * benchmark policy fused); up to two ticks are in flight on separate
+ * streams, so requests that arrive while one runs start on the device before
+ * it ends.  Sessions are admitted while the device bytes they need fit the
+ * budget; otherwise gen_server_open waits for others to close.  Each game is
+ * keyed by the global game id its session was opened with, so its results
+ * do not depend on the other sessions.  Section IV rules throughout. */
+typedef struct gen_server gen_server;
+
+typedef struct gen_server_config {
+    size_t budget_bytes;     /* device bytes sessions may hold (state; outputs too when on the device) */
+    int64_t max_games;       /* game slots */
+    int64_t max_cells;       /* board cells (padded to 16 per game) over all open sessions */
+    int64_t max_plane_cells; /* per-player output cells over all open sessions */
+    int32_t host_outputs;    /* 1: outputs in mapped pinned host memory (host clients); 0: device memory */
+    uint64_t policy_seed;    /* benchmark policy seed of every session */
+} gen_server_config;
+
+typedef struct gen_server_stats {
+    uint64_t requests, frames, ticks;
+    uint64_t sessions_open, sessions_admitted, sessions_waited;
+    double seconds;          /* since creation or the last reset */
+    double frames_per_s;     /* games stepped per second */
+    double lat_p50_ms, lat_p99_ms, lat_mean_ms; /* submit to result in the caller's buffers */
+    double tick_games_mean;  /* games per tick */
+    double bytes_in_use, budget;
+} gen_server_stats;
+
+/* Allocates the arenas for the configured capacities (device memory, and
+ * pinned host memory in host-output mode) and starts the scheduler thread. */
+int gen_server_create(gen_server **out, const gen_params *p, const gen_server_config *cfg);
+
+/* Admit a session of n games (per-game host arrays as gen_create_ex), keyed
+ * by global ids game_id_base + i; waits up to wait_ms for room.  Generates
+ * the games (epoch 0).  h_first_actions [the session's player slots] (may be
+ * NULL) receives the policy's actions for the first step.  GEN_ERR_OOM when
+ * there is no room in time. */
+int gen_server_open(gen_server *sv, int n, const int32_t *h_H, const int32_t *h_W, const int32_t *h_mode,
+                    const int32_t *h_n_players, uint64_t game_id_base, int wait_ms, int32_t *h_first_actions,
+                    int32_t *session_out);
+
+/* Sizes of a session's outputs (as gen_layout; offsets start at 0 within the
+ * session) and, when dev_outputs is non-NULL, device pointers to them. */
+int gen_server_session_layout(gen_server *sv, int session, gen_layout_info *info, gen_outputs *dev_outputs);
+
+/* One step of every game of the session: h_actions [slots] in; blocks until
+ * the tick that carried it completes, then copies the non-NULL fields of
+ * h_out (host memory, session layout) and the policy's next actions.  One
+ * step per session at a time. */
+int gen_server_step(gen_server *sv, int session, const int32_t *h_actions, const gen_outputs *h_out,
+                    int32_t *h_next_actions, double *latency_ms);
+
+/* Release a session's games; waiting sessions may then be admitted. */
+int gen_server_close(gen_server *sv, int session);
+
+/* Counters, throughput and latency percentiles; reset = 1 starts a new window. */
+int gen_server_stats_get(gen_server *sv, gen_server_stats *st, int reset);
+
+/* Stop the scheduler and free everything. */
+void gen_server_destroy(gen_server *sv);
+
+/* Reason for the last server failure on this thread (never NULL). */
+const char *gen_server_last_error(void);
+
+typedef struct gen_sim_config {
+    int32_t clients;            /* simulated actor clients (threads) */
+    double mean_interarrival_ms;/* exponential think time before each step */
+    int32_t min_games, max_games;/* games per session, uniform */
+    int32_t min_side, max_side; /* board sides, uniform, H and W independent */
+    double frac_1v1, frac_2v2;  /* mode mix; the rest is FFA with 8 players */
+    int32_t min_steps, max_steps;/* steps before a client closes its session and opens another */
+    double seconds;             /* measured window (after a short warm-up) */
+    uint64_t seed, policy_seed;
+    size_t budget_bytes;        /* admission budget */
+    int32_t host_outputs;       /* see gen_server_config */
+    int32_t copy_outputs;       /* clients copy every output into their own host buffers */
+} gen_sim_config;
+
+/* Run a server with closed-loop simulated clients and report its stats. */
+int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_server_stats *st);
+
 /* Reason for the last failure on this thread (never NULL). */
 const char *gen_last_error(void);
 

@@ -364,6 +364,7 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
         GameInfo& gi = e->h_info[(size_t)g];
         memset(&gi, 0, sizeof(gi));
         gi.plane_off = plane;
+        gi.game_id = p->game_id_base + (uint64_t)g;
         gi.cell_off = (int32_t)cell;
         gi.player_off = slot;
         gi.H = (int16_t)H;

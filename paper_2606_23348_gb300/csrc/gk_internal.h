@@ -19,9 +19,10 @@ enum Op : int32_t {
     OP_DERIVE = 5,   // recompute cached per-map bits after a state upload
 };
 
-// Read-only description of one game (32 bytes).
+// Read-only description of one game (48 bytes).
 struct alignas(16) GameInfo {
     int64_t plane_off;   // first cell of player 0's plane in every per-player output plane
+    uint64_t game_id;    // global id keying the game's maps and policy draws
     int32_t cell_off;    // first cell in the state arenas
     int32_t player_off;  // first per-player slot (actions, reward, scoreboard)
     int16_t H, W;
@@ -29,9 +30,10 @@ struct alignas(16) GameInfo {
     int8_t mode, P;
     int16_t n_cities;
     int16_t dmin;        // Manhattan spacing of generals
-    int16_t pad;
+    int16_t pad0;
+    int32_t pad1[2];
 };
-static_assert(sizeof(GameInfo) == 32, "GameInfo is 32 bytes");
+static_assert(sizeof(GameInfo) == 48, "GameInfo is 48 bytes");
 
 // Mutable per-game scalars (32 bytes), one row of gen_read_state's h_scalars.
 struct alignas(16) GameScalars {

@@ -669,7 +669,6 @@ namespace {
 template <bool MULTI>
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const int gidx, const int lane) {
     const Game g = load_game(a.info + gidx);
-    const uint64_t gid = a.game_id_base + (uint64_t)gidx;
     GameScalars* sc = a.scal + gidx;
 
     uint32_t turn = 0, frame = 0, epoch = 0, alive = 0, finished = 0, invalid = 0, saturated = 0, err = 0;
@@ -690,7 +689,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
 
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
-        generate(a, g, s, gid, epoch, lane);
+        generate(a, g, s, a.info[gidx].game_id, epoch, lane);
         turn = 0;
         alive = all_alive;
         finished = 0;
@@ -760,7 +759,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
             if (done) {
                 if (a.auto_reset) {
                     epoch += 1;
-                    generate(a, g, s, gid, epoch, lane);
+                    generate(a, g, s, a.info[gidx].game_id, epoch, lane);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, lane);
@@ -794,7 +793,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
         } else if (a.next_actions) {
             output_pass<false, true>(a, g, s, alive, fin, lane, 0);
         }
-        if (a.next_actions) my_act = policy_pass<!MULTI>(a, g, s, alive, fin, frame, gid, lane);
+        if (a.next_actions) my_act = policy_pass<!MULTI>(a, g, s, alive, fin, frame, a.info[gidx].game_id, lane);
     }
     if (MULTI && a.next_actions && lane < g.P) a.next_actions[g.player_off + lane] = my_act;
     if (wrote_state) {

@@ -1,0 +1,900 @@
+// Env server of libgenerals: the games of many client sessions stay resident
+// on the device and are stepped by continuous batching.  Clients submit step
+// requests as they please; a scheduler thread folds every request waiting at
+// that moment into one tick (one size-bucketed set of step launches over all
+// their games), keeps up to two ticks in flight on separate streams so that
+// requests arriving while a tick runs start on the device before it ends,
+// and completes each request when its tick's event fires.  New sessions are
+// admitted against a byte budget of device memory as earlier ones close.
+//
+// Every game keys its maps and policy draws by the global game id its
+// session was opened with, so a session's results do not depend on the slots
+// it got or on the other sessions in its ticks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <random>
+#include <thread>
+#include <vector>
+
+#include "generals.h"
+#include "gk_internal.h"
+
+using gk::GameInfo;
+using gk::GameScalars;
+using gk::KArgs;
+
+namespace {
+
+thread_local char s_err[512] = "no error";
+
+int sfail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(s_err, sizeof(s_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define SCUDA(expr, what)                                                                                      \
+    do {                                                                                                       \
+        cudaError_t e_ = (expr);                                                                               \
+        if (e_ != cudaSuccess) return sfail(GEN_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e_),           \
+                                            cudaGetErrorString(e_));                                           \
+    } while (0)
+
+using Clock = std::chrono::steady_clock;
+double now_ms() { return std::chrono::duration<double, std::milli>(Clock::now().time_since_epoch()).count(); }
+
+constexpr int kMaxSmemPerCta = 227 * 1024;
+constexpr double kTickDeadlineMs = 30000.0;  // a tick still running after this fails its requests
+
+// First-fit allocator of index ranges in [0, cap), with coalescing.
+class RangeAlloc {
+  public:
+    void reset(int64_t cap) {
+        free_.clear();
+        if (cap > 0) free_[0] = cap;
+    }
+    int64_t alloc(int64_t n, int64_t align) {
+        if (n <= 0) return 0;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            const int64_t off = it->first, len = it->second;
+            const int64_t start = (off + align - 1) / align * align;
+            if (start + n > off + len) continue;
+            free_.erase(it);
+            if (start > off) free_[off] = start - off;
+            if (off + len > start + n) free_[start + n] = off + len - (start + n);
+            return start;
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t n) {
+        if (n <= 0) return;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+  private:
+    std::map<int64_t, int64_t> free_;
+};
+
+struct Session {
+    int id = 0;
+    int n = 0;
+    int64_t g0 = 0, c0 = 0, p0 = 0, s0 = 0;  // first game slot, cell, plane cell, player slot
+    int64_t cells = 0, planes = 0, slots = 0;
+    size_t bytes = 0;  // device bytes charged to the budget
+    int npad_max = 0, pmax = 0;
+    std::vector<GameInfo> info;
+    bool busy = false;
+};
+
+struct Request {
+    int session = 0;
+    double t_submit = 0;
+    bool done = false;
+    int rc = GEN_OK;
+    std::mutex m;
+    std::condition_variable cv;
+};
+
+struct ClassShape {
+    int npad_max = 0, pmax = 0, nw_stride = 0, warp_smem = 0, warps = 2, max_ctas = 0;
+};
+
+struct Tick {
+    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    int32_t* d_list = nullptr;
+    int32_t* h_list = nullptr;  // pinned
+    std::vector<Request*> reqs;
+    bool busy = false;
+    double t_launch = 0;
+    int64_t games = 0;
+};
+
+int cell_class(int npad) {
+    for (int edge : {256, 512, 768, 1024, 1536, 2048, 3072, 4096})
+        if (npad <= edge) return edge;
+    return 4096;
+}
+int player_class(int P) { return P <= 2 ? 2 : (P <= 4 ? 4 : 8); }
+
+}  // namespace
+
+struct gen_server {
+    int device = 0;
+    gen_params prm{};
+    uint64_t policy_seed = 0;
+    int host_outputs = 1;
+    size_t budget = 0, in_use = 0;
+    int64_t cap_games = 0, cap_cells = 0, cap_planes = 0, cap_slots = 0;
+    RangeAlloc a_games, a_cells, a_planes, a_slots;
+    GameInfo* d_info = nullptr;
+    GameScalars* d_scal = nullptr;
+    int16_t* d_army = nullptr;
+    int8_t* d_owner = nullptr;
+    int8_t* d_terrain = nullptr;
+    // outputs and actions: mapped host memory (host clients) or device memory
+    gen_outputs out_host{};  // host view (host mode) / NULLs
+    gen_outputs out_dev{};   // device view used by the kernel
+    int32_t* act_host = nullptr;
+    int32_t* act_dev = nullptr;
+    cudaStream_t admin = nullptr;
+    Tick ticks[2];
+    std::map<std::pair<int, int>, ClassShape> shapes;
+    std::mutex mu;
+    std::condition_variable cv_req, cv_admit;
+    std::deque<Request*> queue;
+    std::map<int, Session> sessions;
+    int next_id = 1;
+    bool stop = false;
+    std::thread sched;
+    // statistics
+    std::mutex stat_mu;
+    std::vector<double> lat;
+    uint64_t frames = 0, requests = 0, tick_count = 0, admitted = 0, waited = 0;
+    double t0 = 0, tick_games_sum = 0;
+    std::string fatal;
+};
+
+namespace {
+
+int class_shape(gen_server* sv, int npad, int P, ClassShape* out) {
+    const auto key = std::make_pair(cell_class(npad), player_class(P));
+    auto it = sv->shapes.find(key);
+    if (it != sv->shapes.end()) {
+        *out = it->second;
+        return GEN_OK;
+    }
+    ClassShape c;
+    c.npad_max = key.first;
+    c.pmax = key.second;
+    c.warp_smem = gk::warp_smem_bytes(c.npad_max, c.pmax, &c.nw_stride);
+    c.warps = 0;
+    for (int w : {2, 1})  // 2 games per CTA: the autotuner's choice for mixed large boards
+        if (w * c.warp_smem <= kMaxSmemPerCta) {
+            c.warps = w;
+            break;
+        }
+    if (c.warps == 0) return sfail(GEN_ERR_BAD_ARG, "board of %d cells does not fit shared memory", npad);
+    const int rc = gk::max_resident_ctas(c.warps, c.warps * c.warp_smem, &c.max_ctas);
+    if (rc) return sfail(GEN_ERR_CUDA, "occupancy query failed (%d)", rc);
+    sv->shapes[key] = c;
+    *out = c;
+    return GEN_OK;
+}
+
+KArgs server_args(gen_server* sv, int op, const ClassShape& c) {
+    KArgs a;
+    memset(&a, 0, sizeof(a));
+    a.info = sv->d_info;
+    a.n_games = (int32_t)sv->cap_games;
+    a.op = op;
+    a.army = sv->d_army;
+    a.owner = sv->d_owner;
+    a.terrain = sv->d_terrain;
+    a.scal = sv->d_scal;
+    a.actions = sv->act_dev;
+    a.obs_army = sv->out_dev.obs_army;
+    a.obs_owner = sv->out_dev.obs_owner;
+    a.obs_terrain = sv->out_dev.obs_terrain;
+    a.obs_vis = sv->out_dev.obs_vis;
+    a.mask = sv->out_dev.mask;
+    a.reward = sv->out_dev.reward;
+    a.scoreboard = sv->out_dev.scoreboard;
+    a.done = sv->out_dev.done;
+    a.do_outputs = 1;
+    a.next_actions = sv->act_dev;
+    a.policy_seed = sv->policy_seed;
+    a.seed = sv->prm.seed;
+    a.mtn_thresh = sv->prm.mountain_thresh;
+    a.city_min = sv->prm.city_army_min;
+    a.city_span = sv->prm.city_army_max - sv->prm.city_army_min + 1;
+    a.max_turns = sv->prm.max_turns;
+    a.auto_reset = sv->prm.auto_reset;
+    a.frames = 1;
+    a.plane_stride = sv->cap_planes;
+    a.slot_stride = (int32_t)sv->cap_slots;
+    a.game_stride = (int32_t)sv->cap_games;
+    a.npad_max = c.npad_max;
+    a.nw_stride = c.nw_stride;
+    a.pmax = c.pmax;
+    a.warp_smem = c.warp_smem;
+    return a;
+}
+
+void finish_request(Request* r, int rc) {
+    std::lock_guard<std::mutex> lk(r->m);
+    r->rc = rc;
+    r->done = true;
+    r->cv.notify_all();
+}
+
+// Launch one tick over every game of `reqs` (called with sv->mu held).
+int launch_tick(gen_server* sv, Tick& t) {
+    std::map<std::pair<int, int>, std::vector<int32_t>> by_class;
+    int64_t games = 0;
+    for (Request* r : t.reqs) {
+        const Session& s = sv->sessions[r->session];
+        for (int i = 0; i < s.n; ++i) {
+            const GameInfo& gi = s.info[(size_t)i];
+            by_class[std::make_pair(cell_class(gi.Npad), player_class(gi.P))].push_back((int32_t)(s.g0 + i));
+        }
+        games += s.n;
+    }
+    std::vector<std::pair<std::pair<int, int>, std::pair<int64_t, int64_t>>> ranges;
+    int64_t k = 0;
+    // largest class first: it finishes last
+    for (auto it = by_class.rbegin(); it != by_class.rend(); ++it) {
+        memcpy(t.h_list + k, it->second.data(), sizeof(int32_t) * it->second.size());
+        ranges.push_back({it->first, {k, (int64_t)it->second.size()}});
+        k += (int64_t)it->second.size();
+    }
+    SCUDA(cudaMemcpyAsync(t.d_list, t.h_list, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, t.stream),
+          "tick list upload");
+    if (ranges.size() > 1) SCUDA(cudaEventRecord(t.fork, t.stream), "fork");
+    for (size_t i = 0; i < ranges.size(); ++i) {
+        ClassShape c;
+        int rc = class_shape(sv, ranges[i].first.first, ranges[i].first.second, &c);
+        if (rc) return rc;
+        KArgs a = server_args(sv, gk::OP_STEP, c);
+        a.list = t.d_list + ranges[i].second.first;
+        a.n_items = (int32_t)ranges[i].second.second;
+        cudaStream_t s = i == 0 ? t.stream : t.side[i - 1];
+        if (i > 0) SCUDA(cudaStreamWaitEvent(s, t.fork, 0), "fork wait");
+        rc = gk::launch_step(a, c.warps, c.max_ctas, s);
+        if (rc) return sfail(GEN_ERR_CUDA, "tick launch: %s", cudaGetErrorString((cudaError_t)rc));
+        if (i > 0) {
+            SCUDA(cudaEventRecord(t.join[i - 1], s), "join");
+            SCUDA(cudaStreamWaitEvent(t.stream, t.join[i - 1], 0), "join wait");
+        }
+    }
+    SCUDA(cudaEventRecord(t.done, t.stream), "tick event");
+    t.busy = true;
+    t.games = games;
+    t.t_launch = now_ms();
+    return GEN_OK;
+}
+
+void scheduler(gen_server* sv) {
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (true) {
+        const bool any_busy = sv->ticks[0].busy || sv->ticks[1].busy;
+        if (sv->stop && sv->queue.empty() && !any_busy) break;
+        // complete finished ticks (poll with a deadline)
+        for (Tick& t : sv->ticks) {
+            if (!t.busy) continue;
+            const cudaError_t q = cudaEventQuery(t.done);
+            int rc = GEN_OK;
+            if (q == cudaErrorNotReady) {
+                if (now_ms() - t.t_launch < kTickDeadlineMs) continue;
+                rc = sfail(GEN_ERR_TIMEOUT, "tick still running after %.0f ms", kTickDeadlineMs);
+                sv->fatal = s_err;
+            } else if (q != cudaSuccess) {
+                rc = sfail(GEN_ERR_CUDA, "tick failed: %s", cudaGetErrorString(q));
+                sv->fatal = s_err;
+            }
+            {
+                std::lock_guard<std::mutex> sl(sv->stat_mu);
+                sv->tick_count += 1;
+                sv->tick_games_sum += (double)t.games;
+                if (rc == GEN_OK) sv->frames += (uint64_t)t.games;
+            }
+            for (Request* r : t.reqs) {
+                sv->sessions[r->session].busy = false;
+                finish_request(r, rc);
+            }
+            t.reqs.clear();
+            t.busy = false;
+        }
+        // start a tick with every waiting request
+        if (!sv->queue.empty()) {
+            Tick* free_t = !sv->ticks[0].busy ? &sv->ticks[0] : (!sv->ticks[1].busy ? &sv->ticks[1] : nullptr);
+            if (free_t && sv->fatal.empty()) {
+                free_t->reqs.assign(sv->queue.begin(), sv->queue.end());
+                sv->queue.clear();
+                const int rc = launch_tick(sv, *free_t);
+                if (rc) {
+                    sv->fatal = s_err;
+                    for (Request* r : free_t->reqs) {
+                        sv->sessions[r->session].busy = false;
+                        finish_request(r, rc);
+                    }
+                    free_t->reqs.clear();
+                    free_t->busy = false;
+                }
+                continue;
+            }
+            if (!sv->fatal.empty()) {
+                for (Request* r : sv->queue) {
+                    sv->sessions[r->session].busy = false;
+                    finish_request(r, GEN_ERR_STATE);
+                }
+                sv->queue.clear();
+            }
+        }
+        // sleep until a request arrives or a running tick may have finished
+        const bool busy_now = sv->ticks[0].busy || sv->ticks[1].busy;
+        sv->cv_req.wait_for(lk, std::chrono::microseconds(busy_now ? 20 : 2000));
+    }
+}
+
+void free_server(gen_server* sv) {
+    if (!sv) return;
+    for (Tick& t : sv->ticks) {
+        for (auto s : t.side) cudaStreamDestroy(s);
+        for (auto e : t.join) cudaEventDestroy(e);
+        if (t.fork) cudaEventDestroy(t.fork);
+        if (t.done) cudaEventDestroy(t.done);
+        if (t.stream) cudaStreamDestroy(t.stream);
+        cudaFree(t.d_list);
+        cudaFreeHost(t.h_list);
+    }
+    if (sv->admin) cudaStreamDestroy(sv->admin);
+    cudaFree(sv->d_info);
+    cudaFree(sv->d_scal);
+    cudaFree(sv->d_army);
+    cudaFree(sv->d_owner);
+    cudaFree(sv->d_terrain);
+    auto release = [&](void* p) {
+        if (!p) return;
+        if (sv->host_outputs)
+            cudaFreeHost(p);
+        else
+            cudaFree(p);
+    };
+    gen_outputs& o = sv->host_outputs ? sv->out_host : sv->out_dev;
+    release(o.obs_army);
+    release(o.obs_owner);
+    release(o.obs_terrain);
+    release(o.obs_vis);
+    release(o.mask);
+    release(o.reward);
+    release(o.scoreboard);
+    release(o.done);
+    release(sv->host_outputs ? (void*)sv->act_host : (void*)sv->act_dev);
+    delete sv;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gen_server_last_error(void) { return s_err; }
+
+int gen_server_create(gen_server** out, const gen_params* p, const gen_server_config* cfg) {
+    if (!out || !p || !cfg) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
+    *out = nullptr;
+    if (cfg->max_games < 1 || cfg->max_games > (1 << 26))
+        return sfail(GEN_ERR_BAD_ARG, "max_games %lld outside [1, 2^26]", (long long)cfg->max_games);
+    if (cfg->max_cells < 16 || cfg->max_cells > (int64_t)INT32_MAX - 4096)
+        return sfail(GEN_ERR_BAD_ARG, "max_cells %lld outside [16, 2^31 - 4096]", (long long)cfg->max_cells);
+    if (cfg->max_plane_cells < 16) return sfail(GEN_ERR_BAD_ARG, "max_plane_cells below 16");
+    if (cfg->budget_bytes < 4096) return sfail(GEN_ERR_BAD_ARG, "budget below 4 KiB");
+    gen_server* sv = new gen_server();
+    cudaGetDevice(&sv->device);
+    sv->prm = *p;
+    sv->policy_seed = cfg->policy_seed;
+    sv->host_outputs = cfg->host_outputs ? 1 : 0;
+    sv->budget = cfg->budget_bytes;
+    sv->cap_games = cfg->max_games;
+    sv->cap_cells = cfg->max_cells;
+    sv->cap_planes = cfg->max_plane_cells;
+    sv->cap_slots = 8 * cfg->max_games;
+    sv->a_games.reset(sv->cap_games);
+    sv->a_cells.reset(sv->cap_cells);
+    sv->a_planes.reset(sv->cap_planes);
+    sv->a_slots.reset(sv->cap_slots);
+    cudaError_t ce = cudaSuccess;
+    auto dev_alloc = [&](void** ptr, size_t n) {
+        if (ce == cudaSuccess) ce = cudaMalloc(ptr, n);
+    };
+    dev_alloc((void**)&sv->d_info, sizeof(GameInfo) * (size_t)sv->cap_games);
+    dev_alloc((void**)&sv->d_scal, sizeof(GameScalars) * (size_t)sv->cap_games);
+    dev_alloc((void**)&sv->d_army, 2 * (size_t)sv->cap_cells);
+    dev_alloc((void**)&sv->d_owner, (size_t)sv->cap_cells);
+    dev_alloc((void**)&sv->d_terrain, (size_t)sv->cap_cells);
+    const size_t pc = (size_t)sv->cap_planes, ps = (size_t)sv->cap_slots, G = (size_t)sv->cap_games;
+    const size_t osz[9] = {pc * 2, pc, pc, pc, pc, ps * 4, ps * 8, G, ps * 4};
+    void* optr[9] = {};
+    for (int i = 0; i < 9 && ce == cudaSuccess; ++i) {
+        if (sv->host_outputs) {
+            ce = cudaHostAlloc(&optr[i], osz[i], cudaHostAllocMapped | cudaHostAllocPortable);
+        } else {
+            ce = cudaMalloc(&optr[i], osz[i]);
+        }
+    }
+    gen_outputs& o = sv->host_outputs ? sv->out_host : sv->out_dev;
+    o.obs_army = (int16_t*)optr[0];
+    o.obs_owner = (int8_t*)optr[1];
+    o.obs_terrain = (int8_t*)optr[2];
+    o.obs_vis = (uint8_t*)optr[3];
+    o.mask = (uint8_t*)optr[4];
+    o.reward = (float*)optr[5];
+    o.scoreboard = (int32_t*)optr[6];
+    o.done = (uint8_t*)optr[7];
+    if (sv->host_outputs) {
+        sv->act_host = (int32_t*)optr[8];
+        void* dp[9] = {};
+        for (int i = 0; i < 9 && ce == cudaSuccess; ++i) ce = cudaHostGetDevicePointer(&dp[i], optr[i], 0);
+        sv->out_dev.obs_army = (int16_t*)dp[0];
+        sv->out_dev.obs_owner = (int8_t*)dp[1];
+        sv->out_dev.obs_terrain = (int8_t*)dp[2];
+        sv->out_dev.obs_vis = (uint8_t*)dp[3];
+        sv->out_dev.mask = (uint8_t*)dp[4];
+        sv->out_dev.reward = (float*)dp[5];
+        sv->out_dev.scoreboard = (int32_t*)dp[6];
+        sv->out_dev.done = (uint8_t*)dp[7];
+        sv->act_dev = (int32_t*)dp[8];
+    } else {
+        sv->act_dev = (int32_t*)optr[8];
+    }
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&sv->admin, cudaStreamNonBlocking);
+    for (Tick& t : sv->ticks) {
+        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaMalloc(&t.d_list, sizeof(int32_t) * G);
+        if (ce == cudaSuccess) ce = cudaHostAlloc(&t.h_list, sizeof(int32_t) * G, cudaHostAllocPortable);
+        for (int i = 0; i < 24 && ce == cudaSuccess; ++i) {  // one per size class
+            cudaStream_t s;
+            cudaEvent_t v;
+            ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (ce == cudaSuccess) t.side.push_back(s);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+            if (ce == cudaSuccess) t.join.push_back(v);
+        }
+    }
+    if (ce != cudaSuccess) {
+        free_server(sv);
+        return ce == cudaErrorMemoryAllocation ? sfail(GEN_ERR_OOM, "server allocation failed")
+                                               : sfail(GEN_ERR_CUDA, "server setup: %s", cudaGetErrorString(ce));
+    }
+    sv->t0 = now_ms();
+    sv->sched = std::thread(scheduler, sv);
+    *out = sv;
+    return GEN_OK;
+}
+
+int gen_server_open(gen_server* sv, int n, const int32_t* h_H, const int32_t* h_W, const int32_t* h_mode,
+                    const int32_t* h_n_players, uint64_t game_id_base, int wait_ms, int32_t* h_first_actions,
+                    int32_t* session_out) {
+    if (!sv || !session_out || !h_H || !h_W || !h_mode) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
+    if (n < 1) return sfail(GEN_ERR_BAD_ARG, "session of %d games", n);
+    Session s;
+    s.n = n;
+    s.info.resize((size_t)n);
+    for (int g = 0; g < n; ++g) {
+        const int H = h_H[g], W = h_W[g], mode = h_mode[g];
+        const int P = mode == GEN_MODE_1V1 ? 2 : mode == GEN_MODE_2V2 ? 4 : (h_n_players ? h_n_players[g] : 8);
+        if (H < 1 || W < 1 || H > GEN_MAX_SIDE || W > GEN_MAX_SIDE || mode < 0 || mode > 2 || P < 2 ||
+            P > GEN_MAX_PLAYERS || H * W < P)
+            return sfail(GEN_ERR_BAD_ARG, "game %d: %dx%d mode %d with %d players", g, H, W, mode, P);
+        GameInfo& gi = s.info[(size_t)g];
+        memset(&gi, 0, sizeof(gi));
+        const int N = H * W, Npad = (N + 15) & ~15;
+        gi.H = (int16_t)H;
+        gi.W = (int16_t)W;
+        gi.N = (int16_t)N;
+        gi.Npad = (int16_t)Npad;
+        gi.mode = (int8_t)mode;
+        gi.P = (int8_t)P;
+        gi.game_id = game_id_base + (uint64_t)g;
+        const int nc = sv->prm.n_cities >= 0 ? sv->prm.n_cities : (int)(((int64_t)N * sv->prm.city_per_mille) / 1000);
+        gi.n_cities = (int16_t)nc;
+        const int d = sv->prm.min_general_dist >= 1 ? sv->prm.min_general_dist : (H + W) / 3;
+        gi.dmin = (int16_t)(d < 1 ? 1 : d);
+        s.cells += Npad;
+        s.planes += (int64_t)P * Npad;
+        s.slots += P;
+        s.npad_max = std::max(s.npad_max, Npad);
+        s.pmax = std::max(s.pmax, P);
+    }
+    s.bytes = (size_t)s.cells * 4 + (size_t)n * (sizeof(GameInfo) + sizeof(GameScalars)) +
+              (sv->host_outputs ? 0 : (size_t)s.planes * 6 + (size_t)s.slots * 16 + (size_t)n);
+    if (s.bytes > sv->budget) return sfail(GEN_ERR_OOM, "session needs %zu bytes, budget is %zu", s.bytes, sv->budget);
+    {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        const auto deadline = Clock::now() + std::chrono::milliseconds(wait_ms > 0 ? wait_ms : 0);
+        bool waited = false;
+        while (true) {
+            if (!sv->fatal.empty()) return sfail(GEN_ERR_STATE, "server failed: %s", sv->fatal.c_str());
+            if (sv->in_use + s.bytes <= sv->budget) {
+                s.g0 = sv->a_games.alloc(n, 1);
+                s.c0 = s.g0 >= 0 ? sv->a_cells.alloc(s.cells, 16) : -1;
+                s.p0 = s.c0 >= 0 ? sv->a_planes.alloc(s.planes, 16) : -1;
+                s.s0 = s.p0 >= 0 ? sv->a_slots.alloc(s.slots, 4) : -1;
+                if (s.s0 >= 0) break;
+                if (s.p0 >= 0) sv->a_planes.release(s.p0, s.planes);
+                if (s.c0 >= 0) sv->a_cells.release(s.c0, s.cells);
+                if (s.g0 >= 0) sv->a_games.release(s.g0, n);
+            }
+            waited = true;
+            if (wait_ms <= 0 || sv->cv_admit.wait_until(lk, deadline) == std::cv_status::timeout)
+                return sfail(GEN_ERR_OOM, "no room for %d games (%zu bytes) within %d ms", n, s.bytes, wait_ms);
+        }
+        sv->in_use += s.bytes;
+        s.id = sv->next_id++;
+        int64_t c = s.c0, pl = s.p0, sl = s.s0;
+        for (auto& gi : s.info) {
+            gi.cell_off = (int32_t)c;
+            gi.plane_off = pl;
+            gi.player_off = (int32_t)sl;
+            c += gi.Npad;
+            pl += (int64_t)gi.P * gi.Npad;
+            sl += gi.P;
+        }
+        s.busy = true;  // until its games exist
+        sv->sessions[s.id] = s;
+        std::lock_guard<std::mutex> sl2(sv->stat_mu);
+        sv->admitted += 1;
+        sv->waited += waited ? 1 : 0;
+    }
+    // generate the session's games (epoch 0), write their first observations and policy actions
+    ClassShape c;
+    Session* sp = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sp = &sv->sessions[s.id];  // map nodes stay put while other sessions come and go
+        int rc = class_shape(sv, sp->npad_max, sp->pmax, &c);
+        if (rc) return rc;
+    }
+    const Session& ss = *sp;
+    SCUDA(cudaMemcpyAsync(sv->d_info + ss.g0, ss.info.data(), sizeof(GameInfo) * (size_t)n, cudaMemcpyHostToDevice,
+                          sv->admin),
+          "session table upload");
+    SCUDA(cudaMemsetAsync(sv->d_scal + ss.g0, 0, sizeof(GameScalars) * (size_t)n, sv->admin), "session scalars");
+    KArgs a = server_args(sv, gk::OP_CREATE, c);
+    a.info = sv->d_info + ss.g0;
+    a.scal = sv->d_scal + ss.g0;
+    a.done = sv->out_dev.done + ss.g0;
+    a.n_items = n;
+    a.n_games = n;
+    int rc = gk::launch_step(a, c.warps, c.max_ctas, sv->admin);
+    if (rc) return sfail(GEN_ERR_CUDA, "session create launch: %s", cudaGetErrorString((cudaError_t)rc));
+    if (h_first_actions) {
+        if (sv->host_outputs) {
+            SCUDA(cudaStreamSynchronize(sv->admin), "session create");
+            memcpy(h_first_actions, sv->act_host + ss.s0, sizeof(int32_t) * (size_t)ss.slots);
+        } else {
+            SCUDA(cudaMemcpyAsync(h_first_actions, sv->act_dev + ss.s0, sizeof(int32_t) * (size_t)ss.slots,
+                                  cudaMemcpyDeviceToHost, sv->admin),
+                  "first actions");
+        }
+    }
+    SCUDA(cudaStreamSynchronize(sv->admin), "session create");
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->sessions[s.id].busy = false;
+    }
+    *session_out = s.id;
+    return GEN_OK;
+}
+
+int gen_server_session_layout(gen_server* sv, int session, gen_layout_info* info, gen_outputs* dev_outputs) {
+    if (!sv || !info) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->sessions.find(session);
+    if (it == sv->sessions.end()) return sfail(GEN_ERR_BAD_ARG, "no session %d", session);
+    const Session& s = it->second;
+    info->n_games = s.n;
+    info->player_slots = (int32_t)s.slots;
+    info->plane_cells = s.planes;
+    info->state_cells = s.cells;
+    info->max_players = s.pmax;
+    int nmax = 0;
+    for (auto& gi : s.info) nmax = std::max(nmax, (int)gi.N);
+    info->max_cells = nmax;
+    if (dev_outputs) {
+        const gen_outputs& o = sv->out_dev;
+        dev_outputs->obs_army = o.obs_army + s.p0;
+        dev_outputs->obs_owner = o.obs_owner + s.p0;
+        dev_outputs->obs_terrain = o.obs_terrain + s.p0;
+        dev_outputs->obs_vis = o.obs_vis + s.p0;
+        dev_outputs->mask = o.mask + s.p0;
+        dev_outputs->reward = o.reward + s.s0;
+        dev_outputs->scoreboard = o.scoreboard + 2 * s.s0;
+        dev_outputs->done = o.done + s.g0;
+    }
+    return GEN_OK;
+}
+
+int gen_server_step(gen_server* sv, int session, const int32_t* h_actions, const gen_outputs* h_out,
+                    int32_t* h_next_actions, double* latency_ms) {
+    if (!sv || !h_actions) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
+    const double t_submit = now_ms();
+    Session s;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->sessions.find(session);
+        if (it == sv->sessions.end()) return sfail(GEN_ERR_BAD_ARG, "no session %d", session);
+        if (it->second.busy) return sfail(GEN_ERR_STATE, "session %d already has a step in flight", session);
+        if (!sv->fatal.empty()) return sfail(GEN_ERR_STATE, "server failed: %s", sv->fatal.c_str());
+        it->second.busy = true;
+        s = it->second;
+    }
+    // actions into the session's slots
+    if (sv->host_outputs) {
+        memcpy(sv->act_host + s.s0, h_actions, sizeof(int32_t) * (size_t)s.slots);
+    } else {
+        SCUDA(cudaMemcpy(sv->act_dev + s.s0, h_actions, sizeof(int32_t) * (size_t)s.slots, cudaMemcpyHostToDevice),
+              "actions upload");
+    }
+    Request r;
+    r.session = session;
+    r.t_submit = t_submit;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->queue.push_back(&r);
+    }
+    sv->cv_req.notify_one();
+    {
+        std::unique_lock<std::mutex> lk(r.m);
+        r.cv.wait(lk, [&] { return r.done; });
+    }
+    if (r.rc != GEN_OK) return sfail(r.rc, "step failed: %s", sv->fatal.c_str());
+    // results out of the session's ranges
+    if (sv->host_outputs) {
+        const gen_outputs& o = sv->out_host;
+        if (h_out) {
+            const size_t pc = (size_t)s.planes, ps = (size_t)s.slots;
+            if (h_out->obs_army) memcpy(h_out->obs_army, o.obs_army + s.p0, pc * 2);
+            if (h_out->obs_owner) memcpy(h_out->obs_owner, o.obs_owner + s.p0, pc);
+            if (h_out->obs_terrain) memcpy(h_out->obs_terrain, o.obs_terrain + s.p0, pc);
+            if (h_out->obs_vis) memcpy(h_out->obs_vis, o.obs_vis + s.p0, pc);
+            if (h_out->mask) memcpy(h_out->mask, o.mask + s.p0, pc);
+            if (h_out->reward) memcpy(h_out->reward, o.reward + s.s0, ps * 4);
+            if (h_out->scoreboard) memcpy(h_out->scoreboard, o.scoreboard + 2 * s.s0, ps * 8);
+            if (h_out->done) memcpy(h_out->done, o.done + s.g0, (size_t)s.n);
+        }
+        if (h_next_actions) memcpy(h_next_actions, sv->act_host + s.s0, sizeof(int32_t) * (size_t)s.slots);
+    } else {
+        const gen_outputs& o = sv->out_dev;
+        const size_t pc = (size_t)s.planes, ps = (size_t)s.slots;
+        if (h_out) {
+            if (h_out->obs_army) SCUDA(cudaMemcpy(h_out->obs_army, o.obs_army + s.p0, pc * 2, cudaMemcpyDefault), "out");
+            if (h_out->obs_owner) SCUDA(cudaMemcpy(h_out->obs_owner, o.obs_owner + s.p0, pc, cudaMemcpyDefault), "out");
+            if (h_out->obs_terrain)
+                SCUDA(cudaMemcpy(h_out->obs_terrain, o.obs_terrain + s.p0, pc, cudaMemcpyDefault), "out");
+            if (h_out->obs_vis) SCUDA(cudaMemcpy(h_out->obs_vis, o.obs_vis + s.p0, pc, cudaMemcpyDefault), "out");
+            if (h_out->mask) SCUDA(cudaMemcpy(h_out->mask, o.mask + s.p0, pc, cudaMemcpyDefault), "out");
+            if (h_out->reward) SCUDA(cudaMemcpy(h_out->reward, o.reward + s.s0, ps * 4, cudaMemcpyDefault), "out");
+            if (h_out->scoreboard)
+                SCUDA(cudaMemcpy(h_out->scoreboard, o.scoreboard + 2 * s.s0, ps * 8, cudaMemcpyDefault), "out");
+            if (h_out->done) SCUDA(cudaMemcpy(h_out->done, o.done + s.g0, (size_t)s.n, cudaMemcpyDefault), "out");
+        }
+        if (h_next_actions)
+            SCUDA(cudaMemcpy(h_next_actions, sv->act_dev + s.s0, sizeof(int32_t) * ps, cudaMemcpyDeviceToHost),
+                  "next actions");
+    }
+    const double lat = now_ms() - t_submit;
+    if (latency_ms) *latency_ms = lat;
+    {
+        std::lock_guard<std::mutex> sl(sv->stat_mu);
+        sv->lat.push_back(lat);
+        sv->requests += 1;
+    }
+    return GEN_OK;
+}
+
+int gen_server_close(gen_server* sv, int session) {
+    if (!sv) return sfail(GEN_ERR_BAD_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->sessions.find(session);
+    if (it == sv->sessions.end()) return sfail(GEN_ERR_BAD_ARG, "no session %d", session);
+    if (it->second.busy) return sfail(GEN_ERR_STATE, "session %d has a step in flight", session);
+    const Session& s = it->second;
+    sv->a_games.release(s.g0, s.n);
+    sv->a_cells.release(s.c0, s.cells);
+    sv->a_planes.release(s.p0, s.planes);
+    sv->a_slots.release(s.s0, s.slots);
+    sv->in_use -= s.bytes;
+    sv->sessions.erase(it);
+    sv->cv_admit.notify_all();
+    return GEN_OK;
+}
+
+int gen_server_stats_get(gen_server* sv, gen_server_stats* st, int reset) {
+    if (!sv || !st) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> sl(sv->stat_mu);
+        lat = sv->lat;
+        st->requests = sv->requests;
+        st->frames = sv->frames;
+        st->ticks = sv->tick_count;
+        st->sessions_admitted = sv->admitted;
+        st->sessions_waited = sv->waited;
+        st->seconds = (now_ms() - sv->t0) * 1e-3;
+        st->tick_games_mean = sv->tick_count ? sv->tick_games_sum / (double)sv->tick_count : 0.0;
+        if (reset) {
+            sv->lat.clear();
+            sv->requests = sv->frames = sv->tick_count = sv->admitted = sv->waited = 0;
+            sv->tick_games_sum = 0;
+            sv->t0 = now_ms();
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        st->bytes_in_use = (double)sv->in_use;
+        st->budget = (double)sv->budget;
+        st->sessions_open = (uint64_t)sv->sessions.size();
+    }
+    st->frames_per_s = st->seconds > 0 ? (double)st->frames / st->seconds : 0.0;
+    auto pct = [&](double q) {
+        if (lat.empty()) return 0.0;
+        const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
+        std::nth_element(lat.begin(), lat.begin() + (long)k, lat.end());
+        return lat[k];
+    };
+    st->lat_p50_ms = pct(0.50);
+    st->lat_p99_ms = pct(0.99);
+    double sum = 0;
+    for (double x : lat) sum += x;
+    st->lat_mean_ms = lat.empty() ? 0.0 : sum / (double)lat.size();
+    return GEN_OK;
+}
+
+void gen_server_destroy(gen_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_req.notify_all();
+    if (sv->sched.joinable()) sv->sched.join();
+    cudaDeviceSynchronize();
+    free_server(sv);
+}
+
+// Closed-loop actor clients: each waits an exponential think time, steps its
+// session with the actions the policy gave it last, and after a random
+// number of steps closes the session and opens a new one.
+int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_server_stats* st) {
+    if (!p || !cfg || !st) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
+    if (cfg->clients < 1 || cfg->min_games < 1 || cfg->max_games < cfg->min_games || cfg->min_side < 1 ||
+        cfg->max_side < cfg->min_side || cfg->max_side > GEN_MAX_SIDE || cfg->seconds <= 0)
+        return sfail(GEN_ERR_BAD_ARG, "bad simulation config");
+    gen_server* sv = nullptr;
+    // room for every client to hold its largest session twice over (one closing, one opening)
+    const int64_t max_games = (int64_t)cfg->clients * cfg->max_games * 2;
+    const int64_t side = (int64_t)cfg->max_side;
+    const int64_t mean_cells = ((int64_t)(cfg->min_side + cfg->max_side) / 2 + 1) * ((cfg->min_side + cfg->max_side) / 2 + 1);
+    gen_server_config sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.budget_bytes = cfg->budget_bytes;
+    sc.max_games = max_games;
+    sc.max_cells = std::min<int64_t>((int64_t)INT32_MAX - 4096, std::max<int64_t>(side * side * 64, 2 * max_games * mean_cells));
+    const double mean_p = 2.0 * cfg->frac_1v1 + 4.0 * cfg->frac_2v2 + 8.0 * (1.0 - cfg->frac_1v1 - cfg->frac_2v2);
+    sc.max_plane_cells = std::max<int64_t>(side * side * 8 * 64, (int64_t)((double)sc.max_cells * mean_p * 1.25));
+    sc.host_outputs = cfg->host_outputs;
+    sc.policy_seed = cfg->policy_seed;
+    int rc = gen_server_create(&sv, p, &sc);
+    if (rc) return rc;
+    std::atomic<bool> stop{false};
+    std::atomic<bool> measuring{false};
+    std::atomic<uint64_t> next_game_id{0};
+    std::atomic<int> errors{0};
+    std::mutex err_mu;
+    std::string first_err;
+    auto client = [&](int id) {
+        std::mt19937_64 rng(cfg->seed * 1000003ULL + (uint64_t)id);
+        std::exponential_distribution<double> think(1.0 / std::max(1e-6, cfg->mean_interarrival_ms));
+        std::uniform_int_distribution<int> ngames(cfg->min_games, cfg->max_games);
+        std::uniform_int_distribution<int> side(cfg->min_side, cfg->max_side);
+        std::uniform_int_distribution<int> life(cfg->min_steps, std::max(cfg->min_steps, cfg->max_steps));
+        std::uniform_real_distribution<double> u01(0.0, 1.0);
+        while (!stop.load()) {
+            const int n = ngames(rng);
+            std::vector<int32_t> H((size_t)n), W((size_t)n), M((size_t)n), P((size_t)n, 8);
+            for (int g = 0; g < n; ++g) {
+                H[(size_t)g] = side(rng);
+                W[(size_t)g] = side(rng);
+                const double u = u01(rng);
+                M[(size_t)g] = u < cfg->frac_1v1 ? 0 : (u < cfg->frac_1v1 + cfg->frac_2v2 ? 1 : 2);
+            }
+            const uint64_t base = next_game_id.fetch_add((uint64_t)n);
+            int32_t sid = 0;
+            std::vector<int32_t> acts((size_t)n * 8);
+            int r = gen_server_open(sv, n, H.data(), W.data(), M.data(), P.data(), base, 60000, acts.data(), &sid);
+            if (r) {
+                if (errors.fetch_add(1) == 0) {
+                    std::lock_guard<std::mutex> lk(err_mu);
+                    first_err = s_err;
+                }
+                return;
+            }
+            gen_layout_info li;
+            gen_server_session_layout(sv, sid, &li, nullptr);
+            acts.resize((size_t)li.player_slots);
+            std::vector<int16_t> oa((size_t)li.plane_cells);
+            std::vector<uint8_t> ob((size_t)li.plane_cells * 4);
+            std::vector<float> rw((size_t)li.player_slots);
+            std::vector<int32_t> sb((size_t)li.player_slots * 2);
+            std::vector<uint8_t> dn((size_t)n);
+            gen_outputs ho;
+            ho.obs_army = oa.data();
+            ho.obs_owner = (int8_t*)ob.data();
+            ho.obs_terrain = (int8_t*)ob.data() + li.plane_cells;
+            ho.obs_vis = ob.data() + 2 * li.plane_cells;
+            ho.mask = ob.data() + 3 * li.plane_cells;
+            ho.reward = rw.data();
+            ho.scoreboard = sb.data();
+            ho.done = dn.data();
+            const int steps = life(rng);
+            for (int k = 0; k < steps && !stop.load(); ++k) {
+                std::this_thread::sleep_for(std::chrono::duration<double, std::milli>(think(rng)));
+                double lat = 0;
+                r = gen_server_step(sv, sid, acts.data(), cfg->copy_outputs ? &ho : nullptr, acts.data(), &lat);
+                if (r) {
+                    if (errors.fetch_add(1) == 0) {
+                        std::lock_guard<std::mutex> lk(err_mu);
+                        first_err = s_err;
+                    }
+                    break;
+                }
+            }
+            gen_server_close(sv, sid);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int i = 0; i < cfg->clients; ++i) th.emplace_back(client, i);
+    // warm up, then measure
+    std::this_thread::sleep_for(std::chrono::duration<double>(std::min(2.0, 0.25 * cfg->seconds)));
+    gen_server_stats tmp;
+    gen_server_stats_get(sv, &tmp, 1);
+    std::this_thread::sleep_for(std::chrono::duration<double>(cfg->seconds));
+    gen_server_stats_get(sv, st, 0);
+    stop.store(true);
+    for (auto& t : th) t.join();
+    gen_server_destroy(sv);
+    if (errors.load()) return sfail(GEN_ERR_STATE, "%d client errors; first: %s", errors.load(), first_err.c_str());
+    return GEN_OK;
+}
+
+}  // extern "C"

@@ -30,7 +30,8 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(names) >= 15
     for n in names:
         assert hasattr(lib, n), f"{n} declared but not exported"
-    assert set(names) == set(gen.EXPORTS)
+    from paper_2606_23348_gb300.server import SERVER_EXPORTS
+    assert set(names) == set(gen.EXPORTS) | set(SERVER_EXPORTS)
 
 
 def test_default_params_host_only(lib):
