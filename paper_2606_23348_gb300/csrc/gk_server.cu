@@ -107,6 +107,7 @@ struct Session {
     size_t bytes = 0;  // device bytes charged to the budget
     int npad_max = 0, pmax = 0;
     std::vector<GameInfo> info;
+    std::vector<std::pair<int, std::vector<int32_t>>> by_class;  // class index -> game slots
     bool busy = false;
 };
 
@@ -142,6 +143,24 @@ int cell_class(int npad) {
     return 4096;
 }
 int player_class(int P) { return P <= 2 ? 2 : (P <= 4 ? 4 : 8); }
+
+// size classes in launch order (largest first): 8 cell edges x 3 player classes
+constexpr int kClasses = 24;
+int class_index(int npad, int P) {
+    int ci = 0;
+    for (int edge : {256, 512, 768, 1024, 1536, 2048, 3072, 4096}) {
+        if (npad <= edge) break;
+        ++ci;
+    }
+    ci = ci > 7 ? 7 : ci;
+    const int pi = P <= 2 ? 0 : (P <= 4 ? 1 : 2);
+    return (7 - ci) * 3 + (2 - pi);
+}
+int class_edge(int idx) {
+    static const int edges[8] = {256, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    return edges[7 - idx / 3];
+}
+int class_players(int idx) { return 8 >> (idx % 3); }
 
 }  // namespace
 
@@ -256,42 +275,50 @@ void finish_request(Request* r, int rc) {
 
 // Launch one tick over every game of `reqs` (called with sv->mu held).
 int launch_tick(gen_server* sv, Tick& t) {
-    std::map<std::pair<int, int>, std::vector<int32_t>> by_class;
+    int64_t count[kClasses] = {0};
+    std::vector<const Session*> ss;
+    ss.reserve(t.reqs.size());
     int64_t games = 0;
     for (Request* r : t.reqs) {
         const Session& s = sv->sessions[r->session];
-        for (int i = 0; i < s.n; ++i) {
-            const GameInfo& gi = s.info[(size_t)i];
-            by_class[std::make_pair(cell_class(gi.Npad), player_class(gi.P))].push_back((int32_t)(s.g0 + i));
-        }
+        ss.push_back(&s);
+        for (auto& kv : s.by_class) count[kv.first] += (int64_t)kv.second.size();
         games += s.n;
     }
-    std::vector<std::pair<std::pair<int, int>, std::pair<int64_t, int64_t>>> ranges;
+    int64_t start[kClasses], fill[kClasses];
     int64_t k = 0;
-    // largest class first: it finishes last
-    for (auto it = by_class.rbegin(); it != by_class.rend(); ++it) {
-        memcpy(t.h_list + k, it->second.data(), sizeof(int32_t) * it->second.size());
-        ranges.push_back({it->first, {k, (int64_t)it->second.size()}});
-        k += (int64_t)it->second.size();
+    for (int c = 0; c < kClasses; ++c) {
+        start[c] = fill[c] = k;
+        k += count[c];
     }
+    for (const Session* s : ss)
+        for (auto& kv : s->by_class) {
+            memcpy(t.h_list + fill[kv.first], kv.second.data(), sizeof(int32_t) * kv.second.size());
+            fill[kv.first] += (int64_t)kv.second.size();
+        }
     SCUDA(cudaMemcpyAsync(t.d_list, t.h_list, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, t.stream),
           "tick list upload");
-    if (ranges.size() > 1) SCUDA(cudaEventRecord(t.fork, t.stream), "fork");
-    for (size_t i = 0; i < ranges.size(); ++i) {
-        ClassShape c;
-        int rc = class_shape(sv, ranges[i].first.first, ranges[i].first.second, &c);
+    int used = 0;
+    for (int c = 0; c < kClasses; ++c) used += count[c] > 0;
+    if (used > 1) SCUDA(cudaEventRecord(t.fork, t.stream), "fork");
+    int i = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        if (!count[c]) continue;
+        ClassShape cs;
+        int rc = class_shape(sv, class_edge(c), class_players(c), &cs);
         if (rc) return rc;
-        KArgs a = server_args(sv, gk::OP_STEP, c);
-        a.list = t.d_list + ranges[i].second.first;
-        a.n_items = (int32_t)ranges[i].second.second;
-        cudaStream_t s = i == 0 ? t.stream : t.side[i - 1];
+        KArgs a = server_args(sv, gk::OP_STEP, cs);
+        a.list = t.d_list + start[c];
+        a.n_items = (int32_t)count[c];
+        cudaStream_t s = i == 0 ? t.stream : t.side[(size_t)i - 1];
         if (i > 0) SCUDA(cudaStreamWaitEvent(s, t.fork, 0), "fork wait");
-        rc = gk::launch_step(a, c.warps, c.max_ctas, s);
+        rc = gk::launch_step(a, cs.warps, cs.max_ctas, s);
         if (rc) return sfail(GEN_ERR_CUDA, "tick launch: %s", cudaGetErrorString((cudaError_t)rc));
         if (i > 0) {
-            SCUDA(cudaEventRecord(t.join[i - 1], s), "join");
-            SCUDA(cudaStreamWaitEvent(t.stream, t.join[i - 1], 0), "join wait");
+            SCUDA(cudaEventRecord(t.join[(size_t)i - 1], s), "join");
+            SCUDA(cudaStreamWaitEvent(t.stream, t.join[(size_t)i - 1], 0), "join wait");
         }
+        ++i;
     }
     SCUDA(cudaEventRecord(t.done, t.stream), "tick event");
     t.busy = true;
@@ -397,7 +424,7 @@ void free_server(gen_server* sv) {
     release(o.reward);
     release(o.scoreboard);
     release(o.done);
-    release(sv->host_outputs ? (void*)sv->act_host : (void*)sv->act_dev);
+    if (sv->act_host) cudaFreeHost(sv->act_host);
     delete sv;
 }
 
@@ -442,8 +469,10 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
     const size_t pc = (size_t)sv->cap_planes, ps = (size_t)sv->cap_slots, G = (size_t)sv->cap_games;
     const size_t osz[9] = {pc * 2, pc, pc, pc, pc, ps * 4, ps * 8, G, ps * 4};
     void* optr[9] = {};
+    // outputs: mapped host memory or device memory; actions: always mapped host
+    // memory, so clients pass them without any CUDA call
     for (int i = 0; i < 9 && ce == cudaSuccess; ++i) {
-        if (sv->host_outputs) {
+        if (sv->host_outputs || i == 8) {
             ce = cudaHostAlloc(&optr[i], osz[i], cudaHostAllocMapped | cudaHostAllocPortable);
         } else {
             ce = cudaMalloc(&optr[i], osz[i]);
@@ -472,7 +501,10 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         sv->out_dev.done = (uint8_t*)dp[7];
         sv->act_dev = (int32_t*)dp[8];
     } else {
-        sv->act_dev = (int32_t*)optr[8];
+        sv->act_host = (int32_t*)optr[8];
+        void* dp = nullptr;
+        if (ce == cudaSuccess) ce = cudaHostGetDevicePointer(&dp, optr[8], 0);
+        sv->act_dev = (int32_t*)dp;
     }
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&sv->admin, cudaStreamNonBlocking);
     for (Tick& t : sv->ticks) {
@@ -569,6 +601,13 @@ int gen_server_open(gen_server* sv, int n, const int32_t* h_H, const int32_t* h_
             pl += (int64_t)gi.P * gi.Npad;
             sl += gi.P;
         }
+        {
+            std::vector<int32_t> per[kClasses];
+            for (int g = 0; g < n; ++g)
+                per[class_index(s.info[(size_t)g].Npad, s.info[(size_t)g].P)].push_back((int32_t)(s.g0 + g));
+            for (int c = 0; c < kClasses; ++c)
+                if (!per[c].empty()) s.by_class.emplace_back(c, std::move(per[c]));
+        }
         s.busy = true;  // until its games exist
         sv->sessions[s.id] = s;
         std::lock_guard<std::mutex> sl2(sv->stat_mu);
@@ -597,17 +636,8 @@ int gen_server_open(gen_server* sv, int n, const int32_t* h_H, const int32_t* h_
     a.n_games = n;
     int rc = gk::launch_step(a, c.warps, c.max_ctas, sv->admin);
     if (rc) return sfail(GEN_ERR_CUDA, "session create launch: %s", cudaGetErrorString((cudaError_t)rc));
-    if (h_first_actions) {
-        if (sv->host_outputs) {
-            SCUDA(cudaStreamSynchronize(sv->admin), "session create");
-            memcpy(h_first_actions, sv->act_host + ss.s0, sizeof(int32_t) * (size_t)ss.slots);
-        } else {
-            SCUDA(cudaMemcpyAsync(h_first_actions, sv->act_dev + ss.s0, sizeof(int32_t) * (size_t)ss.slots,
-                                  cudaMemcpyDeviceToHost, sv->admin),
-                  "first actions");
-        }
-    }
     SCUDA(cudaStreamSynchronize(sv->admin), "session create");
+    if (h_first_actions) memcpy(h_first_actions, sv->act_host + ss.s0, sizeof(int32_t) * (size_t)ss.slots);
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->sessions[s.id].busy = false;
@@ -658,13 +688,8 @@ int gen_server_step(gen_server* sv, int session, const int32_t* h_actions, const
         it->second.busy = true;
         s = it->second;
     }
-    // actions into the session's slots
-    if (sv->host_outputs) {
-        memcpy(sv->act_host + s.s0, h_actions, sizeof(int32_t) * (size_t)s.slots);
-    } else {
-        SCUDA(cudaMemcpy(sv->act_dev + s.s0, h_actions, sizeof(int32_t) * (size_t)s.slots, cudaMemcpyHostToDevice),
-              "actions upload");
-    }
+    // actions into the session's slots (mapped host memory)
+    memcpy(sv->act_host + s.s0, h_actions, sizeof(int32_t) * (size_t)s.slots);
     Request r;
     r.session = session;
     r.t_submit = t_submit;
@@ -708,9 +733,7 @@ int gen_server_step(gen_server* sv, int session, const int32_t* h_actions, const
                 SCUDA(cudaMemcpy(h_out->scoreboard, o.scoreboard + 2 * s.s0, ps * 8, cudaMemcpyDefault), "out");
             if (h_out->done) SCUDA(cudaMemcpy(h_out->done, o.done + s.g0, (size_t)s.n, cudaMemcpyDefault), "out");
         }
-        if (h_next_actions)
-            SCUDA(cudaMemcpy(h_next_actions, sv->act_dev + s.s0, sizeof(int32_t) * ps, cudaMemcpyDeviceToHost),
-                  "next actions");
+        if (h_next_actions) memcpy(h_next_actions, sv->act_host + s.s0, sizeof(int32_t) * ps);
     }
     const double lat = now_ms() - t_submit;
     if (latency_ms) *latency_ms = lat;
