@@ -76,6 +76,7 @@ struct gen_env {
     int pmax = 0;
     int npad_max = 0;
     int nmax = 0;
+    bool uniform = false;            // every game has the same board size and mode
     Bucket all;                      // every game, largest carve (used for game-id lists)
     std::vector<Bucket> buckets;     // size buckets covering every game once
     int32_t* d_order = nullptr;      // games sorted by bucket (NULL: identity, one bucket)
@@ -191,6 +192,10 @@ KArgs base_args(const gen_env* e, const Bucket& b, int op) {
     a.nw_stride = b.nw_stride;
     a.pmax = b.pmax;
     a.warp_smem = b.warp_smem;
+    if (e->uniform) {
+        a.uniform = 1;
+        a.ushape = e->h_info[0];
+    }
     return a;
 }
 
@@ -391,6 +396,13 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
     e->state_cells = cell;
     e->plane_cells = plane;
     e->player_slots = slot;
+    e->uniform = true;
+    for (int g = 1; g < batch && e->uniform; ++g) {
+        const GameInfo& x = e->h_info[(size_t)g];
+        const GameInfo& y = e->h_info[0];
+        e->uniform = x.H == y.H && x.W == y.W && x.mode == y.mode && x.P == y.P && x.n_cities == y.n_cities &&
+                     x.dmin == y.dmin;
+    }
     e->all.n = batch;
     e->all.npad_max = e->npad_max;
     e->all.pmax = e->pmax;

@@ -67,6 +67,10 @@ struct KArgs {
     int32_t slot_stride;    // per-player slots of one frame (reward, actions log)
     int32_t game_stride;    // games of one frame (done)
     int32_t* action_log;    // optional [frames][slots]: actions each frame consumed
+    // uniform batch: every game has ushape's board and mode; game g sits at
+    // cell g * Npad, plane cell g * P * Npad, slot g * P, global id base + g
+    int32_t uniform;
+    GameInfo ushape;
     uint64_t policy_seed;
     uint64_t seed;
     uint64_t game_id_base;

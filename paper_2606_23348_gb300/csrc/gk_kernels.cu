@@ -66,7 +66,7 @@ struct Smem {
     uint32_t* colL;    // last column
     uint32_t* vis;     // [pmax][stride]
     uint32_t* tmp;
-    uint16_t* cnt;     // [pmax][chunks]: legal (cell, direction) pairs per 16-cell chunk
+    uint64_t* legal;   // [pmax][chunks]: bit 4j+d = move of chunk cell j towards d is legal
     int32_t* misc;     // [0..7] general cells, [8..15] land, [16..23] army
     int stride;
 };
@@ -90,9 +90,8 @@ __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
     w += pm * st;
     s.tmp = w;
     w += st;
-    s.cnt = reinterpret_cast<uint16_t*>(w);
-    const int cnt_words = (pm * (np >> 4) + 1) / 2;
-    w += (cnt_words + 3) & ~3;
+    s.legal = reinterpret_cast<uint64_t*>(w);  // 16-byte aligned: every region above is
+    w += (2 * pm * (np >> 4) + 3) & ~3;
     s.misc = reinterpret_cast<int32_t*>(w);
     s.stride = st;
     return s;
@@ -487,6 +486,12 @@ __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane)
 
 // 4 bits -> 4 bytes of 0x01
 __device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+// low nibbles of 4 bytes -> 16 bits (byte k's nibble at bits 4k..4k+3)
+__device__ __forceinline__ uint32_t nibbles16(uint32_t x) {
+    x &= 0x0F0F0F0Fu;
+    const uint32_t y = (x | (x >> 4)) & 0x00FF00FFu;
+    return (y | (y >> 8)) & 0xFFFFu;
+}
 
 // ---- observation + mask chunks of 16 cells (Sec. IV-B, App. A, Sec. IV-G) --
 // WRITE: store the planes; COUNT: legal (cell, direction) pairs per chunk.
@@ -513,9 +518,10 @@ __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32
             om[k] = dpb & (spread4((mv >> (4 * k)) & 15u) * 0xFFu);
         }
         if (COUNT) {
-            const uint32_t n = __popc(om[0] & 0x0F0F0F0Fu) + __popc(om[1] & 0x0F0F0F0Fu) +
-                               __popc(om[2] & 0x0F0F0F0Fu) + __popc(om[3] & 0x0F0F0F0Fu);
-            s.cnt[p * nch + ch] = (uint16_t)n;
+            // the chunk's legal moves as 64 bits: 4 per cell in (cell, direction) order
+            const uint32_t lo = nibbles16(om[0]) | (nibbles16(om[1]) << 16);
+            const uint32_t hi = nibbles16(om[2]) | (nibbles16(om[3]) << 16);
+            s.legal[p * nch + ch] = ((uint64_t)hi << 32) | lo;
         }
         if (WRITE) {
             const uint32_t vis16 = (s.vis[p * st + wi] >> sh) & 0xFFFFu;
@@ -565,7 +571,10 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 }
 
 // ---- benchmark policy: uniform legal (cell, direction), split p = 0.2 -------
-// Needs the chunk counts of output_pass<*, true>.
+// Needs the chunk masks of output_pass<*, true>.  Players are scanned two at
+// a time (16-bit counts packed in one 32-bit warp scan: a board has at most
+// 4 x 4096 legal pairs); the lane holding pair j walks its chunks and selects
+// the bit by popcount bisection.
 // Returns, on lane p < P, player p's action; DIRECT also stores it.
 template <bool DIRECT>
 __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished,
@@ -574,6 +583,7 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
     const int nch = g.nch;
     const int cpl = (nch + 31) >> 5;  // consecutive chunks per lane
     const int c_lo = lane * cpl;
+    const int c_hi = min(c_lo + cpl, nch);
     // lane p hashes player p's two draws
     uint32_t u1 = 0, u2 = 0;
     if (lane < g.P) {
@@ -581,57 +591,78 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
         u1 = hdraw(K, 0);
         u2 = hdraw(K, 1);
     }
-    for (int p = 0; p < g.P; ++p) {
-        const uint16_t* cnt = s.cnt + p * nch;
+    for (int p0 = 0; p0 < g.P; p0 += 2) {
         uint32_t mine = 0;
-        for (int c = c_lo; c < c_lo + cpl && c < nch; ++c) mine += cnt[c];
-        const uint32_t incl = warp_incl_scan(mine, lane);
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        const uint32_t pu1 = __shfl_sync(kFull, u1, p);
-        const uint32_t pu2 = __shfl_sync(kFull, u2, p);
-        int32_t action = 0;
-        if (total > 0 && !finished && ((alive >> p) & 1u)) {
-            const uint32_t j = (uint32_t)uniform_below(pu1, total);
-            const int L = __ffs(__ballot_sync(kFull, incl > j)) - 1;
-            // chunk holding pair j, and j's rank inside it (lane L walks its chunks)
-            uint32_t jj = j - __shfl_sync(kFull, incl - mine, L);
-            int chs = 0;
-            if (lane == L) {
-                chs = c_lo;
-                while (jj >= cnt[chs]) {
-                    jj -= cnt[chs];
-                    ++chs;
-                }
-            }
-            chs = __shfl_sync(kFull, chs, L);
-            jj = __shfl_sync(kFull, jj, L);
-            // lanes 0..15 take the 16 cells of the chunk
-            const int c = chs * 16 + (lane & 15);
-            uint32_t dirs = 0;
-            if (lane < 16 && s.owner[c] == p && s.army[c] >= 2) dirs = (s.terrain[c] >> 2) & 15u;
-            const uint32_t nd = __popc(dirs);
-            const uint32_t ic = warp_incl_scan(nd, lane);
-            const int B = __ffs(__ballot_sync(kFull, ic > jj)) - 1;
-            int32_t found = 0;
-            if (lane == B) {
-                const uint32_t r = jj - (ic - nd);
-                uint32_t dd = dirs;
-                for (uint32_t z = 0; z < r; ++z) dd &= dd - 1;
-                const int d = __ffs(dd) - 1;
-                found = c * 9 + ((pu2 < kSplitThresh) ? 5 + d : 1 + d);
-            }
-            action = __shfl_sync(kFull, found, B);
+        for (int c = c_lo; c < c_hi; ++c) {
+            const uint64_t m0 = s.legal[p0 * nch + c];
+            mine += __popcll(m0);
+            if (p0 + 1 < g.P) mine += (uint32_t)__popcll(s.legal[(p0 + 1) * nch + c]) << 16;
         }
-        if (DIRECT) {
-            if (lane == 0) a.next_actions[g.player_off + p] = action;
-        } else if (lane == p) {
-            mine_action = action;
+        const uint32_t incl2 = warp_incl_scan(mine, lane);
+        const uint32_t total2 = __shfl_sync(kFull, incl2, 31);
+        for (int q = 0; q < 2 && p0 + q < g.P; ++q) {
+            const int p = p0 + q;
+            const uint32_t total = (total2 >> (16 * q)) & 0xFFFFu;
+            const uint32_t incl = (incl2 >> (16 * q)) & 0xFFFFu;
+            const uint32_t pu1 = __shfl_sync(kFull, u1, p);
+            const uint32_t pu2 = __shfl_sync(kFull, u2, p);
+            int32_t action = 0;
+            if (total > 0 && !finished && ((alive >> p) & 1u)) {
+                const uint32_t j = (uint32_t)uniform_below(pu1, total);
+                const int L = __ffs(__ballot_sync(kFull, incl > j)) - 1;
+                int32_t found = 0;
+                if (lane == L) {
+                    uint32_t jj = j - (incl - ((mine >> (16 * q)) & 0xFFFFu));
+                    for (int c = c_lo; c < c_hi; ++c) {
+                        const uint64_t m = s.legal[p * nch + c];
+                        const uint32_t n = (uint32_t)__popcll(m);
+                        if (jj >= n) {
+                            jj -= n;
+                            continue;
+                        }
+                        uint32_t x = (uint32_t)m;
+                        int bit = 0;
+                        const uint32_t nlo = __popc(x);
+                        if (jj >= nlo) {
+                            jj -= nlo;
+                            x = (uint32_t)(m >> 32);
+                            bit = 32;
+                        }
+#pragma unroll
+                        for (int w = 16; w >= 1; w >>= 1) {
+                            const uint32_t cw = __popc(x & ((1u << w) - 1u));
+                            if (jj >= cw) {
+                                jj -= cw;
+                                x >>= w;
+                                bit += w;
+                            }
+                        }
+                        const int d = bit & 3;
+                        found = (c * 16 + (bit >> 2)) * 9 + ((pu2 < kSplitThresh) ? 5 + d : 1 + d);
+                        break;
+                    }
+                }
+                action = __shfl_sync(kFull, found, L);
+            }
+            if (DIRECT) {
+                if (lane == 0) a.next_actions[g.player_off + p] = action;
+            } else if (lane == p) {
+                mine_action = action;
+            }
         }
     }
     return mine_action;
 }
 
-__device__ __forceinline__ void load_board(const KArgs& a, const Game& g, const Smem& s, int lane) {
+// All of a board's 16-byte vectors (army, owner, terrain) copied global ->
+// shared with cp.async: every copy is in flight at once and none passes
+// through registers.  board_wait() completes them (a hardware wait).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void board_issue(const KArgs& a, const Game& g, const Smem& s, int lane) {
     const int n16 = g.Npad >> 4;  // 16-byte vectors per int8 plane
     const uint4* ga = reinterpret_cast<const uint4*>(a.army + g.cell_off);
     const uint4* go = reinterpret_cast<const uint4*>(a.owner + g.cell_off);
@@ -639,11 +670,14 @@ __device__ __forceinline__ void load_board(const KArgs& a, const Game& g, const 
     uint4* sa = reinterpret_cast<uint4*>(s.army);
     uint4* so = reinterpret_cast<uint4*>(s.owner);
     uint4* st = reinterpret_cast<uint4*>(s.terrain);
-    for (int v = lane; v < 2 * n16; v += 32) sa[v] = __ldcs(ga + v);
+    for (int v = lane; v < 2 * n16; v += 32) cp_async16(sa + v, ga + v);
     for (int v = lane; v < n16; v += 32) {
-        so[v] = __ldcs(go + v);
-        st[v] = __ldcs(gt + v);
+        cp_async16(so + v, go + v);
+        cp_async16(st + v, gt + v);
     }
+}
+__device__ __forceinline__ void board_wait() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
 }
 
@@ -666,15 +700,37 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
 
 namespace {
 
+__device__ __forceinline__ Game game_of(const KArgs& a, int gidx) {
+    if (!a.uniform) return load_game(a.info + gidx);
+    Game g = load_game(&a.ushape);
+    g.cell_off = gidx * g.Npad;
+    g.player_off = gidx * g.P;
+    g.plane_off = (int64_t)gidx * g.P * g.Npad;
+    return g;
+}
+__device__ __forceinline__ uint64_t game_id_of(const KArgs& a, int gidx) {
+    return a.uniform ? a.game_id_base + (uint64_t)gidx : a.info[gidx].game_id;
+}
+
 template <bool MULTI>
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const int gidx, const int lane) {
-    const Game g = load_game(a.info + gidx);
+    const Game g = game_of(a, gidx);
     GameScalars* sc = a.scal + gidx;
+
+    // every global load of the step is issued here, before any is used
+    const bool board = a.op != OP_CREATE && a.op != OP_RESET;
+    if (board) board_issue(a, g, s, lane);
+    uint4 s0 = make_uint4(0, 0, 0, 0), s1 = make_uint4(0, 0, 0, 0);
+    if (a.op != OP_CREATE) {
+        s0 = *reinterpret_cast<const uint4*>(sc);
+        s1 = *(reinterpret_cast<const uint4*>(sc) + 1);
+    }
+    // player `lane`'s action for the next step (frame 0: from the caller)
+    int32_t my_act = (a.op == OP_STEP && lane < g.P) ? a.actions[g.player_off + lane] : 0;
+    if (board) board_wait();
 
     uint32_t turn = 0, frame = 0, epoch = 0, alive = 0, finished = 0, invalid = 0, saturated = 0, err = 0;
     if (a.op != OP_CREATE) {
-        const uint4 s0 = *reinterpret_cast<const uint4*>(sc);
-        const uint4 s1 = *(reinterpret_cast<const uint4*>(sc) + 1);
         turn = s0.x;
         frame = s0.y;
         epoch = s0.z;
@@ -689,21 +745,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
 
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
-        generate(a, g, s, a.info[gidx].game_id, epoch, lane);
+        generate(a, g, s, game_id_of(a, gidx), epoch, lane);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
-    } else {
-        load_board(a, g, s, lane);
-        if (a.op == OP_DERIVE) {
-            derive_passable(g, s, lane);
-            wrote_state = true;
-        }
+    } else if (a.op == OP_DERIVE) {
+        derive_passable(g, s, lane);
+        wrote_state = true;
     }
-
-    // player `lane`'s action for the next step (frame 0: from the caller)
-    int32_t my_act = (a.op == OP_STEP && lane < g.P) ? a.actions[g.player_off + lane] : 0;
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
     for (int f = 0; f < frames; ++f) {
         float my_reward = 0.0f;
@@ -759,7 +809,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
             if (done) {
                 if (a.auto_reset) {
                     epoch += 1;
-                    generate(a, g, s, a.info[gidx].game_id, epoch, lane);
+                    generate(a, g, s, game_id_of(a, gidx), epoch, lane);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, lane);
@@ -793,7 +843,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
         } else if (a.next_actions) {
             output_pass<false, true>(a, g, s, alive, fin, lane, 0);
         }
-        if (a.next_actions) my_act = policy_pass<!MULTI>(a, g, s, alive, fin, frame, a.info[gidx].game_id, lane);
+        if (a.next_actions) my_act = policy_pass<!MULTI>(a, g, s, alive, fin, frame, game_id_of(a, gidx), lane);
     }
     if (MULTI && a.next_actions && lane < g.P) a.next_actions[g.player_off + lane] = my_act;
     if (wrote_state) {
@@ -845,9 +895,8 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
     int nw = (npad_max + 31) / 32;
     nw = (nw + 3) & ~3;
     if (nw_stride) *nw_stride = nw;
-    const int cnt_words = (pmax * (npad_max >> 4) + 1) / 2;
-    const int cnt_pad = (cnt_words + 3) & ~3;
-    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + 4 * cnt_pad + 4 * 24;
+    const int legal_words = (2 * pmax * (npad_max >> 4) + 3) & ~3;
+    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + 4 * legal_words + 4 * 24;
 }
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
