@@ -254,12 +254,12 @@ def run_ours(args, rank, world, local):
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv, copy_peak_gbps
-    from paper_2606_23348_gb300.workloads import workload
+    from paper_2606_23348_gb300.workloads import shard, workload
 
     torch.cuda.set_device(local)
     H, W, mode, P, gen, _ = workload(WORKLOAD)
     G = int(H.shape[0])
-    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=rank * G, **gen)
+    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
     if args.warps:
         env.set_launch(args.warps)
     out = env.new_outputs()
@@ -339,12 +339,12 @@ def run_rollout_workload(args, rank, world, local):
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
-    from paper_2606_23348_gb300.workloads import workload
+    from paper_2606_23348_gb300.workloads import shard, workload
 
     torch.cuda.set_device(local)
     H, W, mode, P, gen, _ = workload(args.workload)
     G = int(H.shape[0])
-    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=rank * G, **gen)
+    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
     tune = env.autotune(steps=3) if args.autotune else "off"
     K = args.rollout
     stream = torch.cuda.current_stream()

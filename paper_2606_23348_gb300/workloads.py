@@ -75,3 +75,9 @@ def random_actions(rng: np.random.Generator, N: np.ndarray, P: int = 8, p_pass: 
     a[bad] = rng.integers(-5, 5, size=int(bad.sum())) + np.where(rng.random(int(bad.sum())) < 0.5, 0,
                                                                 9 * np.repeat(N, P).reshape(G, P)[bad])
     return a.astype(np.int32)
+
+
+def shard(games_per_rank: int, rank: int) -> int:
+    """Global id of a rank's first game: ranks own disjoint, contiguous id
+    ranges, so no exchange is needed while stepping (weak scaling)."""
+    return int(rank) * int(games_per_rank)

@@ -104,3 +104,65 @@ def test_autotune_keeps_results():
         env.step_policy(acts, out, 3, acts)
         orc.step(a)
     compare_frame(env, out, orc, "after autotune")
+
+
+def _check_sampled(env, out, K, H, W, mode, P, gen, blocks, n, policy_seed, log=None):
+    """Replay sampled blocks of games in the oracle and compare every frame of the rollout buffer."""
+    import torch
+    pc, ps = int(env.layout.plane_cells), int(env.layout.player_slots)
+    for start in blocks:
+        orc = OracleEnv(H[start:start + n], W[start:start + n], mode[start:start + n], P[start:start + n],
+                        game_id_base=start, seed=1, **gen)
+        for k in range(K):
+            a = orc.policy(policy_seed)
+            orc.step(a)
+            for i in range(n):
+                g = start + i
+                for p in range(int(env.P[g])):
+                    ob = orc.observe(i, p)
+                    o = k * pc + int(env.plane_off[g]) + p * int(env.npad[g])
+                    nc = int(env.N[g])
+                    for key, name in (("obs_army", "army"), ("obs_owner", "owner"), ("obs_terrain", "terrain"),
+                                      ("obs_vis", "vis"), ("mask", "mask")):
+                        got = getattr(out, key)[o:o + nc].cpu().numpy()
+                        np.testing.assert_array_equal(got, ob[name], err_msg=f"frame {k} game {g} p{p} {key}")
+                s = orc.scalars(i)
+                assert int(out.done[k * env.G + g].cpu()) == s["done"]
+                if log is not None:
+                    so = k * ps + int(env.player_off[g])
+                    np.testing.assert_array_equal(log[so:so + int(env.P[g])].cpu().numpy(), a[i, :int(env.P[g])])
+
+
+def test_full_size_ragged_131072_resident_64_frames_sampled():
+    """The ragged 131,072-game workload in the form the benchmark times: one
+    resident 64-frame rollout; three blocks of 24 games replayed by the oracle."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import workload
+    H, W, mode, P, gen, _ = workload("1v1-131072-ragged15to30")
+    env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
+    K = 64
+    out = env.new_outputs(frames=K)
+    acts = env.new_actions()
+    log = torch.zeros(K * int(env.layout.player_slots), dtype=torch.int32, device="cuda")
+    env.policy(2, acts)
+    env.rollout(K, 2, acts, out, log, 0)
+    torch.cuda.synchronize()
+    _check_sampled(env, out, K, H, W, mode, P, gen, (0, 65536 - 12, 131072 - 24), 24, 2, log)
+
+
+def test_full_size_mixed_32768_sampled():
+    """The mixed 32,768-game workload (1v1 / 2v2 / FFA-8, sides 20..40, 15 size
+    buckets) stepped frame by frame; three blocks of 16 games replayed."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import workload
+    H, W, mode, P, gen, _ = workload("mixed-32768-sides20to40")
+    env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
+    K = 12
+    out = env.new_outputs(frames=K)
+    acts = env.new_actions()
+    env.policy(2, acts)
+    env.rollout(K, 2, acts, out, None, 2)  # plain launches, one per bucket per frame
+    torch.cuda.synchronize()
+    _check_sampled(env, out, K, H, W, mode, P, gen, (0, 16384, 32768 - 16), 16, 2)
