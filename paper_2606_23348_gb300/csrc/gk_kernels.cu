@@ -130,7 +130,7 @@ __device__ __forceinline__ uint32_t valid_bits(int N, int w) {
 
 // passable-neighbour bits of every cell (bits 2..5 of the terrain byte),
 // from a mountain bitset so that no lane reads a byte another lane writes
-__device__ void derive_passable(const Game& g, const Smem& s, int lane) {
+__device__ __noinline__ void derive_passable(const Game& g, const Smem& s, int lane) {
     const int N = g.N, W = g.W, H = g.H;
     for (int w = 0; w < g.nw; ++w) {
         const int c = 32 * w + lane;
@@ -152,7 +152,8 @@ __device__ void derive_passable(const Game& g, const Smem& s, int lane) {
 }
 
 // ---- map generator (Sec. IV-A) ----------------------------------------------
-__device__ void generate(const KArgs& a, const Game& g, const Smem& s, uint64_t gid, uint32_t epoch, int lane) {
+__device__ __noinline__ void generate(const KArgs& a, const Game& g, const Smem& s, uint64_t gid, uint32_t epoch,
+                                     int lane) {
     const int N = g.N, W = g.W, P = g.P;
     const uint64_t kmtn = hkey(a.seed, gid, epoch, 1);
     for (int c = lane; c < g.Npad; c += 32) {
