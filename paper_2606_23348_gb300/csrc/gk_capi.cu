@@ -393,6 +393,13 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
             return fail(GEN_ERR_BAD_ARG, "batch too large: more than 2^31 state cells");
         }
     }
+    {
+        const int trc = gk::init_tables();  // arguments are valid: now touch the device
+        if (trc != 0) {
+            free_env(e);
+            return cuda_fail((cudaError_t)trc, "device tables");
+        }
+    }
     e->state_cells = cell;
     e->plane_cells = plane;
     e->player_slots = slot;

@@ -98,6 +98,10 @@ int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out);
 // Returns a cudaError_t value.
 int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream);
 
+// Fill the device's constant tables (board column masks); once per device,
+// synchronous.  Returns a cudaError_t value.
+int init_tables();
+
 // 128-bit copy kernel used to measure the HBM roofline denominator.
 int launch_copy(const void* src, void* dst, size_t n16, int blocks, void* stream);
 

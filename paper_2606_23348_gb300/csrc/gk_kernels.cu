@@ -28,6 +28,8 @@
 // No floating point decides anything: all game arithmetic is integer.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "gk_internal.h"
 
 namespace gk {
@@ -432,16 +434,17 @@ __device__ __forceinline__ uint32_t cell_pass(const Game& g, const Smem& s, bool
 }
 
 // ---- board geometry: first and last column bitsets -------------------------
+// g_columns[W-1][0][w] has bit b set when cell 32w+b is in the first column
+// of a W-wide board, [1] the last column; filled once per device.
+constexpr int kColWords = (kMaxSide * kMaxSide) / 32;
+__device__ uint32_t g_columns[kMaxSide][2][kColWords];
+
 __device__ void column_pass(const Game& g, const Smem& s, int lane) {
-    const int N = g.N, W = g.W, nw = g.nw;
-    for (int w = lane; w < nw; w += 32) {
-        const int base = 32 * w;
-        uint32_t c0 = 0, cl = 0;
-        for (int c = ((base + W - 1) / W) * W; c < base + 32; c += W) c0 |= 1u << (c - base);
-        for (int c = ((base + W) / W) * W - 1; c < base + 32; c += W) cl |= 1u << (c - base);
-        const uint32_t v = valid_bits(N, w);
-        s.col0[w] = c0 & v;
-        s.colL[w] = cl & v;
+    const uint32_t* c0 = g_columns[g.W - 1][0];
+    const uint32_t* cl = g_columns[g.W - 1][1];
+    for (int w = lane; w < g.nw; w += 32) {
+        s.col0[w] = c0[w];
+        s.colL[w] = cl[w];
     }
     __syncwarp();
 }
@@ -886,6 +889,20 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
     }
 }
 
+__global__ void k_columns() {
+    const int W = blockIdx.x + 1;
+    for (int w = threadIdx.x; w < kColWords; w += blockDim.x) {
+        uint32_t c0 = 0, cl = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int c = 32 * w + b;
+            if (c % W == 0) c0 |= 1u << b;
+            if (c % W == W - 1) cl |= 1u << b;
+        }
+        g_columns[W - 1][0][w] = c0;
+        g_columns[W - 1][1][w] = cl;
+    }
+}
+
 __global__ void k_copy(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -920,8 +937,24 @@ int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
     return 0;
 }
 
+int init_tables() {
+    static std::mutex mu;
+    static bool ready[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && ready[dev]) return 0;
+    k_columns<<<kMaxSide, 128>>>();
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return (int)e;
+    if (dev >= 0 && dev < 64) ready[dev] = true;
+    return 0;
+}
+
 int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     if (a.n_items <= 0) return 0;
+
     const int smem = a.warp_smem * warps_per_cta;
     int blocks = (a.n_items + warps_per_cta - 1) / warps_per_cta;
     const bool multi = a.frames > 1 || a.action_log;

@@ -443,6 +443,10 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         return sfail(GEN_ERR_BAD_ARG, "max_cells %lld outside [16, 2^31 - 4096]", (long long)cfg->max_cells);
     if (cfg->max_plane_cells < 16) return sfail(GEN_ERR_BAD_ARG, "max_plane_cells below 16");
     if (cfg->budget_bytes < 4096) return sfail(GEN_ERR_BAD_ARG, "budget below 4 KiB");
+    {
+        const int trc = gk::init_tables();
+        if (trc != 0) return sfail(GEN_ERR_CUDA, "device tables: %s", cudaGetErrorString((cudaError_t)trc));
+    }
     gen_server* sv = new gen_server();
     cudaGetDevice(&sv->device);
     sv->prm = *p;
