@@ -62,6 +62,8 @@
 #define PURPOSE_GENERAL 2
 #define PURPOSE_CITY_POS 3
 #define PURPOSE_CITY_ARMY 4
+#define PURPOSE_NEAR_CASTLE_POS 5
+#define PURPOSE_NEAR_CASTLE_ARMY 6
 
 #define GEN_ATTEMPTS 64 /* R: bounded rejection attempts per level */
 
@@ -76,6 +78,9 @@ typedef struct orc_params {
     int32_t min_general_dist;/* >= 1: Manhattan D_min; <= 0: floor((H+W)/3) */
     int32_t max_turns;       /* 0 = no truncation */
     int32_t auto_reset;      /* 1 = regenerate finished games inside step */
+    int32_t max_general_dist;/* spawn-distance curriculum cap (0 = none) */
+    int32_t bfs_distance;    /* 1: spacing measured in BFS steps around mountains */
+    int32_t castle_radius;   /* > 0: each general gets a neutral castle this many steps away */
 } orc_params;
 
 typedef struct orc_game {
@@ -149,6 +154,29 @@ static int orc_dmin_for(const orc_params *prm, int H, int W) {
     return d < 1 ? 1 : d;
 }
 
+/* destination of a move from cell c in direction d (0 up, 1 down, 2 left,
+ * 3 right), or -1 when it leaves the board */
+static int orc_neighbour(const struct orc_game *g, int c, int d);
+
+/* BFS distance in steps from src through non-mountain cells (4-neighbours);
+ * -1 where unreachable.  queue holds N ints. */
+static void orc_bfs(const orc_game *g, int src, int *dist, int *queue) {
+    for (int c = 0; c < g->N; ++c) dist[c] = -1;
+    int head = 0, tail = 0;
+    dist[src] = 0;
+    queue[tail++] = src;
+    while (head < tail) {
+        int c = queue[head++];
+        for (int d = 0; d < 4; ++d) {
+            int n = orc_neighbour(g, c, d);
+            if (n >= 0 && g->terrain[n] != T_MOUNTAIN && dist[n] < 0) {
+                dist[n] = dist[c] + 1;
+                queue[tail++] = n;
+            }
+        }
+    }
+}
+
 /* ======================================================================
  * Map generator (Sec. IV-A; Q13, Q15).  Every draw is an integer from the
  * hash keyed by (seed, global game id, epoch, purpose).
@@ -171,6 +199,10 @@ static void orc_generate(const orc_params *prm, orc_game *g, uint64_t game_id) {
     uint64_t kgen = orc_key(prm->seed, game_id, g->epoch, PURPOSE_GENERAL);
     uint64_t i = 0;
     int D = orc_dmin_for(prm, H, W);
+    const int bfs = prm->bfs_distance != 0;
+    const int Dmax = prm->max_general_dist;  /* curriculum cap (Sec. V spawn-distance curriculum) */
+    int *dist = (int *)malloc(sizeof(int) * (size_t)N * (P + 1));  /* BFS from each placed general */
+    int *queue = dist + (size_t)N * P;
     for (int p = 0; p < P; ++p) {
         int placed = -1;
         while (placed < 0) {
@@ -181,22 +213,37 @@ static void orc_generate(const orc_params *prm, orc_game *g, uint64_t game_id) {
                     if (g->terrain[c] == T_MOUNTAIN) continue;
                     int ok = 1;
                     for (int q = 0; q < p; ++q) {
-                        int dist = orc_abs(c / W - g->gpos[q] / W) + orc_abs(c % W - g->gpos[q] % W);
-                        if (dist < D) ok = 0;
+                        int d = bfs ? dist[(size_t)q * N + c]
+                                    : orc_abs(c / W - g->gpos[q] / W) + orc_abs(c % W - g->gpos[q] % W);
+                        if (d < 0 || d < D) ok = 0;           /* unreachable or too close */
+                        if (Dmax > 0 && d > Dmax) ok = 0;     /* beyond the curriculum cap */
                     }
                     if (ok) placed = c;
                 }
                 if (placed < 0) D -= 1;
             } else {
-                for (int c = 0; c < N && placed < 0; ++c) {
-                    int taken = 0;
-                    for (int q = 0; q < p; ++q)
-                        if (g->gpos[q] == c) taken = 1;
-                    if (!taken) placed = c;
-                }
+                /* first row-major cell holding no general; in BFS mode first
+                 * try cells reachable from every earlier general within the
+                 * cap, then cells reachable from general 0, then any cell */
+                for (int pass = bfs ? 0 : 2; pass < 3 && placed < 0; ++pass)
+                    for (int c = 0; c < N && placed < 0; ++c) {
+                        int taken = 0;
+                        for (int q = 0; q < p; ++q)
+                            if (g->gpos[q] == c) taken = 1;
+                        if (taken) continue;
+                        if (pass < 2 && g->terrain[c] == T_MOUNTAIN) continue;
+                        int fits = 1;
+                        for (int q = 0; q < p; ++q) {
+                            const int d = dist[(size_t)q * N + c];
+                            if (pass == 0 && (d < 0 || (Dmax > 0 && d > Dmax))) fits = 0;
+                            if (pass == 1 && q == 0 && d < 0) fits = 0;
+                        }
+                        if (fits) placed = c;
+                    }
             }
         }
         g->gpos[p] = placed;
+        if (bfs) orc_bfs(g, placed, dist + (size_t)p * N, queue);
     }
     for (int p = P; p < MAXP; ++p) g->gpos[p] = -1;
     for (int p = 0; p < P; ++p) {
@@ -206,8 +253,12 @@ static void orc_generate(const orc_params *prm, orc_game *g, uint64_t game_id) {
     }
 
     /* 3. connectivity (Q15): an L-shaped path from general p to general p+1,
-     *    rows first, then columns; mountains on it become plain. */
-    for (int p = 0; p + 1 < P; ++p) {
+     *    rows first, then columns; mountains on it become plain.  In BFS mode
+     *    only when some general cannot reach general 0. */
+    int carve = !bfs;
+    for (int p = 1; p < P && bfs; ++p)
+        if (dist[g->gpos[p]] < 0) carve = 1;
+    for (int p = 0; carve && p + 1 < P; ++p) {
         int r = g->gpos[p] / W, c = g->gpos[p] % W;
         int r1 = g->gpos[p + 1] / W, c1 = g->gpos[p + 1] % W;
         while (r != r1) {
@@ -238,6 +289,35 @@ static void orc_generate(const orc_params *prm, orc_game *g, uint64_t game_id) {
             }
         }
     }
+
+    /* 5. castle near every general (Sec. IV-A): when no neutral castle lies
+     *    within castle_radius BFS steps, one is placed on the k-th free plain
+     *    cell (row-major) of that ball, k uniform. */
+    if (prm->castle_radius > 0) {
+        uint64_t knp = orc_key(prm->seed, game_id, g->epoch, PURPOSE_NEAR_CASTLE_POS);
+        uint64_t kna = orc_key(prm->seed, game_id, g->epoch, PURPOSE_NEAR_CASTLE_ARMY);
+        for (int p = 0; p < P; ++p) {
+            orc_bfs(g, g->gpos[p], dist, queue);
+            int have = 0, count = 0;
+            for (int c = 0; c < N; ++c) {
+                if (dist[c] < 0 || dist[c] > prm->castle_radius) continue;
+                if (g->terrain[c] == T_CASTLE && g->owner[c] == NEUTRAL) have = 1;
+                if (g->terrain[c] == T_PLAIN && g->owner[c] == NEUTRAL) count += 1;
+            }
+            if (have || count == 0) continue;
+            int k = orc_uniform(orc_draw(knp, (uint64_t)p), (uint32_t)count);
+            for (int c = 0; c < N; ++c) {
+                if (dist[c] < 0 || dist[c] > prm->castle_radius) continue;
+                if (g->terrain[c] != T_PLAIN || g->owner[c] != NEUTRAL) continue;
+                if (k-- == 0) {
+                    g->terrain[c] = T_CASTLE;
+                    g->army[c] = (int16_t)(prm->city_army_min + orc_uniform(orc_draw(kna, (uint64_t)p), span));
+                    break;
+                }
+            }
+        }
+    }
+    free(dist);
 
     g->turn = 0;
     g->alive = (P >= 32) ? 0xFFFFFFFFu : ((1u << P) - 1u);

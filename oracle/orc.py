@@ -35,6 +35,9 @@ class OracleParams(C.Structure):
         ("min_general_dist", C.c_int32),
         ("max_turns", C.c_int32),
         ("auto_reset", C.c_int32),
+        ("max_general_dist", C.c_int32),
+        ("bfs_distance", C.c_int32),
+        ("castle_radius", C.c_int32),
     ]
 
 
@@ -106,7 +109,7 @@ class OracleEnv:
 
     def __init__(self, H, W, mode, n_players, *, seed=1, game_id_base=0, mountain_thresh=858993459,
                  n_cities=8, city_per_mille=0, city_army_min=40, city_army_max=50, min_general_dist=0,
-                 max_turns=0, auto_reset=1):
+                 max_turns=0, auto_reset=1, max_general_dist=0, bfs_distance=0, castle_radius=0):
         self.lib = oracle_lib()
         self.H = np.ascontiguousarray(H, dtype=np.int32)
         self.W = np.ascontiguousarray(W, dtype=np.int32)
@@ -116,7 +119,8 @@ class OracleEnv:
         self.P = np.array([players_for(m, n) for m, n in zip(self.mode, self.n_players)], dtype=np.int32)
         self.N = (self.H * self.W).astype(np.int64)
         self.params = OracleParams(seed, game_id_base, mountain_thresh, n_cities, city_per_mille, city_army_min,
-                                   city_army_max, min_general_dist, max_turns, auto_reset)
+                                   city_army_max, min_general_dist, max_turns, auto_reset, max_general_dist,
+                                   bfs_distance, castle_radius)
         h = C.c_void_p()
         rc = self.lib.orc_env_new(C.byref(h), self.G, _ptr(self.H), _ptr(self.W), _ptr(self.mode),
                                   _ptr(self.n_players), C.byref(self.params))
