@@ -484,6 +484,43 @@ def run_served(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_generator(args, rank, world, local):
+    """Map generation throughput: gen_reset of every game of the default
+    workload's shapes, for each generator option set."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import workload
+
+    torch.cuda.set_device(local)
+    H, W, mode, P, gen, _ = workload(WORKLOAD)
+    G = int(H.shape[0])
+    res = {}
+    for name, opts in (("manhattan", {}), ("bfs", dict(bfs_distance=1, min_general_dist=17)),
+                       ("bfs+cap4", dict(bfs_distance=1, min_general_dist=1, max_general_dist=4)),
+                       ("bfs+castle6", dict(bfs_distance=1, min_general_dist=17, castle_radius=6))):
+        env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, **{**gen, **opts})
+        out = env.new_outputs()
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            env.reset(out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        n = max(3, min(args.steps, 20))
+        e0.record(stream)
+        for _ in range(n):
+            env.reset(out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        res[name] = {"maps_per_s": G / (ms * 1e-3), "ms_per_reset": ms}
+        del env, out
+    if rank == 0:
+        print(json.dumps({"metric": "maps/s (reset of every game, outputs written)", "value": res["manhattan"]["maps_per_s"],
+                          "unit": "maps/s", "n_gpus": world, "higher_is_better": True,
+                          "config": {"workload": "generator-65536x24x24", "games": G}, "forms": res}), flush=True)
+
+
 def len_buckets(env) -> int:
     """Size buckets of the batch (one launch each per frame)."""
     cls = set()
@@ -524,6 +561,8 @@ def main():
             run_ours(args, rank, world, local)
         elif args.workload == "served-256-clients":
             run_served(args, rank, world, local)
+        elif args.workload == "generator-65536x24x24":
+            run_generator(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

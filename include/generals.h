@@ -79,6 +79,9 @@ typedef struct gen_params {
     int32_t min_general_dist;  /* Manhattan spacing of generals; <= 0: floor((H+W)/3) */
     int32_t max_turns;         /* 0 = no truncation; else done code 2 at this turn */
     int32_t auto_reset;        /* 1: a finished game is regenerated inside gen_step */
+    int32_t max_general_dist;  /* spawn-distance curriculum cap (0 = none), Section V */
+    int32_t bfs_distance;      /* 1: general spacing in BFS steps around mountains ("17 steps") */
+    int32_t castle_radius;     /* > 0: a neutral castle within this many steps of every general (6) */
 } gen_params;
 
 /* Caller-provided device output buffers (sizes from gen_layout). */
@@ -209,6 +212,12 @@ int gen_read_state(gen_env *env, int16_t *h_army, int8_t *h_owner, int8_t *h_ter
  * gen_read_state; the error word is ignored).  Synchronous on `stream`. */
 int gen_write_state(gen_env *env, const int16_t *h_army, const int8_t *h_owner, const int8_t *h_terrain,
                     const uint32_t *h_scalars, void *stream);
+
+/* Change the spawn spacing of every later map of this environment (the
+ * spawn-distance curriculum of Section V raises max_dist over training):
+ * min_dist <= 0 keeps floor((H+W)/3), max_dist 0 removes the cap.  Takes
+ * effect at the next reset or auto-reset; synchronous. */
+int gen_set_spawn_range(gen_env *env, int min_dist, int max_dist);
 
 /* Launch shape of this environment's step kernel: games (warps) per CTA,
  * one of 1, 2, 4, 8 that fits the shared-memory limit.  Used by the

@@ -133,6 +133,8 @@ int check_params(const gen_params* p) {
         return fail(GEN_ERR_BAD_ARG, "city_per_mille %d outside [0, 1000]", p->city_per_mille);
     if (p->n_cities > 4096) return fail(GEN_ERR_BAD_ARG, "n_cities %d too large", p->n_cities);
     if (p->max_turns < 0) return fail(GEN_ERR_BAD_ARG, "max_turns < 0");
+    if (p->max_general_dist < 0 || p->castle_radius < 0 || p->castle_radius > 127)
+        return fail(GEN_ERR_BAD_ARG, "spawn cap %d or castle radius %d invalid", p->max_general_dist, p->castle_radius);
     return GEN_OK;
 }
 
@@ -180,6 +182,9 @@ KArgs base_args(const gen_env* e, const Bucket& b, int op) {
     a.seed = e->prm.seed;
     a.game_id_base = e->prm.game_id_base;
     a.mtn_thresh = e->prm.mountain_thresh;
+    a.spawn_dmax = e->prm.max_general_dist;
+    a.spawn_bfs = e->prm.bfs_distance ? 1 : 0;
+    a.castle_radius = e->prm.castle_radius;
     a.city_min = e->prm.city_army_min;
     a.city_span = e->prm.city_army_max - e->prm.city_army_min + 1;
     a.max_turns = e->prm.max_turns;
@@ -781,6 +786,21 @@ int gen_write_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, co
     int rc = launch_buckets(e, gk::OP_DERIVE, [](KArgs&) {}, stream, "derive launch");
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(s), "write_state sync");
+    return GEN_OK;
+}
+
+int gen_set_spawn_range(gen_env* e, int min_dist, int max_dist) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (max_dist < 0 || max_dist > 32767 || min_dist > 32767)
+        return fail(GEN_ERR_BAD_ARG, "spawn range [%d, %d] invalid", min_dist, max_dist);
+    e->prm.min_general_dist = min_dist;
+    e->prm.max_general_dist = max_dist;
+    for (auto& gi : e->h_info) {
+        const int d = min_dist >= 1 ? min_dist : (gi.H + gi.W) / 3;
+        gi.dmin = (int16_t)(d < 1 ? 1 : d);
+    }
+    CUDA_TRY(cudaMemcpy(e->d_info, e->h_info.data(), sizeof(GameInfo) * (size_t)e->G, cudaMemcpyHostToDevice),
+             "upload game table");
     return GEN_OK;
 }
 

@@ -84,6 +84,10 @@ struct KArgs {
     int32_t nw_stride;  // 32-bit words per bitset
     int32_t pmax;
     int32_t warp_smem;  // bytes per warp
+    // spawn options of the map generator (all zero: the plain generator)
+    int32_t spawn_dmax;     // cap on a general's distance to every earlier one (0: none)
+    int32_t spawn_bfs;      // 1: spacing in BFS steps around mountains
+    int32_t castle_radius;  // > 0: a neutral castle within this many steps of every general
 };
 
 // Bytes of shared memory one warp needs for games up to npad_max cells and

@@ -153,6 +153,393 @@ __device__ __noinline__ void derive_passable(const Game& g, const Smem& s, int l
     __syncwarp();
 }
 
+// ---- board geometry: first and last column bitsets -------------------------
+// g_columns[W-1][0][w] has bit b set when cell 32w+b is in the first column
+// of a W-wide board, [1] the last column; filled once per device.
+constexpr int kColWords = (kMaxSide * kMaxSide) / 32;
+__device__ uint32_t g_columns[kMaxSide][2][kColWords];
+
+__device__ __forceinline__ void column_pass(const Game& g, const Smem& s, int lane) {
+    const uint32_t* c0 = g_columns[g.W - 1][0];
+    const uint32_t* cl = g_columns[g.W - 1][1];
+    for (int w = lane; w < g.nw; w += 32) {
+        s.col0[w] = c0[w];
+        s.colL[w] = cl[w];
+    }
+    __syncwarp();
+}
+
+// ---- bitset BFS (generator options) ----------------------------------------
+// Word arrays of nw words in shared memory, one lane per word.  Bit c of
+// dilate4(x) is set when a 4-neighbour of cell c is set in x.
+__device__ void dilate4(const uint32_t* x, uint32_t* out, const Game& g, const Smem& s, int lane) {
+    const int nw = g.nw, q = g.W >> 5, sh = g.W & 31;
+    for (int w = lane; w < nw; w += 32) {
+        const uint32_t X = x[w];
+        const uint32_t Xm = w > 0 ? x[w - 1] : 0u, Xp = w + 1 < nw ? x[w + 1] : 0u;
+        const uint32_t L = (X << 1) | (Xm >> 31);  // bit c <- cell c-1
+        const uint32_t R = (X >> 1) | (Xp << 31);  // bit c <- cell c+1
+        uint32_t v = (L & ~s.col0[w]) | (R & ~s.colL[w]);
+        const int wa = w - q;  // bit c <- cell c-W
+        if (wa >= 0) v |= x[wa] << sh;
+        if (sh && wa - 1 >= 0) v |= x[wa - 1] >> (32 - sh);
+        const int wb = w + q;  // bit c <- cell c+W
+        if (wb < nw) v |= x[wb] >> sh;
+        if (sh && wb + 1 < nw) v |= x[wb + 1] << (32 - sh);
+        out[w] = v & valid_bits(g.N, w);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void set_single(uint32_t* x, int c, const Game& g, int lane) {
+    for (int w = lane; w < g.nw; w += 32) x[w] = (w == (c >> 5)) ? (1u << (c & 31)) : 0u;
+    __syncwarp();
+}
+
+// BFS from src through `pass`.  keep_out (when lo >= 0): cells within lo
+// steps leave `allowed`; then `allowed` keeps only cells within hi steps
+// (hi <= 0: all reachable cells).  vis / front / nxt are scratch.
+__device__ void bfs_restrict(int src, int lo, int hi, const uint32_t* pass, uint32_t* allowed, uint32_t* vis,
+                             uint32_t* front, uint32_t* nxt, const Game& g, const Smem& s, int lane) {
+    set_single(vis, src, g, lane);
+    set_single(front, src, g, lane);
+    bool cut = false;
+    if (lo == 0) {
+        for (int w = lane; w < g.nw; w += 32) allowed[w] &= ~vis[w];
+        cut = true;
+    }
+    for (int step = 1; hi <= 0 || step <= hi; ++step) {
+        dilate4(front, nxt, g, s, lane);
+        bool any = false;
+        for (int w = lane; w < g.nw; w += 32) {
+            const uint32_t n = nxt[w] & pass[w] & ~vis[w];
+            front[w] = n;
+            vis[w] |= n;
+            any |= n != 0u;
+        }
+        __syncwarp();
+        if (!__any_sync(kFull, any)) break;
+        if (step == lo) {
+            for (int w = lane; w < g.nw; w += 32) allowed[w] &= ~vis[w];
+            cut = true;
+        }
+    }
+    __syncwarp();
+    for (int w = lane; w < g.nw; w += 32) allowed[w] &= (lo >= 0 && !cut) ? 0u : vis[w];
+    __syncwarp();
+}
+
+// first set bit (row-major) of x, or -1
+__device__ int first_bit(const uint32_t* x, const Game& g, int lane) {
+    int best = 0x7FFFFFFF;
+    for (int w = lane; w < g.nw; w += 32)
+        if (x[w]) best = min(best, 32 * w + __ffs(x[w]) - 1);
+    best = (int)__reduce_min_sync(kFull, (unsigned)best);
+    return best == 0x7FFFFFFF ? -1 : best;
+}
+
+// cell of the k-th (0-based, row-major) set bit of x; x holds more than k bits
+__device__ int kth_bit(const uint32_t* x, uint32_t k, const Game& g, int lane) {
+    const int wpl = (g.nw + 31) >> 5, w0 = lane * wpl;
+    uint32_t mine = 0;
+    for (int w = w0; w < w0 + wpl && w < g.nw; ++w) mine += __popc(x[w]);
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int L = __ffs(__ballot_sync(kFull, incl > k)) - 1;
+    int cell = 0;
+    if (lane == L) {
+        uint32_t r = k - (incl - mine);
+        for (int w = w0; w < w0 + wpl && w < g.nw; ++w) {
+            uint32_t v = x[w];
+            const uint32_t n = __popc(v);
+            if (r >= n) {
+                r -= n;
+                continue;
+            }
+            for (uint32_t z = 0; z < r; ++z) v &= v - 1;
+            cell = 32 * w + __ffs(v) - 1;
+            break;
+        }
+    }
+    return __shfl_sync(kFull, cell, L);
+}
+
+// bitset of cells matching a predicate on (terrain type, owner), one ballot per word
+template <class Pred>
+__device__ void cell_bits(uint32_t* out, const Game& g, const Smem& s, int lane, Pred pred) {
+    for (int w = 0; w < g.nw; ++w) {
+        const int c = 32 * w + lane;
+        const bool b = c < g.N && pred(s.terrain[c] & 3, (int)s.owner[c]);
+        const unsigned m = __ballot_sync(kFull, b);
+        if (lane == 0) out[w] = m;
+    }
+    __syncwarp();
+}
+
+// ---- map generator with spawn options (Sec. IV-A) --------------------------
+// Scratch bitsets of the spawn options; the step rebuilds these arrays.
+struct GenScratch {
+    uint32_t *pass, *front, *nxt, *vis, *allowed, *gens;
+};
+__device__ __forceinline__ GenScratch gen_scratch(const Smem& s) {
+    const int st = s.stride;
+    return GenScratch{s.big, s.own, s.own + st, s.vis, s.vis + st, s.tmp};
+}
+
+// Generals at BFS distance (through non-mountain cells) in [D, dmax] of every
+// earlier general, D falling by one after each kGenAttempts rejected draws;
+// at D = 0 the first cell (row-major) within the cap of every earlier general,
+// else reachable from general 0, else any free cell.  Lane p returns player
+// p's general in the low 16 bits; bit 20 says whether a general cannot reach
+// general 0 (the L-path carve is then needed).
+__device__ __noinline__ int place_generals_bfs(const Game& g, const Smem& s, uint64_t kgen, int dmax, int lane) {
+    const int N = g.N, P = g.P;
+    const GenScratch z = gen_scratch(s);
+    column_pass(g, s, lane);
+    cell_bits(z.pass, g, s, lane, [](int t, int) { return t != kMountain; });
+    for (int w = lane; w < g.nw; w += 32) z.gens[w] = 0u;
+    __syncwarp();
+    uint32_t i = 0;
+    int D = g.dmin;
+    int my_gpos = -1;
+    for (int p = 0; p < P; ++p) {
+        int placed = -1;
+        while (placed < 0) {
+            if (D >= 1) {
+                for (int w = lane; w < g.nw; w += 32) z.allowed[w] = z.pass[w];
+                __syncwarp();
+                for (int q = 0; q < p; ++q)
+                    bfs_restrict(__shfl_sync(kFull, my_gpos, q), D - 1, dmax, z.pass, z.allowed, z.vis, z.front,
+                                 z.nxt, g, s, lane);
+                int found = -1;
+                for (int base = 0; base < kGenAttempts; base += 32) {
+                    const int t = base + lane;
+                    const int c = uniform_below(hdraw(kgen, (uint64_t)(i + t)), (uint32_t)N);
+                    const bool ok = t < kGenAttempts && ((z.allowed[c >> 5] >> (c & 31)) & 1u);
+                    const unsigned b = __ballot_sync(kFull, ok);
+                    if (b) {
+                        const int l = __ffs(b) - 1;
+                        found = base + l;
+                        placed = __shfl_sync(kFull, c, l);
+                        break;
+                    }
+                }
+                if (found >= 0) {
+                    i += (uint32_t)found + 1;
+                } else {
+                    i += kGenAttempts;
+                    D -= 1;
+                }
+            } else {
+                for (int w = lane; w < g.nw; w += 32) z.allowed[w] = z.pass[w] & ~z.gens[w];
+                __syncwarp();
+                for (int q = 0; q < p; ++q)
+                    bfs_restrict(__shfl_sync(kFull, my_gpos, q), -1, dmax, z.pass, z.allowed, z.vis, z.front, z.nxt,
+                                 g, s, lane);
+                placed = first_bit(z.allowed, g, lane);
+                if (placed < 0) {
+                    for (int w = lane; w < g.nw; w += 32) z.allowed[w] = z.pass[w] & ~z.gens[w];
+                    __syncwarp();
+                    if (p > 0)
+                        bfs_restrict(__shfl_sync(kFull, my_gpos, 0), -1, 0, z.pass, z.allowed, z.vis, z.front, z.nxt,
+                                     g, s, lane);
+                    placed = first_bit(z.allowed, g, lane);
+                }
+                if (placed < 0) {
+                    for (int w = lane; w < g.nw; w += 32) z.allowed[w] = ~z.gens[w] & valid_bits(N, w);
+                    __syncwarp();
+                    placed = first_bit(z.allowed, g, lane);
+                }
+            }
+        }
+        if (lane == p) my_gpos = placed;
+        if (lane == (placed >> 5)) z.gens[placed >> 5] |= 1u << (placed & 31);
+        __syncwarp();
+    }
+    bool carve = false;
+    if (P > 1) {
+        for (int w = lane; w < g.nw; w += 32) z.allowed[w] = z.gens[w];
+        __syncwarp();
+        bfs_restrict(__shfl_sync(kFull, my_gpos, 0), -1, 0, z.pass, z.allowed, z.vis, z.front, z.nxt, g, s, lane);
+        bool miss = false;
+        for (int w = lane; w < g.nw; w += 32) miss |= z.allowed[w] != z.gens[w];
+        carve = __any_sync(kFull, miss);
+    }
+    return (my_gpos & 0xFFFF) | (carve ? (1 << 20) : 0);
+}
+
+// A neutral castle within `radius` BFS steps of every general (s.misc holds
+// the generals): where none is, one on a free plain cell of the ball, the
+// k-th such cell in row-major order with k drawn uniformly.
+__device__ __noinline__ void castle_guarantee(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
+                                              uint32_t epoch, int radius, int lane) {
+    const GenScratch z = gen_scratch(s);
+    column_pass(g, s, lane);
+    uint32_t* free_plain = z.gens;
+    cell_bits(z.pass, g, s, lane, [](int t, int) { return t != kMountain; });
+    cell_bits(free_plain, g, s, lane, [](int t, int o) { return t == kPlain && o == -1; });
+    const uint64_t knp = hkey(a.seed, gid, epoch, 5);
+    const uint64_t kna = hkey(a.seed, gid, epoch, 6);
+    for (int p = 0; p < g.P; ++p) {
+        const int gp = s.misc[p];
+        cell_bits(z.allowed, g, s, lane, [](int t, int o) { return t == kCastle && o == -1; });
+        bfs_restrict(gp, -1, radius, z.pass, z.allowed, z.vis, z.front, z.nxt, g, s, lane);
+        bool have = false;
+        for (int w = lane; w < g.nw; w += 32) have |= z.allowed[w] != 0u;
+        if (__any_sync(kFull, have)) continue;
+        for (int w = lane; w < g.nw; w += 32) z.allowed[w] = free_plain[w] & z.vis[w];  // vis: the ball
+        __syncwarp();
+        uint32_t cnt = 0;
+        for (int w = lane; w < g.nw; w += 32) cnt += __popc(z.allowed[w]);
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (cnt == 0) continue;
+        const int cell = kth_bit(z.allowed, (uint32_t)uniform_below(hdraw(knp, (uint64_t)p), cnt), g, lane);
+        if (lane == 0) {
+            s.terrain[cell] = kCastle;
+            s.army[cell] = (int16_t)(a.city_min + uniform_below(hdraw(kna, (uint64_t)p), (uint32_t)a.city_span));
+        }
+        if (lane == (cell >> 5)) free_plain[cell >> 5] &= ~(1u << (cell & 31));
+        __syncwarp();
+    }
+}
+
+// The generator with spawn options (the launch's spawn_dmax, spawn_bfs,
+// castle_radius).  It is a separate function of a separate kernel
+// instantiation so that the options' register pressure never reaches the
+// step kernel that runs without them.
+__device__ __noinline__ void generate_spawn(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
+                                           uint32_t epoch, int lane) {
+    const int N = g.N, W = g.W, P = g.P;
+    const uint64_t kmtn = hkey(a.seed, gid, epoch, 1);
+    for (int c = lane; c < g.Npad; c += 32) {
+        bool m = c < N && hdraw(kmtn, (uint64_t)c) < a.mtn_thresh;
+        s.army[c] = 0;
+        s.owner[c] = -1;
+        s.terrain[c] = m ? kMountain : kPlain;
+    }
+    __syncwarp();
+
+    // generals: 32 candidate draws evaluated at once; the first accepted in
+    // draw order wins, so the draw counter advances exactly as one by one
+    const uint64_t kgen = hkey(a.seed, gid, epoch, 2);
+    const int dmax = a.spawn_dmax;
+    int my_gpos = -1;  // lane p holds player p's general
+    bool carve = true;
+    if (a.spawn_bfs) {
+        const int r = place_generals_bfs(g, s, kgen, dmax, lane);
+        my_gpos = lane < P ? (r & 0xFFFF) : -1;
+        carve = (r >> 20) & 1;
+    } else {
+        uint32_t i = 0;
+        int D = g.dmin;
+        for (int p = 0; p < P; ++p) {
+            int placed = -1;
+            while (placed < 0) {
+                if (D >= 1) {
+                    int found = -1;
+                    for (int base = 0; base < kGenAttempts; base += 32) {
+                        int t = base + lane;
+                        int c = uniform_below(hdraw(kgen, (uint64_t)(i + t)), (uint32_t)N);
+                        bool ok = (t < kGenAttempts) && s.terrain[c] != kMountain;
+                        int rc = c / W, cc = c - rc * W;
+                        for (int q = 0; q < p; ++q) {
+                            int gq = __shfl_sync(kFull, my_gpos, q);
+                            int rq = gq / W, cq = gq - rq * W;
+                            const int d = abs(rc - rq) + abs(cc - cq);
+                            if (d < D || (dmax > 0 && d > dmax)) ok = false;
+                        }
+                        unsigned b = __ballot_sync(kFull, ok);
+                        if (b) {
+                            int l = __ffs(b) - 1;
+                            found = base + l;
+                            placed = __shfl_sync(kFull, c, l);
+                            break;
+                        }
+                    }
+                    if (found >= 0) {
+                        i += (uint32_t)found + 1;
+                    } else {
+                        i += kGenAttempts;
+                        D -= 1;
+                    }
+                } else {
+                    for (int base = 0; base < N && placed < 0; base += 32) {
+                        int c = base + lane;
+                        bool ok = c < N;
+                        for (int q = 0; q < p; ++q)
+                            if (__shfl_sync(kFull, my_gpos, q) == c) ok = false;
+                        unsigned b = __ballot_sync(kFull, ok);
+                        if (b) placed = base + __ffs(b) - 1;
+                    }
+                }
+            }
+            if (lane == p) my_gpos = placed;
+        }
+    }
+    if (lane < P) {
+        s.terrain[my_gpos] = kGeneral;
+        s.owner[my_gpos] = (int8_t)lane;
+        s.army[my_gpos] = 1;
+        s.misc[lane] = my_gpos;
+    }
+    __syncwarp();
+
+    // L-path rows first, then columns, between consecutive generals (in BFS
+    // mode only when some general cannot reach general 0)
+    if (carve && lane == 0) {
+        for (int p = 0; p + 1 < P; ++p) {
+            int r = s.misc[p] / W, c = s.misc[p] % W;
+            int r1 = s.misc[p + 1] / W, c1 = s.misc[p + 1] % W;
+            while (r != r1) {
+                r += (r1 > r) ? 1 : -1;
+                if (s.terrain[r * W + c] == kMountain) s.terrain[r * W + c] = kPlain;
+            }
+            while (c != c1) {
+                c += (c1 > c) ? 1 : -1;
+                if (s.terrain[r * W + c] == kMountain) s.terrain[r * W + c] = kPlain;
+            }
+        }
+    }
+    __syncwarp();
+
+    // neutral castles on neutral plain cells
+    const uint64_t kpos = hkey(a.seed, gid, epoch, 3);
+    const uint64_t karm = hkey(a.seed, gid, epoch, 4);
+    uint32_t j = 0;
+    for (int k = 0; k < g.n_cities; ++k) {
+        int found = -1, cell = 0;
+        for (int base = 0; base < kGenAttempts; base += 32) {
+            int t = base + lane;
+            int c = uniform_below(hdraw(kpos, (uint64_t)(j + t)), (uint32_t)N);
+            bool ok = (t < kGenAttempts) && s.terrain[c] == kPlain && s.owner[c] == -1;
+            unsigned b = __ballot_sync(kFull, ok);
+            if (b) {
+                int l = __ffs(b) - 1;
+                found = base + l;
+                cell = __shfl_sync(kFull, c, l);
+                break;
+            }
+        }
+        if (found >= 0) {
+            j += (uint32_t)found + 1;
+            if (lane == 0) {
+                s.terrain[cell] = kCastle;
+                s.army[cell] = (int16_t)(a.city_min + uniform_below(hdraw(karm, (uint64_t)k), (uint32_t)a.city_span));
+            }
+            __syncwarp();
+        } else {
+            j += kGenAttempts;
+        }
+    }
+
+    if (a.castle_radius > 0) castle_guarantee(a, g, s, gid, epoch, a.castle_radius, lane);
+    derive_passable(g, s, lane);
+}
+
 // ---- map generator (Sec. IV-A) ----------------------------------------------
 __device__ __noinline__ void generate(const KArgs& a, const Game& g, const Smem& s, uint64_t gid, uint32_t epoch,
                                      int lane) {
@@ -433,22 +820,6 @@ __device__ __forceinline__ uint32_t cell_pass(const Game& g, const Smem& s, bool
     return chunk_pass<8>(g, s, grow_s, grow_p, lane);
 }
 
-// ---- board geometry: first and last column bitsets -------------------------
-// g_columns[W-1][0][w] has bit b set when cell 32w+b is in the first column
-// of a W-wide board, [1] the last column; filled once per device.
-constexpr int kColWords = (kMaxSide * kMaxSide) / 32;
-__device__ uint32_t g_columns[kMaxSide][2][kColWords];
-
-__device__ void column_pass(const Game& g, const Smem& s, int lane) {
-    const uint32_t* c0 = g_columns[g.W - 1][0];
-    const uint32_t* cl = g_columns[g.W - 1][1];
-    for (int w = lane; w < g.nw; w += 32) {
-        s.col0[w] = c0[w];
-        s.colL[w] = cl[w];
-    }
-    __syncwarp();
-}
-
 // ---- fog: 3x3 dilation of the (team) ownership bitset (Sec. IV-B) ----------
 // Also counts each player's land for the scoreboard.
 __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane) {
@@ -716,7 +1087,7 @@ __device__ __forceinline__ uint64_t game_id_of(const KArgs& a, int gidx) {
     return a.uniform ? a.game_id_base + (uint64_t)gidx : a.info[gidx].game_id;
 }
 
-template <bool MULTI>
+template <bool MULTI, bool SPAWN>
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const int gidx, const int lane) {
     const Game g = game_of(a, gidx);
     GameScalars* sc = a.scal + gidx;
@@ -749,7 +1120,10 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
 
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
-        generate(a, g, s, game_id_of(a, gidx), epoch, lane);
+        if constexpr (SPAWN)
+            generate_spawn(a, g, s, game_id_of(a, gidx), epoch, lane);
+        else
+            generate(a, g, s, game_id_of(a, gidx), epoch, lane);
         turn = 0;
         alive = all_alive;
         finished = 0;
@@ -813,7 +1187,10 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
             if (done) {
                 if (a.auto_reset) {
                     epoch += 1;
-                    generate(a, g, s, game_id_of(a, gidx), epoch, lane);
+                    if constexpr (SPAWN)
+                        generate_spawn(a, g, s, game_id_of(a, gidx), epoch, lane);
+                    else
+                        generate(a, g, s, game_id_of(a, gidx), epoch, lane);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, lane);
@@ -866,7 +1243,8 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
 
 // One warp per game; warps walk the item list with a grid stride.  MULTI:
 // several frames per launch (rollouts) with the board kept in shared memory.
-template <bool MULTI>
+// SPAWN: the map generator with spawn options.
+template <bool MULTI, bool SPAWN>
 __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
     extern __shared__ __align__(16) char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -878,14 +1256,14 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
         if (item >= a.n_items) return;
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) return;
-        run_game<MULTI>(a, s, gidx, lane);
+        run_game<MULTI, SPAWN>(a, s, gidx, lane);
         return;
     }
     for (int item = blockIdx.x * wpc + wid; item < a.n_items; item += gridDim.x * wpc) {
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) continue;
         __syncwarp();
-        run_game<MULTI>(a, s, gidx, lane);
+        run_game<MULTI, SPAWN>(a, s, gidx, lane);
     }
 }
 
@@ -921,14 +1299,15 @@ int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
     static int configured = 48 * 1024;  // only ever raised, so every env's launches stay legal
     cudaError_t e = cudaSuccess;
     if (smem_bytes > configured) {
-        e = cudaFuncSetAttribute(k_generals<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_generals<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        const void* fns[4] = {(const void*)k_generals<false, false>, (const void*)k_generals<true, false>,
+                              (const void*)k_generals<false, true>, (const void*)k_generals<true, true>};
+        for (const void* f : fns)
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
         if (e != cudaSuccess) return (int)e;
         configured = smem_bytes;
     }
     int per_sm = 0, dev = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false>, 32 * warps_per_cta,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false>, 32 * warps_per_cta,
                                                            smem_bytes)) != cudaSuccess)
         return (int)e;
     cudaGetDevice(&dev);
@@ -960,10 +1339,17 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     const bool multi = a.frames > 1 || a.action_log;
     // multi-frame launches: a grid of many waves, warps stride over any items beyond it
     if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
-    if (multi)
-        k_generals<true><<<blocks, 32 * warps_per_cta, smem, (cudaStream_t)stream>>>(a);
+    const bool spawn = a.spawn_dmax > 0 || a.spawn_bfs || a.castle_radius > 0;
+    const dim3 grid(blocks), block(32 * warps_per_cta);
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (multi && spawn)
+        k_generals<true, true><<<grid, block, smem, st>>>(a);
+    else if (multi)
+        k_generals<true, false><<<grid, block, smem, st>>>(a);
+    else if (spawn)
+        k_generals<false, true><<<grid, block, smem, st>>>(a);
     else
-        k_generals<false><<<blocks, 32 * warps_per_cta, smem, (cudaStream_t)stream>>>(a);
+        k_generals<false, false><<<grid, block, smem, st>>>(a);
     return (int)cudaGetLastError();
 }
 

@@ -251,6 +251,9 @@ KArgs server_args(gen_server* sv, int op, const ClassShape& c) {
     a.policy_seed = sv->policy_seed;
     a.seed = sv->prm.seed;
     a.mtn_thresh = sv->prm.mountain_thresh;
+    a.spawn_dmax = std::max(sv->prm.max_general_dist, 0);
+    a.spawn_bfs = sv->prm.bfs_distance ? 1 : 0;
+    a.castle_radius = std::max(sv->prm.castle_radius, 0);
     a.city_min = sv->prm.city_army_min;
     a.city_span = sv->prm.city_army_max - sv->prm.city_army_min + 1;
     a.max_turns = sv->prm.max_turns;
@@ -443,6 +446,8 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         return sfail(GEN_ERR_BAD_ARG, "max_cells %lld outside [16, 2^31 - 4096]", (long long)cfg->max_cells);
     if (cfg->max_plane_cells < 16) return sfail(GEN_ERR_BAD_ARG, "max_plane_cells below 16");
     if (cfg->budget_bytes < 4096) return sfail(GEN_ERR_BAD_ARG, "budget below 4 KiB");
+    if (p->max_general_dist < 0 || p->castle_radius < 0 || p->castle_radius > 127)
+        return sfail(GEN_ERR_BAD_ARG, "spawn cap %d or castle radius %d invalid", p->max_general_dist, p->castle_radius);
     {
         const int trc = gk::init_tables();
         if (trc != 0) return sfail(GEN_ERR_CUDA, "device tables: %s", cudaGetErrorString((cudaError_t)trc));

@@ -33,6 +33,9 @@ class GenParams(C.Structure):
         ("min_general_dist", C.c_int32),
         ("max_turns", C.c_int32),
         ("auto_reset", C.c_int32),
+        ("max_general_dist", C.c_int32),
+        ("bfs_distance", C.c_int32),
+        ("castle_radius", C.c_int32),
     ]
 
 
@@ -55,7 +58,7 @@ class GenLayoutInfo(C.Structure):
 EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "gen_reset", "gen_observe",
            "gen_step", "gen_step_policy", "gen_policy", "gen_rollout", "gen_step_host", "gen_read_state",
            "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
-           "gen_step_host_static")
+           "gen_step_host_static", "gen_set_spawn_range")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -88,6 +91,7 @@ def load_library(path: str = LIB_PATH):
             "gen_read_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "gen_write_state": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "gen_set_launch": (C.c_int, [vp, C.c_int]),
+            "gen_set_spawn_range": (C.c_int, [vp, C.c_int, C.c_int]),
             "gen_copy_peak": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
@@ -259,6 +263,9 @@ class GeneralsEnv:
         _check(self.lib.gen_step_host_static(self.h, C.c_void_p(h_actions.data_ptr()), C.byref(h_out.struct),
                                              int(policy_seed), nxt, stream or _cur_stream()),
                "gen_step_host_static")
+
+    def set_spawn_range(self, min_dist: int, max_dist: int):
+        _check(self.lib.gen_set_spawn_range(self.h, int(min_dist), int(max_dist)), "gen_set_spawn_range")
 
     def set_launch(self, warps_per_cta: int):
         _check(self.lib.gen_set_launch(self.h, int(warps_per_cta)), "gen_set_launch")

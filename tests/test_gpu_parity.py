@@ -235,3 +235,35 @@ def test_full_size_24x24_65536_sampled():
                                   ("obs_vis", "vis"), ("mask", "mask")):
                     o = int(env.plane_off[g]) + p * 576
                     np.testing.assert_array_equal(getattr(out, key)[o:o + 576].cpu().numpy(), ob[name])
+
+
+@pytest.mark.parametrize("opts", [
+    dict(bfs_distance=1),
+    dict(bfs_distance=1, max_general_dist=4, min_general_dist=1),
+    dict(bfs_distance=1, castle_radius=6),
+    dict(bfs_distance=0, castle_radius=6, max_general_dist=9),
+    dict(bfs_distance=1, castle_radius=3, max_general_dist=6, mountain_thresh=0x60000000),
+], ids=["bfs", "bfs-cap4", "bfs-castle6", "manhattan-castle6-cap9", "bfs-dense-mountains"])
+def test_generator_options_match_oracle(opts):
+    """Spawn spacing in BFS steps, the curriculum cap and the castle guarantee,
+    over mixed modes and sizes, through many resets."""
+    G = 64
+    H, W, mode, P = shapes(G, (4, 26), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=21)
+    P = np.where(mode == 2, np.minimum(P, H * W), P).astype(np.int32)
+    kw = dict(seed=17, n_cities=3, max_turns=30, **opts)
+    env, orc = pair(H, W, mode, P, **kw)
+    rollout_policy(env, orc, 70, policy_seed=5, check_every=2, tag=str(opts))
+
+
+def test_spawn_range_curriculum_update():
+    import torch
+    G = 48
+    H, W, mode, P = shapes(G, (10, 20), seed=4)
+    kw = dict(seed=3, n_cities=4, bfs_distance=1, castle_radius=6)
+    env, _ = pair(H, W, mode, P, max_general_dist=4, min_general_dist=1, **kw)
+    out = env.new_outputs()
+    env.set_spawn_range(2, 9)  # the curriculum widens
+    env.reset(out)
+    orc = OracleEnv(H, W, mode, P, max_general_dist=9, min_general_dist=2, **kw)
+    orc.reset()
+    compare_frame(env, out, orc, "after widening", check_reward=False)
