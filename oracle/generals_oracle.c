@@ -36,6 +36,7 @@
  * tried action by action, generator statistics and BFS connectivity, policy
  * uniformity, and invariants over exhaustive joint actions on 3x3 boards.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -689,4 +690,234 @@ void orc_set_game(orc_env *e, int32_t g, const int16_t *army, const int8_t *owne
     for (int p = 0; p < MAXP; ++p) gm->gpos[p] = -1;
     for (int c = 0; c < gm->N; ++c)
         if (terrain[c] == T_GENERAL && owner[c] >= 0) gm->gpos[(int)owner[c]] = c;
+}
+
+/* ======================================================================
+ * Feature tensor (Appendix A, Table "Observation channels"): per player
+ * C = 24 + 2 * hist float channels over the game's own H x W cells, in the
+ * table's order.  Persistent memory (rows 4-8, 20-21) and the army-delta
+ * history (rows 24 on) accumulate over the frames the builder is run on and
+ * are cleared when the game's epoch changes (a new episode).  Readings
+ * (Q26-Q33 in the design notes):
+ *   Q26 "opponent" = a player of another team (1v1 and FFA: any other
+ *       player; 2v2: the other team); an ally's cells appear only in
+ *       row 0 (armies) of the instantaneous rows;
+ *   Q27 enemy_army (row 2) and the enemy deltas use the fogged view: army
+ *       on VISIBLE opponent cells, 0 elsewhere; own_army is the agent's
+ *       own cells (always visible to a living agent);
+ *   Q28 neutral_cells (row 9) = visible, unowned and not a mountain;
+ *   Q29 structures_in_fog (row 13) = fogged and either shown as an
+ *       obstacle by the fogged observation (mountain or castle) or a
+ *       remembered general;
+ *   Q30 rows 16-19 come from the public scoreboard (Sec. IV-B): own land
+ *       and army, summed land and army of the opponents;
+ *   Q31 last_enemy_army_seen (row 20) takes the enemy army of a cell each
+ *       frame the cell is visible (0 when visible without an enemy) and
+ *       keeps it while fogged; last_enemy_army_age (row 21) is
+ *       log(1 + dt) / 5 with dt = turns since an enemy was last seen on
+ *       the cell, 0 when the cell is visible or no enemy was ever seen
+ *       there in this episode;
+ *   Q32 coords: column / (W - 1) and row / (H - 1), 0 when the side is 1;
+ *       each game uses its own H x W, so no padded border exists;
+ *   Q33 deltas: row 24 + k = own(t - k) - own(t - k - 1) for k = 0 ..
+ *       hist - 1 over consecutive builder frames; frames before the
+ *       episode count as all-zero planes.  Row 14 is the turn counter.
+ * Float rows are evaluated in double and rounded to float once.
+ * ====================================================================== */
+
+typedef struct orc_pmem {
+    int64_t epoch;          /* epoch folded in last; -1: none yet */
+    int64_t frame;          /* frame folded in last */
+    uint8_t *seen, *enemy_seen, *generals, *castles, *mountains; /* [N] */
+    int32_t *last_enemy_army; /* [N] */
+    int32_t *last_enemy_turn; /* [N], meaningful where enemy_seen */
+    int32_t *own_hist;      /* [hist + 1][N]: [k] = own army plane of the k-th latest folded frame */
+    int32_t *enemy_hist;    /* [hist + 1][N] */
+} orc_pmem;
+
+typedef struct orc_feat {
+    const orc_env *e;       /* read by orc_feat_build only */
+    int32_t G, hist;
+    int32_t *P;             /* [G] players per game, kept for orc_feat_free */
+    orc_pmem *mem;          /* [G][MAXP] */
+} orc_feat;
+
+static int orc_is_opponent(const orc_game *g, int p, int o) {
+    return o >= 0 && orc_team(g, o) != orc_team(g, p);
+}
+
+int orc_feat_new(orc_feat **out, const orc_env *e, int32_t hist) {
+    *out = NULL;
+    if (hist < 1 || hist > 16) return -1;
+    orc_feat *f = (orc_feat *)calloc(1, sizeof(orc_feat));
+    f->e = e;
+    f->G = e->G;
+    f->hist = hist;
+    f->P = (int32_t *)calloc((size_t)(e->G > 0 ? e->G : 1), sizeof(int32_t));
+    for (int g = 0; g < e->G; ++g) f->P[g] = e->games[g].P;
+    f->mem = (orc_pmem *)calloc((size_t)(e->G > 0 ? e->G : 1) * MAXP, sizeof(orc_pmem));
+    for (int g = 0; g < e->G; ++g)
+        for (int p = 0; p < e->games[g].P; ++p) {
+            orc_pmem *m = &f->mem[g * MAXP + p];
+            size_t n = (size_t)e->games[g].N;
+            m->epoch = -1;
+            m->frame = -1;
+            m->seen = (uint8_t *)calloc(n, 1);
+            m->enemy_seen = (uint8_t *)calloc(n, 1);
+            m->generals = (uint8_t *)calloc(n, 1);
+            m->castles = (uint8_t *)calloc(n, 1);
+            m->mountains = (uint8_t *)calloc(n, 1);
+            m->last_enemy_army = (int32_t *)calloc(n, sizeof(int32_t));
+            m->last_enemy_turn = (int32_t *)calloc(n, sizeof(int32_t));
+            m->own_hist = (int32_t *)calloc(n * (size_t)(hist + 1), sizeof(int32_t));
+            m->enemy_hist = (int32_t *)calloc(n * (size_t)(hist + 1), sizeof(int32_t));
+        }
+    *out = f;
+    return 0;
+}
+
+void orc_feat_free(orc_feat *f) {
+    if (!f) return;
+    for (int g = 0; g < f->G; ++g)
+        for (int p = 0; p < f->P[g]; ++p) {
+            orc_pmem *m = &f->mem[g * MAXP + p];
+            free(m->seen);
+            free(m->enemy_seen);
+            free(m->generals);
+            free(m->castles);
+            free(m->mountains);
+            free(m->last_enemy_army);
+            free(m->last_enemy_turn);
+            free(m->own_hist);
+            free(m->enemy_hist);
+        }
+    free(f->mem);
+    free(f->P);
+    free(f);
+}
+
+/* features of player p of game g into out[C][N]; folds the current frame
+ * into the player's memory first (once per frame) */
+static void orc_feat_player(orc_feat *f, int gi, int p, float *out) {
+    const orc_game *g = &f->e->games[gi];
+    orc_pmem *m = &f->mem[gi * MAXP + p];
+    const int N = g->N, W = g->W, H = g->H, hist = f->hist;
+    float *ch[64];
+    for (int k = 0; k < 24 + 2 * hist; ++k) ch[k] = out + (size_t)k * N;
+
+    /* current frame, fogged as the observation shows it */
+    int32_t *own = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    int32_t *enemy = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    uint8_t *vis = (uint8_t *)calloc((size_t)N, 1);
+    for (int c = 0; c < N; ++c) {
+        vis[c] = (uint8_t)orc_sees(g, p, c);
+        own[c] = g->owner[c] == p ? g->army[c] : 0;
+        enemy[c] = (vis[c] && orc_is_opponent(g, p, g->owner[c])) ? g->army[c] : 0;
+    }
+
+    /* a new episode clears the memory (Q33: the past counts as zero) */
+    if (m->epoch != (int64_t)g->epoch) {
+        memset(m->seen, 0, (size_t)N);
+        memset(m->enemy_seen, 0, (size_t)N);
+        memset(m->generals, 0, (size_t)N);
+        memset(m->castles, 0, (size_t)N);
+        memset(m->mountains, 0, (size_t)N);
+        memset(m->last_enemy_army, 0, sizeof(int32_t) * (size_t)N);
+        memset(m->last_enemy_turn, 0, sizeof(int32_t) * (size_t)N);
+        memset(m->own_hist, 0, sizeof(int32_t) * (size_t)N * (size_t)(hist + 1));
+        memset(m->enemy_hist, 0, sizeof(int32_t) * (size_t)N * (size_t)(hist + 1));
+        m->epoch = (int64_t)g->epoch;
+        m->frame = -1;
+    }
+    const int fold = m->frame != (int64_t)g->frame;
+
+    /* rows 4-8, 20: what this frame reveals (Q31) */
+    if (fold)
+        for (int c = 0; c < N; ++c) {
+            if (!vis[c]) continue;
+            m->seen[c] = 1;
+            if (orc_is_opponent(g, p, g->owner[c])) {
+                m->enemy_seen[c] = 1;
+                m->last_enemy_turn[c] = g->turn;
+            }
+            if (g->terrain[c] == T_GENERAL) m->generals[c] = 1;
+            if (g->terrain[c] == T_CASTLE) m->castles[c] = 1;
+            if (g->terrain[c] == T_MOUNTAIN) m->mountains[c] = 1;
+            m->last_enemy_army[c] = enemy[c];
+        }
+    /* history: the folded frame becomes plane 0, older planes move back */
+    if (fold) {
+        for (int k = hist; k >= 1; --k) {
+            memcpy(m->own_hist + (size_t)k * N, m->own_hist + (size_t)(k - 1) * N, sizeof(int32_t) * (size_t)N);
+            memcpy(m->enemy_hist + (size_t)k * N, m->enemy_hist + (size_t)(k - 1) * N, sizeof(int32_t) * (size_t)N);
+        }
+        memcpy(m->own_hist, own, sizeof(int32_t) * (size_t)N);
+        memcpy(m->enemy_hist, enemy, sizeof(int32_t) * (size_t)N);
+        m->frame = (int64_t)g->frame;
+    }
+
+    /* scoreboard (Q30) */
+    int32_t land[MAXP], army[MAXP];
+    orc_scoreboard(g, land, army);
+    int64_t opp_land = 0, opp_army = 0;
+    for (int q = 0; q < g->P; ++q)
+        if (orc_is_opponent(g, p, q)) {
+            opp_land += land[q];
+            opp_army += army[q];
+        }
+
+    for (int c = 0; c < N; ++c) {
+        const int r = c / W, col = c % W, o = g->owner[c], t = g->terrain[c];
+        const int v = vis[c];
+        ch[0][c] = (float)(v ? g->army[c] : 0);
+        ch[1][c] = (float)own[c];
+        ch[2][c] = (float)enemy[c];
+        ch[3][c] = (float)((v && o == NEUTRAL) ? g->army[c] : 0);
+        ch[4][c] = (float)m->seen[c];
+        ch[5][c] = (float)m->enemy_seen[c];
+        ch[6][c] = (float)m->generals[c];
+        ch[7][c] = (float)m->castles[c];
+        ch[8][c] = (float)m->mountains[c];
+        ch[9][c] = (float)(v && o == NEUTRAL && t != T_MOUNTAIN);
+        ch[10][c] = (float)(o == p);
+        ch[11][c] = (float)(v && orc_is_opponent(g, p, o));
+        ch[12][c] = (float)(!v);
+        ch[13][c] = (float)(!v && (t == T_MOUNTAIN || t == T_CASTLE || m->generals[c]));
+        ch[14][c] = (float)g->turn;
+        ch[15][c] = (float)((double)(g->turn % 50) / 50.0);
+        ch[16][c] = (float)land[p];
+        ch[17][c] = (float)army[p];
+        ch[18][c] = (float)opp_land;
+        ch[19][c] = (float)opp_army;
+        ch[20][c] = (float)m->last_enemy_army[c];
+        {
+            int dt = 0;
+            if (!v && m->enemy_seen[c]) dt = g->turn - m->last_enemy_turn[c];
+            ch[21][c] = (float)(log(1.0 + (double)dt) / 5.0);
+        }
+        ch[22][c] = (float)(W > 1 ? (double)col / (double)(W - 1) : 0.0);
+        ch[23][c] = (float)(H > 1 ? (double)r / (double)(H - 1) : 0.0);
+        /* deltas (Q33) between consecutive folded frames */
+        for (int k = 0; k < hist; ++k) {
+            ch[24 + k][c] = (float)(m->own_hist[(size_t)k * N + c] - m->own_hist[(size_t)(k + 1) * N + c]);
+            ch[24 + hist + k][c] =
+                (float)(m->enemy_hist[(size_t)k * N + c] - m->enemy_hist[(size_t)(k + 1) * N + c]);
+        }
+    }
+
+    free(own);
+    free(enemy);
+    free(vis);
+}
+
+/* every game and player, in order: out holds sum over games of P * C * N
+ * floats, game g's player p at [C][N] after those of earlier pairs */
+void orc_feat_build(orc_feat *f, float *out) {
+    const int C = 24 + 2 * f->hist;
+    size_t off = 0;
+    for (int g = 0; g < f->e->G; ++g)
+        for (int p = 0; p < f->e->games[g].P; ++p) {
+            orc_feat_player(f, g, p, out + off);
+            off += (size_t)C * (size_t)f->e->games[g].N;
+        }
 }

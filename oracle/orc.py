@@ -46,7 +46,7 @@ def build_oracle(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -77,6 +77,10 @@ def oracle_lib():
             lib.orc_get_board.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
             lib.orc_set_game.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                          C.c_uint32, C.c_uint32, C.c_uint32]
+            lib.orc_feat_new.restype = C.c_int
+            lib.orc_feat_new.argtypes = [P(C.c_void_p), C.c_void_p, C.c_int32]
+            lib.orc_feat_free.argtypes = [C.c_void_p]
+            lib.orc_feat_build.argtypes = [C.c_void_p, C.c_void_p]
             _lib = lib
     return _lib
 
@@ -199,3 +203,37 @@ class OracleEnv:
             alive = (1 << int(self.P[g])) - 1
         self.lib.orc_set_game(self.h, g, _ptr(army), _ptr(owner), _ptr(terrain), int(turn), int(alive),
                               int(frame), int(epoch))
+
+
+class OracleFeatures:
+    """Feature tensor builder over an OracleEnv (Appendix A): C = 24 + 2 * hist
+    channels per player.  ``build()`` folds the current frame into each
+    player's memory and returns a list over games of [P][C][N] float32."""
+
+    def __init__(self, env: OracleEnv, hist: int = 7):
+        self.env = env
+        self.lib = env.lib
+        self.hist = int(hist)
+        self.C = 24 + 2 * self.hist
+        h = C.c_void_p()
+        if self.lib.orc_feat_new(C.byref(h), env.h, self.hist) != 0:
+            raise ValueError("orc_feat_new failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.orc_feat_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def build(self):
+        sizes = [int(P) * self.C * int(N) for P, N in zip(self.env.P, self.env.N)]
+        out = np.zeros(int(sum(sizes)), np.float32)
+        self.lib.orc_feat_build(self.h, _ptr(out))
+        res, off = [], 0
+        for (P, N), n in zip(zip(self.env.P, self.env.N), sizes):
+            res.append(out[off:off + n].reshape(int(P), self.C, int(N)))
+            off += n
+        return res
