@@ -484,6 +484,82 @@ def run_served(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def feature_bytes_per_player_cell(hist: int, players: int) -> float:
+    """Algorithmic HBM bytes of the feature builder per player and board cell:
+    the float32 rows written, the memory read and written back (masks 1 B,
+    last enemy army 2 B, its turn 4 B, one new own/enemy plane pair 4 B), the
+    hist older plane pairs read (4 B each), and the board (4 B per cell)
+    shared by the game's players."""
+    C = 24 + 2 * hist
+    return 4 * C + 7 + 4 * hist + 11 + 4.0 / players
+
+
+def run_features(args, rank, world, local):
+    """Per frame: the fused step + policy, then the 38-channel feature tensor
+    of every player (App. A) with its persistent memory."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import shard, workload
+
+    torch.cuda.set_device(local)
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
+    G = int(H.shape[0])
+    hist = 7
+    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
+    fb = env.features(hist)
+    out = env.new_outputs()
+    acts = env.new_actions()
+    fout = fb.new_output()
+    stream = torch.cuda.current_stream()
+    env.policy(POLICY_SEED, acts)
+    for _ in range(max(3, args.warmup)):
+        env.step_policy(acts, out, POLICY_SEED, acts)
+        fb.build(fout)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        t_all[0].record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            env.step_policy(acts, out, POLICY_SEED, acts)
+            ev[k][1].record(stream)
+            fb.build(fout)
+            ev[k][2].record(stream)
+        t_all[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    elapsed_ms = max_over_ranks(t_all[0].elapsed_time(t_all[1]), world)
+    step_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    feat_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    value = sum_over_ranks(float(G * K), world) / (elapsed_ms * 1e-3)
+    cells = 2 * 576 * G
+    nbytes = feature_bytes_per_player_cell(hist, 2) * cells
+    peak, peak_kind = peaks()
+    achieved = nbytes / (feat_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "game frames/s with the 38-channel feature tensor", "value": value, "unit": "frames/s",
+            "n_gpus": world, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
+            "config": {"workload": "features-65536x24x24", "games_per_gpu": G, "hist": hist, "channels": 24 + 2 * hist,
+                       "l2": "inputs larger than L2 (features 11.5 GB + memory 2.9 GB per frame)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_launch": nbytes, "launch_ms": feat_ms,
+                         "kernel": "k_features (38-channel feature tensor)"},
+            "step_launch_ms": step_ms,
+            "gpu_launches": 2 * K,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_generator(args, rank, world, local):
     """Map generation throughput: gen_reset of every game of the default
     workload's shapes, for each generator option set."""
@@ -563,6 +639,8 @@ def main():
             run_served(args, rank, world, local)
         elif args.workload == "generator-65536x24x24":
             run_generator(args, rank, world, local)
+        elif args.workload == "features-65536x24x24":
+            run_features(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

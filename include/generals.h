@@ -325,6 +325,46 @@ typedef struct gen_sim_config {
 int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_server_stats *st);
 
 /* Reason for the last failure on this thread (never NULL). */
+/* ---- feature tensor (App. A, table of observation channels) -------------
+ * Per player C = 24 + 2 * hist float32 planes of Npad_g cells each, in the
+ * table's order: 0 armies, 1 own army, 2 enemy army, 3 neutral army,
+ * 4 seen, 5 enemy seen, 6 generals, 7 castles, 8 mountains (persistent
+ * memory), 9 neutral cells, 10 owned cells, 11 opponent cells, 12 fog,
+ * 13 structures in fog, 14 turn, 15 (turn mod 50) / 50, 16 own land,
+ * 17 own army, 18 opponents' land, 19 opponents' army (public scoreboard),
+ * 20 last enemy army seen, 21 log(1 + turns since an enemy was last seen)
+ * / 5, 22 column / (W-1), 23 row / (H-1), 24 .. 24+hist-1 own army deltas
+ * (newest first), 24+hist .. 24+2hist-1 enemy army deltas.  "Opponent" is
+ * a player of another team; enemy planes are the fogged view.
+ * Layout: the player plane q = plane_off[g] + p * Npad_g (as for the
+ * observation planes) holds channel ch of cell c at float index
+ * q * C + ch * Npad_g + c; a uniform batch is [G][P][C][Npad].  Padding
+ * cells N_g .. Npad_g-1 read 0 in every channel.
+ * Memory: the builder keeps per player and cell the five persistent masks,
+ * the last enemy army and turn, and hist + 1 frames of own / enemy army
+ * planes (about 15 + 4 * (hist + 1) bytes per plane cell, allocated at
+ * creation).  Each build folds the current frame into that memory once
+ * (keyed by the game's frame counter; a second build in the same frame
+ * changes nothing) and clears a game's memory when its epoch changes (a
+ * new episode).  Call it after every step for the paper's definition of
+ * the memory and delta rows.  The environment must outlive the builder. */
+typedef struct gen_features gen_features;
+
+/* hist in [1, 16] (the paper's default is 7: 38 channels).  Allocates the
+ * memory on the environment's device; synchronous.  GEN_ERR_BAD_ARG for a
+ * NULL env or hist out of range, GEN_ERR_CUDA when allocation fails. */
+int gen_features_create(gen_features **out, gen_env *env, int hist);
+
+/* Channels C and the number of floats the output buffer must hold. */
+int gen_features_layout(const gen_features *f, int32_t *channels, int64_t *n_floats);
+
+/* Fold the current frame into the memory and write every player's features
+ * to d_out (device, 16-byte aligned, n_floats floats).  Asynchronous on
+ * `stream`; order it after the step that produced the frame. */
+int gen_features_build(gen_features *f, float *d_out, void *stream);
+
+void gen_features_destroy(gen_features *f);
+
 const char *gen_last_error(void);
 
 void gen_destroy(gen_env *env);

@@ -804,6 +804,82 @@ int gen_set_spawn_range(gen_env* e, int min_dist, int max_dist) {
     return GEN_OK;
 }
 
+struct gen_features {
+    gen_env* env = nullptr;
+    int hist = 0;
+    void* d_mem = nullptr;  // one allocation: headers, masks, last army, last turn, ring
+    gk::FArgs args{};
+};
+
+int gen_features_create(gen_features** out, gen_env* e, int hist) {
+    if (!out) return fail(GEN_ERR_BAD_ARG, "out is NULL");
+    *out = nullptr;
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (hist < 1 || hist > 16) return fail(GEN_ERR_BAD_ARG, "hist %d outside [1, 16]", hist);
+    const int64_t pc = e->plane_cells;
+    const size_t hdr = (size_t)e->player_slots * sizeof(uint4);
+    const size_t bits = ((size_t)pc + 15) & ~(size_t)15;
+    const size_t army = ((size_t)pc * 2 + 15) & ~(size_t)15;
+    const size_t turn = (size_t)pc * 4;
+    const size_t ring = (size_t)(hist + 1) * 2 * (size_t)pc * 2;
+    auto* f = new gen_features();
+    f->env = e;
+    f->hist = hist;
+    char* m = nullptr;
+    cudaError_t ce = cudaMalloc(&m, hdr + bits + army + turn + ring);
+    if (ce != cudaSuccess) {
+        delete f;
+        return cuda_fail(ce, "cudaMalloc feature memory");
+    }
+    if ((ce = cudaMemset(m, 0, hdr)) != cudaSuccess) {
+        cudaFree(m);
+        delete f;
+        return cuda_fail(ce, "clear feature headers");
+    }
+    f->d_mem = m;
+    gk::FArgs& a = f->args;
+    a.info = e->d_info;
+    a.army = e->d_army;
+    a.owner = e->d_owner;
+    a.terrain = e->d_terrain;
+    a.scal = e->d_scal;
+    a.n_games = e->G;
+    a.hist = hist;
+    a.plane_cells = pc;
+    a.hdr = reinterpret_cast<uint4*>(m);
+    a.mem_bits = reinterpret_cast<uint8_t*>(m + hdr);
+    a.mem_army = reinterpret_cast<int16_t*>(m + hdr + bits);
+    a.mem_turn = reinterpret_cast<int32_t*>(m + hdr + bits + army);
+    a.ring = reinterpret_cast<int16_t*>(m + hdr + bits + army + turn);
+    a.npad_max = e->npad_max;
+    *out = f;
+    return GEN_OK;
+}
+
+int gen_features_layout(const gen_features* f, int32_t* channels, int64_t* n_floats) {
+    if (!f) return fail(GEN_ERR_BAD_ARG, "features is NULL");
+    const int C = 24 + 2 * f->hist;
+    if (channels) *channels = C;
+    if (n_floats) *n_floats = f->env->plane_cells * C;
+    return GEN_OK;
+}
+
+int gen_features_build(gen_features* f, float* d_out, void* stream) {
+    if (!f || !d_out) return fail(GEN_ERR_BAD_ARG, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(d_out) & 15u) return fail(GEN_ERR_BAD_ARG, "d_out is not 16-byte aligned");
+    gk::FArgs a = f->args;
+    a.out = d_out;
+    const int rc = gk::launch_features(a, stream);
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "feature launch");
+    return GEN_OK;
+}
+
+void gen_features_destroy(gen_features* f) {
+    if (!f) return;
+    cudaFree(f->d_mem);
+    delete f;
+}
+
 int gen_set_launch(gen_env* e, int warps_per_cta) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)

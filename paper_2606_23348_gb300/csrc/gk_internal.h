@@ -90,6 +90,28 @@ struct KArgs {
     int32_t castle_radius;  // > 0: a neutral castle within this many steps of every general
 };
 
+// Feature-tensor builder (App. A): one warp per game, players in turn.
+struct FArgs {
+    const GameInfo* info;
+    const int16_t* army;
+    const int8_t* owner;
+    const int8_t* terrain;
+    const GameScalars* scal;
+    int32_t n_games;
+    int32_t hist;          // delta history length K: channels 24 + 2K
+    int64_t plane_cells;   // cells of the per-player plane set
+    uint4* hdr;            // per player slot: epoch + 1 folded (0: none), frame folded, ring head, valid planes
+    uint8_t* mem_bits;     // per plane cell: bit 0 seen, 1 enemy seen, 2 general, 3 castle, 4 mountain
+    int16_t* mem_army;     // per plane cell: last enemy army seen
+    int32_t* mem_turn;     // per plane cell: turn an enemy was last seen
+    int16_t* ring;         // [(K + 1) * 2][plane_cells]: own / enemy army planes of folded frames
+    float* out;            // player plane q = plane_off + p * Npad: channel ch of cell c at q * C + ch * Npad + c
+    int32_t npad_max;      // largest board (cells, multiple of 16)
+};
+
+// Launch the feature builder over every game on `stream`.  Returns a cudaError_t.
+int launch_features(const FArgs& f, void* stream);
+
 // Bytes of shared memory one warp needs for games up to npad_max cells and
 // pmax players; also returns the bitset stride in words.
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride);

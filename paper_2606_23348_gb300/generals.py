@@ -58,7 +58,8 @@ class GenLayoutInfo(C.Structure):
 EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "gen_reset", "gen_observe",
            "gen_step", "gen_step_policy", "gen_policy", "gen_rollout", "gen_step_host", "gen_read_state",
            "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
-           "gen_step_host_static", "gen_set_spawn_range")
+           "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
+           "gen_features_build", "gen_features_destroy")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -93,6 +94,10 @@ def load_library(path: str = LIB_PATH):
             "gen_set_launch": (C.c_int, [vp, C.c_int]),
             "gen_set_spawn_range": (C.c_int, [vp, C.c_int, C.c_int]),
             "gen_copy_peak": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
+            "gen_features_create": (C.c_int, [C.POINTER(vp), vp, C.c_int]),
+            "gen_features_layout": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int64)]),
+            "gen_features_build": (C.c_int, [vp, vp, vp]),
+            "gen_features_destroy": (None, [vp]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
         }
@@ -267,6 +272,10 @@ class GeneralsEnv:
     def set_spawn_range(self, min_dist: int, max_dist: int):
         _check(self.lib.gen_set_spawn_range(self.h, int(min_dist), int(max_dist)), "gen_set_spawn_range")
 
+    def features(self, hist: int = 7) -> "Features":
+        """Feature-tensor builder over this environment (App. A)."""
+        return Features(self, hist)
+
     def set_launch(self, warps_per_cta: int):
         _check(self.lib.gen_set_launch(self.h, int(warps_per_cta)), "gen_set_launch")
 
@@ -298,3 +307,54 @@ class GeneralsEnv:
         """Player p's plane of game g from a flat per-player output tensor (padding removed)."""
         o = int(self.plane_off[g]) + p * int(self.npad[g])
         return t[o:o + int(self.N[g])]
+
+
+class Features:
+    """The 24 + 2 * hist channel feature tensor of every player (gen_features_*).
+
+    ``build()`` folds the current frame into the per-player memory and
+    returns a float32 device tensor of ``n_floats`` (a uniform batch views as
+    [G][P][C][H*W]); call it after every step.
+    """
+
+    def __init__(self, env: GeneralsEnv, hist: int = 7):
+        self.env = env
+        self.lib = env.lib
+        h = C.c_void_p()
+        _check(self.lib.gen_features_create(C.byref(h), env.h, int(hist)), "gen_features_create")
+        self.h = h
+        ch, n = C.c_int32(), C.c_int64()
+        _check(self.lib.gen_features_layout(h, C.byref(ch), C.byref(n)), "gen_features_layout")
+        self.channels, self.n_floats, self.hist = int(ch.value), int(n.value), int(hist)
+
+    def new_output(self):
+        import torch
+        return torch.empty(self.n_floats, dtype=torch.float32, device="cuda")
+
+    def build(self, out=None):
+        if self.env.h is None:
+            raise GeneralsError("the environment of this feature builder is closed")
+        if out is None:
+            out = self.new_output()
+        assert out.numel() >= self.n_floats and out.dtype.itemsize == 4 and out.is_cuda
+        _check(self.lib.gen_features_build(self.h, C.c_void_p(out.data_ptr()), _cur_stream()), "gen_features_build")
+        return out
+
+    def player_view(self, out, g: int, p: int):
+        """[C][H_g * W_g] view of game g, player p inside a build() output."""
+        npad = int(self.env.npad[g])
+        q = int(self.env.plane_off[g]) + p * npad
+        n = int(self.env.H[g]) * int(self.env.W[g])
+        C = self.channels
+        return out[q * C:q * C + C * npad].view(C, npad)[:, :n]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gen_features_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,183 @@
+"""Feature tensor (App. A) on the GPU vs the oracle, through the C-ABI.
+
+Every channel of every player and game is compared element by element with
+the oracle's builder run on the same frames: exact for every channel except
+the age row (log(1 + dt) / 5), where both sides evaluate the logarithm in
+double precision and round once to float, so they may differ by at most one
+float ulp when the two libraries' double logarithms differ in their last
+bit.  Padding cells must read 0 in every channel.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import OracleEnv
+from oracle.orc import OracleFeatures
+from paper_2606_23348_gb300.workloads import shapes, workload
+
+pytestmark = pytest.mark.gpu
+
+AGE = 21
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2606_23348_gb300.build import build_library
+    build_library()
+
+
+def compare_features(env, fb, out, want, tag, games=None, orc_index=None):
+    import torch
+    torch.cuda.synchronize()
+    C = fb.channels
+    games = range(env.G) if games is None else games
+    for k, g in enumerate(games):
+        npad, N, P = int(env.npad[g]), int(env.N[g]), int(env.P[g])
+        for p in range(P):
+            q = int(env.plane_off[g]) + p * npad
+            got = out[q * C:q * C + C * npad].view(C, npad).cpu().numpy()
+            w = want[k if orc_index is None else orc_index(k)][p]
+            assert not got[:, N:].any(), f"{tag} game {g} player {p}: padding cells not zero"
+            exact = np.ones(C, bool)
+            exact[AGE] = False
+            if not np.array_equal(got[exact, :N], w[exact]):
+                bad = np.argwhere(got[:, :N] != w)
+                ch, c = bad[0]
+                raise AssertionError(f"{tag} game {g} player {p}: channel {ch} cell {c}: gpu {got[ch, c]} oracle "
+                                     f"{w[ch, c]} ({len(bad)} differences)")
+            np.testing.assert_array_max_ulp(got[AGE, :N], w[AGE], maxulp=1)
+
+
+def lockstep(env, orc, fb, ofb, frames, policy_seed, tag, every=1, subset_reset=None):
+    import torch
+    out = env.new_outputs()
+    acts = env.new_actions()
+    fout = fb.new_output()
+    env.observe(out)
+    fb.build(fout)
+    compare_features(env, fb, fout, ofb.build(), f"{tag} create")
+    env.policy(policy_seed, acts)
+    for f in range(frames):
+        a = orc.policy(policy_seed)
+        env.step_policy(acts, out, policy_seed, acts)
+        orc.step(a)
+        if subset_reset is not None and f == frames // 2:
+            ids = np.asarray(subset_reset, np.int32)
+            env.reset(out, torch.from_numpy(ids).cuda())
+            orc.reset(ids)
+            env.policy(policy_seed, acts)  # the reset games' actions come from their new maps
+        fb.build(fout)
+        want = ofb.build()
+        if (f + 1) % every == 0 or f == frames - 1:
+            compare_features(env, fb, fout, want, f"{tag} frame {f + 1}")
+    return fout
+
+
+def pair(H, W, mode, P, hist=7, **kw):
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    env = GeneralsEnv(H, W, mode, P, **kw)
+    orc = OracleEnv(H, W, mode, P, **kw)
+    return env, orc, env.features(hist), OracleFeatures(orc, hist)
+
+
+def test_features_mixed_modes_with_resets():
+    """Ragged 1v1 / 2v2 / FFA boards, truncation resets every 25 turns, every frame compared."""
+    G = 24
+    H, W, mode, P = shapes(G, (4, 12), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=8)
+    env, orc, fb, ofb = pair(H, W, mode, P, seed=4, n_cities=2, max_turns=25)
+    lockstep(env, orc, fb, ofb, 80, 6, "mixed")
+
+
+@pytest.mark.parametrize("hist", [1, 16])
+def test_features_history_lengths(hist):
+    H, W, mode, P, gen, _ = workload("1v1-64x15x15")
+    env, orc, fb, ofb = pair(H[:16], W[:16], mode[:16], P[:16], hist=hist, seed=1, **gen)
+    assert fb.channels == 24 + 2 * hist
+    lockstep(env, orc, fb, ofb, 30, 3, f"hist {hist}", every=3)
+
+
+def test_features_subset_reset_and_repeat_build():
+    """A reset of some games clears their memory; a second build in one frame changes nothing."""
+    G = 12
+    H, W, mode, P = shapes(G, (6, 9), ((0, 0.5), (2, 0.5)), seed=2)
+    env, orc, fb, ofb = pair(H, W, mode, P, seed=3, n_cities=2)
+    fout = lockstep(env, orc, fb, ofb, 20, 5, "subset", subset_reset=[0, 5, 11])
+    again = fb.build()
+    import torch
+    torch.cuda.synchronize()
+    assert torch.equal(fout, again)
+
+
+@pytest.mark.parametrize("H,W,mode,P", [(1, 2, 0, 2), (40, 1, 2, 3), (33, 5, 1, 4), (64, 64, 2, 8), (3, 3, 2, 8)])
+def test_features_edge_shapes(H, W, mode, P):
+    env, orc, fb, ofb = pair([H, H], [W, W], [mode, mode], [P, P], seed=5, n_cities=1, max_turns=15)
+    lockstep(env, orc, fb, ofb, 20, 9, f"edge {H}x{W}", every=4)
+
+
+def _golden_cases():
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "features")
+    return sorted(os.path.join(d, f) for f in os.listdir(d) if f.endswith(".txt") and f != "README.txt")
+
+
+@pytest.mark.parametrize("path", _golden_cases(), ids=lambda p: os.path.basename(p)[:-4])
+def test_feature_golden_on_gpu(path):
+    """The hand-worked feature scenarios, loaded into the GPU state."""
+    import torch
+    from test_oracle_features import load_feature_case
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    sc = load_feature_case(path)
+    P = sc["P"]
+    env = GeneralsEnv([sc["H"]], [sc["W"]], [sc["mode"]], [P], seed=7, auto_reset=0, n_cities=0,
+                      min_general_dist=1)
+    army, owner, terrain = sc["board"]
+    npad = int(env.npad[0])
+    pad = lambda x, v: np.concatenate([x, np.full(npad - x.shape[0], v, x.dtype)])
+    scal = np.array([[sc["turn"], 0, 0, (1 << P) - 1, 0, 0, 0, 0]], np.uint32)
+    env.write_state(pad(army, 0), pad(owner, -1), pad(terrain, 0), scal)
+    fb = env.features(sc["hist"])
+    out = env.new_outputs()
+    n = 0
+    for fr in sc["frames"]:
+        if fr["actions"] is not None:
+            env.step(torch.from_numpy(fr["actions"][:P].copy()).cuda(), out)
+        f = fb.build()
+        torch.cuda.synchronize()
+        for p, ch, want in fr["checks"]:
+            got = fb.player_view(f, 0, p)[ch].cpu().numpy().astype(np.float64)
+            np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9, err_msg=f"player {p} channel {ch}")
+            n += 1
+    assert n > 10
+
+
+def test_features_full_size_24x24_65536_sampled():
+    """65,536 games of 24x24: features built every frame on the GPU; three
+    blocks of 32 games replayed by the oracle and compared at the end."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
+    env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
+    fb = env.features(7)
+    out = env.new_outputs()
+    acts = env.new_actions()
+    fout = fb.new_output()
+    env.policy(2, acts)
+    fb.build(fout)
+    frames = 12
+    for f in range(frames):
+        env.step_policy(acts, out, 2, acts)
+        fb.build(fout)
+    torch.cuda.synchronize()
+    for start in (0, 40000, 65536 - 32):
+        n = 32
+        orc = OracleEnv(H[start:start + n], W[start:start + n], mode[start:start + n], P[start:start + n], seed=1,
+                        game_id_base=start, **gen)
+        ofb = OracleFeatures(orc, 7)
+        ofb.build()
+        for f in range(frames):
+            orc.step(orc.policy(2))
+            want = ofb.build()
+        compare_features(env, fb, fout, want, f"full size block {start}", games=range(start, start + n))
