@@ -81,12 +81,51 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
 __device__ __forceinline__ int lo16(uint32_t x) { return (int)(int16_t)(x & 0xFFFFu); }
 __device__ __forceinline__ int hi16(uint32_t x) { return (int)(int16_t)(x >> 16); }
 
-// age row: log(1 + dt) / 5 in double, rounded once
-__device__ __forceinline__ float age_value(int dt) {
-    return dt > 0 ? (float)(log(1.0 + (double)dt) / 5.0) : 0.0f;
+// flag byte of one cell
+constexpr uint32_t kFIn = 1u;          // on the board (not padding)
+constexpr uint32_t kFVis = 2u;         // visible
+constexpr uint32_t kFOwn = 4u;         // owned by the player
+constexpr uint32_t kFOpp = 8u;         // visible and owned by an opponent
+constexpr uint32_t kFUnowned = 16u;    // visible and unowned
+constexpr uint32_t kFNeutral = 32u;    // visible, unowned, not a mountain
+constexpr uint32_t kFFogStruct = 64u;  // fogged structure
+constexpr uint32_t kFKeep = 128u;      // fogged and seen before: keep the last enemy army
+
+// four int16 values, each kept where the cell's flag byte has `bit`, else 0
+__device__ __forceinline__ uint2 select16(uint2 x, uint32_t fl, uint32_t bit) {
+    const uint32_t m0 = (fl & bit) ? 0x0000FFFFu : 0u;
+    const uint32_t m1 = (fl & (bit << 8)) ? 0xFFFF0000u : 0u;
+    const uint32_t m2 = (fl & (bit << 16)) ? 0x0000FFFFu : 0u;
+    const uint32_t m3 = (fl & (bit << 24)) ? 0xFFFF0000u : 0u;
+    return make_uint2(x.x & (m0 | m1), x.y & (m2 | m3));
+}
+__device__ __forceinline__ uint2 or2(uint2 a, uint2 b) { return make_uint2(a.x | b.x, a.y | b.y); }
+
+__device__ __forceinline__ void st4i(float* p, uint2 x) {
+    __stcs(reinterpret_cast<float4*>(p),
+           make_float4((float)lo16(x.x), (float)hi16(x.x), (float)lo16(x.y), (float)hi16(x.y)));
+}
+// 1.0 where the byte of each cell has `bit`
+__device__ __forceinline__ void st4b(float* p, uint32_t w, uint32_t bit) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4((w & bit) ? 1.0f : 0.0f, (w & (bit << 8)) ? 1.0f : 0.0f,
+                                                     (w & (bit << 16)) ? 1.0f : 0.0f, (w & (bit << 24)) ? 1.0f : 0.0f));
+}
+// a broadcast scalar on board cells, 0 on padding
+__device__ __forceinline__ void st4s(float* p, uint32_t fl, float x) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4((fl & kFIn) ? x : 0.0f, (fl & (kFIn << 8)) ? x : 0.0f,
+                                                     (fl & (kFIn << 16)) ? x : 0.0f, (fl & (kFIn << 24)) ? x : 0.0f));
+}
+// a - b per int16 lane
+__device__ __forceinline__ void st4d(float* p, uint2 a, uint2 b) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4((float)(lo16(a.x) - lo16(b.x)), (float)(hi16(a.x) - hi16(b.x)),
+                                                     (float)(lo16(a.y) - lo16(b.y)), (float)(hi16(a.y) - hi16(b.y))));
 }
 
-__global__ void __launch_bounds__(256) k_features(const FArgs f) {
+// age row: log(1 + dt) / 5 in double, rounded once (out of line: rare)
+__device__ __noinline__ float age_log(int dt) { return (float)(log(1.0 + (double)dt) / 5.0); }
+__device__ __forceinline__ float age_value(int dt) { return dt > 0 ? age_log(dt) : 0.0f; }
+
+__global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gidx = blockIdx.x * kWarps + wid;
@@ -198,135 +237,116 @@ __global__ void __launch_bounds__(256) k_features(const FArgs f) {
         float* out = f.out + q0 * C;
         for (int c = 4 * lane; c < Npad; c += 128) {
             const int64_t pc = q0 + c;
+            // memory of cells c..c+3 (loads first)
+            uint32_t mb = 0u;
+            uint2 lea = make_uint2(0u, 0u);
+            int4 let = make_int4(0, 0, 0, 0);
+            if (!cleared) {
+                mb = __ldcs(reinterpret_cast<const unsigned int*>(f.mem_bits + pc));
+                lea = __ldcs(reinterpret_cast<const uint2*>(f.mem_army + pc));
+                let = __ldcs(reinterpret_cast<const int4*>(f.mem_turn + pc));
+            }
             // board of cells c..c+3
             const uint2 a2 = *reinterpret_cast<const uint2*>(s_army + c);
             const uint32_t ow = *reinterpret_cast<const uint32_t*>(s_owner + c);
             const uint32_t tw = *reinterpret_cast<const uint32_t*>(s_terrain + c);
             const uint32_t vbits = (s_vis[c >> 5] >> (c & 31)) & 0xFu;
-            // memory of cells c..c+3
-            uint32_t mb = cleared ? 0u : *reinterpret_cast<const uint32_t*>(f.mem_bits + pc);
-            uint2 lea = make_uint2(0u, 0u);
-            int4 let = make_int4(0, 0, 0, 0);
-            if (!cleared) {
-                lea = *reinterpret_cast<const uint2*>(f.mem_army + pc);
-                let = *reinterpret_cast<const int4*>(f.mem_turn + pc);
-            }
-            int av[4], own[4], enemy[4], neut[4], lea_n[4], dt[4];
-            uint32_t flags = 0;  // per cell byte: bit 0 in board, 1 visible, 2 own, 3 opponent, 5 neutral, 6 fog structure
-            int let_n[4] = {let.x, let.y, let.z, let.w};
-            const int lea_o[4] = {lo16(lea.x), hi16(lea.x), lo16(lea.y), hi16(lea.y)};
-            const int arm[4] = {lo16(a2.x), hi16(a2.x), lo16(a2.y), hi16(a2.y)};
+            // one flag byte per cell (kF*) and the folded memory masks
+            uint32_t fl = 0u;
+            int lt[4] = {let.x, let.y, let.z, let.w};
+            float age[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const bool in = c + i < N;
                 const int o = (int)(int8_t)(ow >> (8 * i));
-                const int t = (int)((tw >> (8 * i)) & 0x3u);
+                const uint32_t t = (tw >> (8 * i)) & 0x3u;
                 const bool v = in && ((vbits >> i) & 1u);
-                const bool isown = in && o == p;
-                const bool isopp = in && o >= 0 && (mode == 1 ? (o >> 1) : o) != tp;
-                const int a = in ? arm[i] : 0;
-                av[i] = v ? a : 0;
-                own[i] = isown ? a : 0;
-                enemy[i] = (v && isopp) ? a : 0;
-                neut[i] = (v && o == -1) ? a : 0;
+                const bool opp = in && o >= 0 && (mode == 1 ? (o >> 1) : o) != tp;
                 uint32_t m = (mb >> (8 * i)) & 0x1Fu;
                 const bool seen_old = m & 1u;
                 if (v) {
                     m |= 1u;
-                    if (isopp) {
+                    if (opp) {
                         m |= 2u;
-                        let_n[i] = turn;
+                        lt[i] = turn;
                     }
-                    if (t == 3) m |= 4u;
-                    if (t == 2) m |= 8u;
-                    if (t == 1) m |= 16u;
+                    m |= t == 3u ? 4u : t == 2u ? 8u : t == 1u ? 16u : 0u;
                 }
                 mb = (mb & ~(0xFFu << (8 * i))) | (m << (8 * i));
-                lea_n[i] = v ? enemy[i] : (seen_old ? lea_o[i] : 0);
-                dt[i] = (!v && (m & 2u)) ? turn - let_n[i] : 0;
-                uint32_t fl = in ? 1u : 0u;
-                if (v) fl |= 2u;
-                if (isown) fl |= 4u;
-                if (v && isopp) fl |= 8u;
-                if (v && o == -1 && t != 1) fl |= 32u;
-                if (in && !v && (t == 1 || t == 2 || (m & 4u))) fl |= 64u;
-                flags |= fl << (8 * i);
+                age[i] = age_value((!v && (m & 2u)) ? turn - lt[i] : 0);
+                uint32_t b = in ? kFIn : 0u;
+                if (v) b |= kFVis;
+                if (in && o == p) b |= kFOwn;
+                if (v && opp) b |= kFOpp;
+                if (v && o == -1) b |= kFUnowned;
+                if (v && o == -1 && t != 1u) b |= kFNeutral;
+                if (in && !v && (t == 1u || t == 2u || (m & 4u))) b |= kFFogStruct;
+                if (!v && seen_old) b |= kFKeep;
+                fl |= b << (8 * i);
             }
-            auto flag = [&](int i, uint32_t b) { return (float)((flags >> (8 * i + b)) & 1u); };
-            auto bit = [&](int i, int b) { return (float)((mb >> (8 * i + b)) & 1u); };
-            auto row = [&](int ch) { return out + (int64_t)ch * Npad + c; };
-            st4(row(0), (float)av[0], (float)av[1], (float)av[2], (float)av[3]);
-            st4(row(1), (float)own[0], (float)own[1], (float)own[2], (float)own[3]);
-            st4(row(2), (float)enemy[0], (float)enemy[1], (float)enemy[2], (float)enemy[3]);
-            st4(row(3), (float)neut[0], (float)neut[1], (float)neut[2], (float)neut[3]);
-#pragma unroll
-            for (int b = 0; b < 5; ++b) st4(row(4 + b), bit(0, b), bit(1, b), bit(2, b), bit(3, b));
-            st4(row(9), flag(0, 5), flag(1, 5), flag(2, 5), flag(3, 5));
-            st4(row(10), flag(0, 2), flag(1, 2), flag(2, 2), flag(3, 2));
-            st4(row(11), flag(0, 3), flag(1, 3), flag(2, 3), flag(3, 3));
-            {
-                auto fog = [&](int i) { return (float)(((flags >> (8 * i)) & 3u) == 1u); };  // in, not visible
-                st4(row(12), fog(0), fog(1), fog(2), fog(3));
-            }
-            st4(row(13), flag(0, 6), flag(1, 6), flag(2, 6), flag(3, 6));
-            {
-                auto in_ = [&](int i, float x) { return ((flags >> (8 * i)) & 1u) ? x : 0.0f; };
-                st4(row(14), in_(0, f_turn), in_(1, f_turn), in_(2, f_turn), in_(3, f_turn));
-                st4(row(15), in_(0, f_phase), in_(1, f_phase), in_(2, f_phase), in_(3, f_phase));
-                st4(row(16), in_(0, f_own_land), in_(1, f_own_land), in_(2, f_own_land), in_(3, f_own_land));
-                st4(row(17), in_(0, f_own_army), in_(1, f_own_army), in_(2, f_own_army), in_(3, f_own_army));
-                st4(row(18), in_(0, f_opp_land), in_(1, f_opp_land), in_(2, f_opp_land), in_(3, f_opp_land));
-                st4(row(19), in_(0, f_opp_army), in_(1, f_opp_army), in_(2, f_opp_army), in_(3, f_opp_army));
-                st4(row(20), (float)lea_n[0], (float)lea_n[1], (float)lea_n[2], (float)lea_n[3]);
-                st4(row(21), age_value(dt[0]), age_value(dt[1]), age_value(dt[2]), age_value(dt[3]));
-                // coordinates (Q32)
-                float cx[4], cy[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int cc = c + i, r = cc / W, col = cc - r * W;
-                    cx[i] = in_(i, W > 1 ? (float)col / (float)(W - 1) : 0.0f);
-                    cy[i] = in_(i, H > 1 ? (float)r / (float)(H - 1) : 0.0f);
-                }
-                st4(row(22), cx[0], cx[1], cx[2], cx[3]);
-                st4(row(23), cy[0], cy[1], cy[2], cy[3]);
-            }
-            // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back
-            {
-                int po[4] = {own[0], own[1], own[2], own[3]};
-                int pe[4] = {enemy[0], enemy[1], enemy[2], enemy[3]};
-                for (int k = 0; k < K; ++k) {
-                    int no[4] = {0, 0, 0, 0}, ne[4] = {0, 0, 0, 0};
-                    if (k + 1 < nvalid) {
-                        const int s = (head - (k + 1) + R) % R;
-                        const uint2 xo = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * s) * f.plane_cells + pc));
-                        const uint2 xe =
-                            __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * s + 1) * f.plane_cells + pc));
-                        no[0] = lo16(xo.x), no[1] = hi16(xo.x), no[2] = lo16(xo.y), no[3] = hi16(xo.y);
-                        ne[0] = lo16(xe.x), ne[1] = hi16(xe.x), ne[2] = lo16(xe.y), ne[3] = hi16(xe.y);
-                    }
-                    st4(row(24 + k), (float)(po[0] - no[0]), (float)(po[1] - no[1]), (float)(po[2] - no[2]),
-                        (float)(po[3] - no[3]));
-                    st4(row(24 + K + k), (float)(pe[0] - ne[0]), (float)(pe[1] - ne[1]), (float)(pe[2] - ne[2]),
-                        (float)(pe[3] - ne[3]));
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        po[i] = no[i];
-                        pe[i] = ne[i];
-                    }
-                }
-            }
+            const uint2 own = select16(a2, fl, kFOwn);
+            const uint2 ene = select16(a2, fl, kFOpp);
+            const uint2 lea_n = or2(ene, select16(lea, fl, kFKeep));  // Q31
             if (fold) {
                 *reinterpret_cast<uint32_t*>(f.mem_bits + pc) = mb;
-                *reinterpret_cast<uint2*>(f.mem_army + pc) =
-                    make_uint2(((uint32_t)lea_n[0] & 0xFFFFu) | ((uint32_t)lea_n[1] << 16),
-                               ((uint32_t)lea_n[2] & 0xFFFFu) | ((uint32_t)lea_n[3] << 16));
-                *reinterpret_cast<int4*>(f.mem_turn + pc) = make_int4(let_n[0], let_n[1], let_n[2], let_n[3]);
-                *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * head) * f.plane_cells + pc) =
-                    make_uint2(((uint32_t)own[0] & 0xFFFFu) | ((uint32_t)own[1] << 16),
-                               ((uint32_t)own[2] & 0xFFFFu) | ((uint32_t)own[3] << 16));
-                *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * head + 1) * f.plane_cells + pc) =
-                    make_uint2(((uint32_t)enemy[0] & 0xFFFFu) | ((uint32_t)enemy[1] << 16),
-                               ((uint32_t)enemy[2] & 0xFFFFu) | ((uint32_t)enemy[3] << 16));
+                *reinterpret_cast<uint2*>(f.mem_army + pc) = lea_n;
+                *reinterpret_cast<int4*>(f.mem_turn + pc) = make_int4(lt[0], lt[1], lt[2], lt[3]);
+                *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * head) * f.plane_cells + pc) = own;
+                *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * head + 1) * f.plane_cells + pc) = ene;
+            }
+            float* row = out + c;
+            st4i(row, select16(a2, fl, kFVis));
+            st4i(row += Npad, own);
+            st4i(row += Npad, ene);
+            st4i(row += Npad, select16(a2, fl, kFUnowned));
+            st4b(row += Npad, mb, 1u);
+            st4b(row += Npad, mb, 2u);
+            st4b(row += Npad, mb, 4u);
+            st4b(row += Npad, mb, 8u);
+            st4b(row += Npad, mb, 16u);
+            st4b(row += Npad, fl, kFNeutral);
+            st4b(row += Npad, fl, kFOwn);
+            st4b(row += Npad, fl, kFOpp);
+            st4b(row += Npad, fl & ~(fl >> 1), kFIn);  // on the board and not visible
+            st4b(row += Npad, fl, kFFogStruct);
+            st4s(row += Npad, fl, f_turn);
+            st4s(row += Npad, fl, f_phase);
+            st4s(row += Npad, fl, f_own_land);
+            st4s(row += Npad, fl, f_own_army);
+            st4s(row += Npad, fl, f_opp_land);
+            st4s(row += Npad, fl, f_opp_army);
+            st4i(row += Npad, lea_n);
+            st4(row += Npad, age[0], age[1], age[2], age[3]);
+            {  // coordinates (Q32)
+                float cx[4], cy[4];
+                int r = c / W, col = c - r * W;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool in = (fl >> (8 * i)) & kFIn;
+                    cx[i] = in && W > 1 ? (float)col / (float)(W - 1) : 0.0f;
+                    cy[i] = in && H > 1 ? (float)r / (float)(H - 1) : 0.0f;
+                    if (++col == W) {
+                        col = 0;
+                        ++r;
+                    }
+                }
+                st4(row += Npad, cx[0], cx[1], cx[2], cx[3]);
+                st4(row += Npad, cy[0], cy[1], cy[2], cy[3]);
+            }
+            // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back
+            uint2 po = own, pe = ene;
+            float* rd = row + (int64_t)Npad;
+            for (int k = 0; k < K; ++k, rd += Npad) {
+                uint2 no = make_uint2(0u, 0u), ne = make_uint2(0u, 0u);
+                if (k + 1 < nvalid) {
+                    const int sl = (head - (k + 1) + R) % R;
+                    no = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
+                    ne = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
+                }
+                st4d(rd, po, no);
+                st4d(rd + (int64_t)K * Npad, pe, ne);
+                po = no;
+                pe = ne;
             }
         }
         if (fold && lane == 0) f.hdr[slot] = make_uint4(sc.epoch + 1u, sc.frame, (uint32_t)head, (uint32_t)nvalid);
