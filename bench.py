@@ -38,11 +38,18 @@ MAP_SEED = 1
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel
 # from one ncu capture, valid only for the kernel source with this hash.
-NCU_TRAFFIC = {"kernel_sha1": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) of one launch from ncu, captured on a smaller case
+# of the same kernel with inputs larger than L2 and scaled by the games it
+# processes (traffic grows in proportion); valid only for the kernel source
+# it was taken on.
+NCU_TRAFFIC = {"kernel_sha1": "70fd9db3fc4e", "bytes_per_launch": 2 * 365316864.0,
+               "captured": "32,768 games (x2)", "games": 65536}
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "67b218310e74", "bytes_per_launch": 8 * 1837613224.0,
+                       "captured": "8,192 games (x8)", "games": 65536}
 
 
-def kernel_sha1() -> str:
-    p = os.path.join(ROOT, "paper_2606_23348_gb300", "csrc", "gk_kernels.cu")
+def kernel_sha1(name: str = "gk_kernels.cu") -> str:
+    p = os.path.join(ROOT, "paper_2606_23348_gb300", "csrc", name)
     return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
 
 
@@ -257,7 +264,7 @@ def run_ours(args, rank, world, local):
     from paper_2606_23348_gb300.workloads import shard, workload
 
     torch.cuda.set_device(local)
-    H, W, mode, P, gen, _ = workload(WORKLOAD)
+    H, W, mode, P, gen, _ = workload(WORKLOAD, G=args.games or None)
     G = int(H.shape[0])
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
     if args.warps:
@@ -320,7 +327,8 @@ def run_ours(args, rank, world, local):
     nbytes = algorithmic_bytes(env)
     peak, peak_kind = peaks()
     achieved = nbytes / (launch_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_sha1"] == kernel_sha1() else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["kernel_sha1"] == kernel_sha1() and G == NCU_TRAFFIC["games"] else None)
     own_peak = copy_peak_gbps(1 << 30, 5) if (rank == 0 and not args.no_copy_peak) else None
 
     cpu = None
@@ -503,7 +511,7 @@ def run_features(args, rank, world, local):
     from paper_2606_23348_gb300.workloads import shard, workload
 
     torch.cuda.set_device(local)
-    H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=args.games or None)
     G = int(H.shape[0])
     hist = 7
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
@@ -550,8 +558,12 @@ def run_features(args, rank, world, local):
             "config": {"workload": "features-65536x24x24", "games_per_gpu": G, "hist": hist, "channels": 24 + 2 * hist,
                        "l2": "inputs larger than L2 (features 11.5 GB + memory 2.9 GB per frame)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "traffic": (FEATURE_NCU_TRAFFIC["bytes_per_launch"]
+                                     if FEATURE_NCU_TRAFFIC["kernel_sha1"] == kernel_sha1("gk_features.cu")
+                                     and G == FEATURE_NCU_TRAFFIC["games"] else None),
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": feat_ms,
+                         "kernel_sha1": kernel_sha1("gk_features.cu"),
                          "kernel": "k_features (38-channel feature tensor)"},
             "step_launch_ms": step_ms,
             "gpu_launches": 2 * K,
@@ -620,6 +632,8 @@ def main():
     ap.add_argument("--no-copy-peak", action="store_true")
     ap.add_argument("--no-resident", action="store_true", help="skip the resident-rollout figure")
     ap.add_argument("--workload", default=WORKLOAD, help="workload name (paper_2606_23348_gb300.workloads)")
+    ap.add_argument("--games", type=int, default=0,
+                    help="fewer games than the workload (profiling captures; 0 = the workload's count)")
     ap.add_argument("--rollout", type=int, default=64, help="frames per rollout (ragged / mixed workloads)")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--served-seconds", type=float, default=10.0, help="measured window of the served workload")
