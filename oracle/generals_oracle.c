@@ -722,6 +722,10 @@ void orc_set_game(orc_env *e, int32_t g, const int16_t *army, const int8_t *owne
  *   Q33 deltas: row 24 + k = own(t - k) - own(t - k - 1) for k = 0 ..
  *       hist - 1 over consecutive builder frames; frames before the
  *       episode count as all-zero planes.  Row 14 is the turn counter.
+ *   Q34 temporal tokens (App. A, the two non-spatial tokens): per player
+ *       the opponents' summed army and land (rows 19 and 18) of the last
+ *       `window` builder frames, entry k = k frames back (newest first),
+ *       as (army, land) int32 pairs; frames before the episode are 0.
  * Float rows are evaluated in double and rounded to float once.
  * ====================================================================== */
 
@@ -733,11 +737,12 @@ typedef struct orc_pmem {
     int32_t *last_enemy_turn; /* [N], meaningful where enemy_seen */
     int32_t *own_hist;      /* [hist + 1][N]: [k] = own army plane of the k-th latest folded frame */
     int32_t *enemy_hist;    /* [hist + 1][N] */
+    int32_t *series;        /* [window][2]: [k] = (opponents' army, land) k frames back */
 } orc_pmem;
 
 typedef struct orc_feat {
     const orc_env *e;       /* read by orc_feat_build only */
-    int32_t G, hist;
+    int32_t G, hist, window;
     int32_t *P;             /* [G] players per game, kept for orc_feat_free */
     orc_pmem *mem;          /* [G][MAXP] */
 } orc_feat;
@@ -746,13 +751,14 @@ static int orc_is_opponent(const orc_game *g, int p, int o) {
     return o >= 0 && orc_team(g, o) != orc_team(g, p);
 }
 
-int orc_feat_new(orc_feat **out, const orc_env *e, int32_t hist) {
+int orc_feat_new(orc_feat **out, const orc_env *e, int32_t hist, int32_t window) {
     *out = NULL;
-    if (hist < 1 || hist > 16) return -1;
+    if (hist < 1 || hist > 16 || window < 0 || window > 4096) return -1;
     orc_feat *f = (orc_feat *)calloc(1, sizeof(orc_feat));
     f->e = e;
     f->G = e->G;
     f->hist = hist;
+    f->window = window;
     f->P = (int32_t *)calloc((size_t)(e->G > 0 ? e->G : 1), sizeof(int32_t));
     for (int g = 0; g < e->G; ++g) f->P[g] = e->games[g].P;
     f->mem = (orc_pmem *)calloc((size_t)(e->G > 0 ? e->G : 1) * MAXP, sizeof(orc_pmem));
@@ -771,6 +777,7 @@ int orc_feat_new(orc_feat **out, const orc_env *e, int32_t hist) {
             m->last_enemy_turn = (int32_t *)calloc(n, sizeof(int32_t));
             m->own_hist = (int32_t *)calloc(n * (size_t)(hist + 1), sizeof(int32_t));
             m->enemy_hist = (int32_t *)calloc(n * (size_t)(hist + 1), sizeof(int32_t));
+            m->series = (int32_t *)calloc((size_t)(window > 0 ? window : 1) * 2, sizeof(int32_t));
         }
     *out = f;
     return 0;
@@ -790,6 +797,7 @@ void orc_feat_free(orc_feat *f) {
             free(m->last_enemy_turn);
             free(m->own_hist);
             free(m->enemy_hist);
+            free(m->series);
         }
     free(f->mem);
     free(f->P);
@@ -798,7 +806,7 @@ void orc_feat_free(orc_feat *f) {
 
 /* features of player p of game g into out[C][N]; folds the current frame
  * into the player's memory first (once per frame) */
-static void orc_feat_player(orc_feat *f, int gi, int p, float *out) {
+static void orc_feat_player(orc_feat *f, int gi, int p, float *out, int32_t *series_out) {
     const orc_game *g = &f->e->games[gi];
     orc_pmem *m = &f->mem[gi * MAXP + p];
     const int N = g->N, W = g->W, H = g->H, hist = f->hist;
@@ -826,6 +834,7 @@ static void orc_feat_player(orc_feat *f, int gi, int p, float *out) {
         memset(m->last_enemy_turn, 0, sizeof(int32_t) * (size_t)N);
         memset(m->own_hist, 0, sizeof(int32_t) * (size_t)N * (size_t)(hist + 1));
         memset(m->enemy_hist, 0, sizeof(int32_t) * (size_t)N * (size_t)(hist + 1));
+        if (f->window > 0) memset(m->series, 0, sizeof(int32_t) * 2 * (size_t)f->window);
         m->epoch = (int64_t)g->epoch;
         m->frame = -1;
     }
@@ -865,6 +874,18 @@ static void orc_feat_player(orc_feat *f, int gi, int p, float *out) {
             opp_land += land[q];
             opp_army += army[q];
         }
+
+    /* temporal tokens (Q34): the newest entry first, older ones move back */
+    if (fold && f->window > 0) {
+        for (int k = f->window - 1; k >= 1; --k) {
+            m->series[2 * k] = m->series[2 * (k - 1)];
+            m->series[2 * k + 1] = m->series[2 * (k - 1) + 1];
+        }
+        m->series[0] = (int32_t)opp_army;
+        m->series[1] = (int32_t)opp_land;
+    }
+    if (series_out && f->window > 0)
+        memcpy(series_out, m->series, sizeof(int32_t) * 2 * (size_t)f->window);
 
     for (int c = 0; c < N; ++c) {
         const int r = c / W, col = c % W, o = g->owner[c], t = g->terrain[c];
@@ -911,13 +932,15 @@ static void orc_feat_player(orc_feat *f, int gi, int p, float *out) {
 }
 
 /* every game and player, in order: out holds sum over games of P * C * N
- * floats, game g's player p at [C][N] after those of earlier pairs */
-void orc_feat_build(orc_feat *f, float *out) {
+ * floats, game g's player p at [C][N] after those of earlier pairs; series
+ * (may be NULL) holds window * 2 int32 per player in the same order */
+void orc_feat_build(orc_feat *f, float *out, int32_t *series) {
     const int C = 24 + 2 * f->hist;
-    size_t off = 0;
+    size_t off = 0, soff = 0;
     for (int g = 0; g < f->e->G; ++g)
         for (int p = 0; p < f->e->games[g].P; ++p) {
-            orc_feat_player(f, g, p, out + off);
+            orc_feat_player(f, g, p, out + off, series ? series + soff : NULL);
             off += (size_t)C * (size_t)f->e->games[g].N;
+            soff += 2 * (size_t)f->window;
         }
 }

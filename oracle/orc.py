@@ -78,9 +78,9 @@ def oracle_lib():
             lib.orc_set_game.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                          C.c_uint32, C.c_uint32, C.c_uint32]
             lib.orc_feat_new.restype = C.c_int
-            lib.orc_feat_new.argtypes = [P(C.c_void_p), C.c_void_p, C.c_int32]
+            lib.orc_feat_new.argtypes = [P(C.c_void_p), C.c_void_p, C.c_int32, C.c_int32]
             lib.orc_feat_free.argtypes = [C.c_void_p]
-            lib.orc_feat_build.argtypes = [C.c_void_p, C.c_void_p]
+            lib.orc_feat_build.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
     return _lib
 
@@ -208,15 +208,19 @@ class OracleEnv:
 class OracleFeatures:
     """Feature tensor builder over an OracleEnv (Appendix A): C = 24 + 2 * hist
     channels per player.  ``build()`` folds the current frame into each
-    player's memory and returns a list over games of [P][C][N] float32."""
+    player's memory and returns a list over games of [P][C][N] float32;
+    ``series`` then holds, per game, [P][window][2] int32 (opponents' army,
+    land; newest first) when ``window`` > 0."""
 
-    def __init__(self, env: OracleEnv, hist: int = 7):
+    def __init__(self, env: OracleEnv, hist: int = 7, window: int = 0):
         self.env = env
         self.lib = env.lib
         self.hist = int(hist)
+        self.window = int(window)
         self.C = 24 + 2 * self.hist
+        self.series = None
         h = C.c_void_p()
-        if self.lib.orc_feat_new(C.byref(h), env.h, self.hist) != 0:
+        if self.lib.orc_feat_new(C.byref(h), env.h, self.hist, self.window) != 0:
             raise ValueError("orc_feat_new failed")
         self.h = h
 
@@ -231,7 +235,14 @@ class OracleFeatures:
     def build(self):
         sizes = [int(P) * self.C * int(N) for P, N in zip(self.env.P, self.env.N)]
         out = np.zeros(int(sum(sizes)), np.float32)
-        self.lib.orc_feat_build(self.h, _ptr(out))
+        ser = np.zeros(int(sum(self.env.P)) * 2 * max(self.window, 1), np.int32)
+        self.lib.orc_feat_build(self.h, _ptr(out), _ptr(ser) if self.window > 0 else None)
+        if self.window > 0:
+            self.series, soff = [], 0
+            for P in self.env.P:
+                n = int(P) * 2 * self.window
+                self.series.append(ser[soff:soff + n].reshape(int(P), self.window, 2))
+                soff += n
         res, off = [], 0
         for (P, N), n in zip(zip(self.env.P, self.env.N), sizes):
             res.append(out[off:off + n].reshape(int(P), self.C, int(N)))

@@ -44,11 +44,17 @@ def load_feature_case(path):
         elif t[0] == "hist":
             sc["hist"] = int(t[1])
             i += 1
+        elif t[0] == "window":
+            sc["window"] = int(t[1])
+            i += 1
+        elif t[0] == "series":
+            sc["frames"][-1]["series"].append(tuple(int(x) for x in t[1:5]))
+            i += 1
         elif t[0] == "board":
             sc["board"] = parse_board(lines[i + 1:i + 1 + H], H, W)
             i += 1 + H
         elif t[0] == "frame":
-            sc["frames"].append({"actions": None, "checks": []})
+            sc["frames"].append({"actions": None, "checks": [], "series": []})
             i += 1
         elif t[0] == "step":
             acts = np.zeros(8, np.int32)
@@ -57,7 +63,7 @@ def load_feature_case(path):
                 p, a = action_index(lines[i], W)
                 acts[p] = a
                 i += 1
-            sc["frames"].append({"actions": acts, "checks": []})
+            sc["frames"].append({"actions": acts, "checks": [], "series": []})
         elif t[0] == "ch":
             grid = np.array([[float(x) for x in ln.split()] for ln in lines[i + 1:i + 1 + H]]).reshape(-1)
             sc["frames"][-1]["checks"].append((int(t[1]), int(t[2]), grid))
@@ -80,7 +86,7 @@ def test_feature_golden(name):
     env = OracleEnv([sc["H"]], [sc["W"]], [sc["mode"]], [sc["P"]], auto_reset=0)
     army, owner, terrain = sc["board"]
     env.set_game(0, army, owner, terrain, turn=sc["turn"])
-    fb = OracleFeatures(env, hist=sc["hist"])
+    fb = OracleFeatures(env, hist=sc["hist"], window=sc.get("window", 0))
     n_checks = 0
     for k, fr in enumerate(sc["frames"]):
         if fr["actions"] is not None:
@@ -91,6 +97,9 @@ def test_feature_golden(name):
             got = feats[p, ch].astype(np.float64)
             np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9,
                                        err_msg=f"{name}: frame {k} player {p} channel {ch}")
+            n_checks += 1
+        for p, k, army, land in fr["series"]:
+            assert tuple(fb.series[0][p, k]) == (army, land), (name, k, p, fb.series[0][p, k])
             n_checks += 1
     assert n_checks > 10
 
@@ -116,9 +125,10 @@ def test_feature_invariants(mode, P, side):
     G = 4
     H = rng.integers(side[0], side[1] + 1, G)
     W = rng.integers(side[0], side[1] + 1, G)
-    hist = 4
+    hist, window = 4, 16
     env = OracleEnv(H, W, np.full(G, mode), np.full(G, P), seed=5 + mode, n_cities=3, max_turns=37)
-    fb = OracleFeatures(env, hist=hist)
+    fb = OracleFeatures(env, hist=hist, window=window)
+    series = {}      # (g, p) -> recorded (opponents' army, land), newest first
     own_hist = {}    # (g, p) -> planes, newest first, of this episode
     enemy_hist = {}
     prev = {}
@@ -136,6 +146,7 @@ def test_feature_invariants(mode, P, side):
                 for p in range(P):
                     own_hist.pop((g, p), None)
                     enemy_hist.pop((g, p), None)
+                    series.pop((g, p), None)
                     prev.pop((g, p), None)
             army, owner, terrain = env.board(g)
             land, tot = env.scoreboard(g)
@@ -160,6 +171,12 @@ def test_feature_invariants(mode, P, side):
                 assert f[16][0] == land[p] and f[17][0] == tot[p]
                 assert f[18][0] == sum(land[q] for q in oppq) and f[19][0] == sum(tot[q] for q in oppq)
                 assert np.all(f[14] == sc["turn"])
+                # temporal tokens: this frame's opponents' totals first, then the recorded past, zeros before
+                rec = [(sum(tot[q] for q in oppq), sum(land[q] for q in oppq))] + series.get((g, p), [])
+                series[(g, p)] = rec[:window]
+                want = np.zeros((window, 2), np.int64)
+                want[:len(series[(g, p)])] = series[(g, p)]
+                np.testing.assert_array_equal(fb.series[g][p], want)
                 # memory
                 assert np.all(f[4] >= vis)
                 assert np.all(f[5] >= (vis & opp))
