@@ -513,17 +513,18 @@ def run_features(args, rank, world, local):
     torch.cuda.set_device(local)
     H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=args.games or None)
     G = int(H.shape[0])
-    hist = 7
+    hist, window = 7, 512
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
-    fb = env.features(hist)
+    fb = env.features(hist, window)
     out = env.new_outputs()
     acts = env.new_actions()
     fout = fb.new_output()
+    ser = fb.new_series()
     stream = torch.cuda.current_stream()
     env.policy(POLICY_SEED, acts)
     for _ in range(max(3, args.warmup)):
         env.step_policy(acts, out, POLICY_SEED, acts)
-        fb.build(fout)
+        fb.build(fout, ser)
     torch.cuda.synchronize()
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
@@ -536,7 +537,7 @@ def run_features(args, rank, world, local):
             ev[k][0].record(stream)
             env.step_policy(acts, out, POLICY_SEED, acts)
             ev[k][1].record(stream)
-            fb.build(fout)
+            fb.build(fout, ser)
             ev[k][2].record(stream)
         t_all[1].record(stream)
         torch.cuda.synchronize()
@@ -546,16 +547,19 @@ def run_features(args, rank, world, local):
     feat_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     value = sum_over_ranks(float(G * K), world) / (elapsed_ms * 1e-3)
     cells = 2 * 576 * G
-    nbytes = feature_bytes_per_player_cell(hist, 2) * cells
+    # + temporal tokens per player: T - 1 ring entries read, one written, T written out (8 B each)
+    nbytes = feature_bytes_per_player_cell(hist, 2) * cells + 2 * G * 8 * (2 * window)
     peak, peak_kind = peaks()
     achieved = nbytes / (feat_ms * 1e-3) / 1e9
     if rank == 0:
         line = {
-            "metric": "game frames/s with the 38-channel feature tensor", "value": value, "unit": "frames/s",
+            "metric": "game frames/s with the 38-channel feature tensor and temporal tokens", "value": value,
+            "unit": "frames/s",
             "n_gpus": world, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
             "config": {"workload": "features-65536x24x24", "games_per_gpu": G, "hist": hist, "channels": 24 + 2 * hist,
+                       "temporal_window": window,
                        "l2": "inputs larger than L2 (features 11.5 GB + memory 2.9 GB per frame)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (FEATURE_NCU_TRAFFIC["bytes_per_launch"]

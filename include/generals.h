@@ -355,13 +355,30 @@ typedef struct gen_features gen_features;
  * NULL env or hist out of range, GEN_ERR_CUDA when allocation fails. */
 int gen_features_create(gen_features **out, gen_env *env, int hist);
 
+/* As gen_features_create, with the temporal tokens of App. A: per player
+ * the opponents' summed army and land (public scoreboard) of the last
+ * `window` builder frames (the paper's window: 512), kept in a device ring
+ * of window int32 pairs per player.  window in [0, 4096]; 0 = none. */
+int gen_features_create_ex(gen_features **out, gen_env *env, int hist, int window);
+
 /* Channels C and the number of floats the output buffer must hold. */
 int gen_features_layout(const gen_features *f, int32_t *channels, int64_t *n_floats);
+
+/* Window T and the int32 count of the temporal-token output:
+ * player_slots * T * 2. */
+int gen_features_series_layout(const gen_features *f, int32_t *window, int64_t *n_ints);
 
 /* Fold the current frame into the memory and write every player's features
  * to d_out (device, 16-byte aligned, n_floats floats).  Asynchronous on
  * `stream`; order it after the step that produced the frame. */
 int gen_features_build(gen_features *f, float *d_out, void *stream);
+
+/* As gen_features_build, also writing the temporal tokens to d_series
+ * (device, 8-byte aligned, NULL: not written): player slot s holds T
+ * (army, land) int32 pairs at s * T * 2, entry k = k frames back (newest
+ * first), 0 before the episode.  GEN_ERR_BAD_ARG when d_series is given to a
+ * builder created without a window. */
+int gen_features_build_ex(gen_features *f, float *d_out, int32_t *d_series, void *stream);
 
 void gen_features_destroy(gen_features *f);
 

@@ -807,26 +807,32 @@ int gen_set_spawn_range(gen_env* e, int min_dist, int max_dist) {
 struct gen_features {
     gen_env* env = nullptr;
     int hist = 0;
+    int window = 0;
     void* d_mem = nullptr;  // one allocation: headers, masks, last army, last turn, ring
     gk::FArgs args{};
 };
 
-int gen_features_create(gen_features** out, gen_env* e, int hist) {
+int gen_features_create(gen_features** out, gen_env* e, int hist) { return gen_features_create_ex(out, e, hist, 0); }
+
+int gen_features_create_ex(gen_features** out, gen_env* e, int hist, int window) {
     if (!out) return fail(GEN_ERR_BAD_ARG, "out is NULL");
     *out = nullptr;
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (hist < 1 || hist > 16) return fail(GEN_ERR_BAD_ARG, "hist %d outside [1, 16]", hist);
+    if (window < 0 || window > 4096) return fail(GEN_ERR_BAD_ARG, "window %d outside [0, 4096]", window);
     const int64_t pc = e->plane_cells;
     const size_t hdr = (size_t)e->player_slots * sizeof(uint4);
     const size_t bits = ((size_t)pc + 15) & ~(size_t)15;
     const size_t army = ((size_t)pc * 2 + 15) & ~(size_t)15;
     const size_t turn = (size_t)pc * 4;
     const size_t ring = (size_t)(hist + 1) * 2 * (size_t)pc * 2;
+    const size_t series = (size_t)e->player_slots * (size_t)window * sizeof(int2);
     auto* f = new gen_features();
     f->env = e;
     f->hist = hist;
+    f->window = window;
     char* m = nullptr;
-    cudaError_t ce = cudaMalloc(&m, hdr + bits + army + turn + ring);
+    cudaError_t ce = cudaMalloc(&m, hdr + bits + army + turn + ring + series);
     if (ce != cudaSuccess) {
         delete f;
         return cuda_fail(ce, "cudaMalloc feature memory");
@@ -852,7 +858,17 @@ int gen_features_create(gen_features** out, gen_env* e, int hist) {
     a.mem_turn = reinterpret_cast<int32_t*>(m + hdr + bits + army);
     a.ring = reinterpret_cast<int16_t*>(m + hdr + bits + army + turn);
     a.npad_max = e->npad_max;
+    a.window = window;
+    a.series_ring = window > 0 ? reinterpret_cast<int2*>(m + hdr + bits + army + turn + ring) : nullptr;
+    a.series_out = nullptr;
     *out = f;
+    return GEN_OK;
+}
+
+int gen_features_series_layout(const gen_features* f, int32_t* window, int64_t* n_ints) {
+    if (!f) return fail(GEN_ERR_BAD_ARG, "features is NULL");
+    if (window) *window = f->window;
+    if (n_ints) *n_ints = (int64_t)f->env->player_slots * f->window * 2;
     return GEN_OK;
 }
 
@@ -865,10 +881,17 @@ int gen_features_layout(const gen_features* f, int32_t* channels, int64_t* n_flo
 }
 
 int gen_features_build(gen_features* f, float* d_out, void* stream) {
+    return gen_features_build_ex(f, d_out, nullptr, stream);
+}
+
+int gen_features_build_ex(gen_features* f, float* d_out, int32_t* d_series, void* stream) {
     if (!f || !d_out) return fail(GEN_ERR_BAD_ARG, "NULL argument");
     if (reinterpret_cast<uintptr_t>(d_out) & 15u) return fail(GEN_ERR_BAD_ARG, "d_out is not 16-byte aligned");
+    if (d_series && f->window == 0) return fail(GEN_ERR_BAD_ARG, "this builder has no temporal window");
+    if (reinterpret_cast<uintptr_t>(d_series) & 7u) return fail(GEN_ERR_BAD_ARG, "d_series is not 8-byte aligned");
     gk::FArgs a = f->args;
     a.out = d_out;
+    a.series_out = reinterpret_cast<int2*>(d_series);
     const int rc = gk::launch_features(a, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, "feature launch");
     return GEN_OK;

@@ -229,9 +229,28 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
         const uint4 h = f.hdr[slot];
         const bool cleared = h.x != sc.epoch + 1u;
         const bool fold = cleared || h.y != sc.frame;
-        const int nvalid_old = cleared ? 0 : (int)h.w;
-        const int head = fold ? (cleared ? 0 : (int)((h.z + 1u) % (uint32_t)R)) : (int)h.z;
-        const int nvalid = fold ? min(nvalid_old + 1, R) : nvalid_old;
+        const uint32_t n_fold = (cleared ? 0u : h.z) + (fold ? 1u : 0u);  // frames folded this episode
+        const int head = (int)((n_fold - 1u) % (uint32_t)R);             // ring slot of this frame
+        const int nvalid = (int)min(n_fold, (uint32_t)R);
+
+        // temporal tokens (App. A): opponents' army and land, newest first
+        if (f.window > 0) {
+            const uint32_t T = (uint32_t)f.window;
+            int2* ring = f.series_ring + (int64_t)slot * T;
+            if (fold && lane == 0) ring[(n_fold - 1u) % T] = make_int2(opp_army, opp_land);
+            if (f.series_out) {
+                int2* so = f.series_out + (int64_t)slot * T;
+                const uint32_t valid = min(n_fold, T);
+                for (uint32_t k = lane; k < T; k += 32) {
+                    int2 v = make_int2(0, 0);
+                    if (k == 0)
+                        v = make_int2(opp_army, opp_land);
+                    else if (k < valid)
+                        v = ring[(n_fold - 1u - k) % T];
+                    so[k] = v;
+                }
+            }
+        }
 
         const int64_t q0 = gi.plane_off + (int64_t)p * Npad;  // this player's plane
         float* out = f.out + q0 * C;
@@ -349,7 +368,7 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
                 pe = ne;
             }
         }
-        if (fold && lane == 0) f.hdr[slot] = make_uint4(sc.epoch + 1u, sc.frame, (uint32_t)head, (uint32_t)nvalid);
+        if (fold && lane == 0) f.hdr[slot] = make_uint4(sc.epoch + 1u, sc.frame, n_fold, 0u);
         __syncwarp();
     }
 }

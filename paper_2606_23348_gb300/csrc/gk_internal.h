@@ -100,13 +100,16 @@ struct FArgs {
     int32_t n_games;
     int32_t hist;          // delta history length K: channels 24 + 2K
     int64_t plane_cells;   // cells of the per-player plane set
-    uint4* hdr;            // per player slot: epoch + 1 folded (0: none), frame folded, ring head, valid planes
+    uint4* hdr;            // per player slot: epoch + 1 folded (0: none), frame folded, frames folded this episode
     uint8_t* mem_bits;     // per plane cell: bit 0 seen, 1 enemy seen, 2 general, 3 castle, 4 mountain
     int16_t* mem_army;     // per plane cell: last enemy army seen
     int32_t* mem_turn;     // per plane cell: turn an enemy was last seen
     int16_t* ring;         // [(K + 1) * 2][plane_cells]: own / enemy army planes of folded frames
     float* out;            // player plane q = plane_off + p * Npad: channel ch of cell c at q * C + ch * Npad + c
     int32_t npad_max;      // largest board (cells, multiple of 16)
+    int32_t window;        // temporal-token window T (0: none)
+    int2* series_ring;     // [slot][T]: (opponents' army, land), entry (n - 1) mod T = the n-th folded frame
+    int2* series_out;      // optional [slot][T]: newest first, 0 before the episode
 };
 
 // Launch the feature builder over every game on `stream`.  Returns a cudaError_t.

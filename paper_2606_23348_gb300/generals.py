@@ -59,7 +59,8 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_step", "gen_step_policy", "gen_policy", "gen_rollout", "gen_step_host", "gen_read_state",
            "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
            "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
-           "gen_features_build", "gen_features_destroy")
+           "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
+           "gen_features_build_ex")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -98,6 +99,9 @@ def load_library(path: str = LIB_PATH):
             "gen_features_layout": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int64)]),
             "gen_features_build": (C.c_int, [vp, vp, vp]),
             "gen_features_destroy": (None, [vp]),
+            "gen_features_create_ex": (C.c_int, [C.POINTER(vp), vp, C.c_int, C.c_int]),
+            "gen_features_series_layout": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int64)]),
+            "gen_features_build_ex": (C.c_int, [vp, vp, vp, vp]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
         }
@@ -272,9 +276,10 @@ class GeneralsEnv:
     def set_spawn_range(self, min_dist: int, max_dist: int):
         _check(self.lib.gen_set_spawn_range(self.h, int(min_dist), int(max_dist)), "gen_set_spawn_range")
 
-    def features(self, hist: int = 7) -> "Features":
-        """Feature-tensor builder over this environment (App. A)."""
-        return Features(self, hist)
+    def features(self, hist: int = 7, window: int = 0) -> "Features":
+        """Feature-tensor builder over this environment (App. A); window > 0
+        adds the temporal tokens (opponents' army and land, newest first)."""
+        return Features(self, hist, window)
 
     def set_launch(self, warps_per_cta: int):
         _check(self.lib.gen_set_launch(self.h, int(warps_per_cta)), "gen_set_launch")
@@ -317,28 +322,47 @@ class Features:
     [G][P][C][H*W]); call it after every step.
     """
 
-    def __init__(self, env: GeneralsEnv, hist: int = 7):
+    def __init__(self, env: GeneralsEnv, hist: int = 7, window: int = 0):
         self.env = env
         self.lib = env.lib
         h = C.c_void_p()
-        _check(self.lib.gen_features_create(C.byref(h), env.h, int(hist)), "gen_features_create")
+        _check(self.lib.gen_features_create_ex(C.byref(h), env.h, int(hist), int(window)), "gen_features_create_ex")
         self.h = h
         ch, n = C.c_int32(), C.c_int64()
         _check(self.lib.gen_features_layout(h, C.byref(ch), C.byref(n)), "gen_features_layout")
         self.channels, self.n_floats, self.hist = int(ch.value), int(n.value), int(hist)
+        w, ns = C.c_int32(), C.c_int64()
+        _check(self.lib.gen_features_series_layout(h, C.byref(w), C.byref(ns)), "gen_features_series_layout")
+        self.window, self.n_series = int(w.value), int(ns.value)
 
     def new_output(self):
         import torch
         return torch.empty(self.n_floats, dtype=torch.float32, device="cuda")
 
-    def build(self, out=None):
+    def new_series(self):
+        import torch
+        return torch.empty(self.n_series, dtype=torch.int32, device="cuda")
+
+    def build(self, out=None, series=None):
+        """Features into `out` (allocated when None); with `series` (a tensor
+        of n_series int32) the temporal tokens too."""
         if self.env.h is None:
             raise GeneralsError("the environment of this feature builder is closed")
         if out is None:
             out = self.new_output()
         assert out.numel() >= self.n_floats and out.dtype.itemsize == 4 and out.is_cuda
-        _check(self.lib.gen_features_build(self.h, C.c_void_p(out.data_ptr()), _cur_stream()), "gen_features_build")
+        sp = None
+        if series is not None:
+            assert series.numel() >= self.n_series and series.dtype.itemsize == 4 and series.is_cuda
+            sp = C.c_void_p(series.data_ptr())
+        _check(self.lib.gen_features_build_ex(self.h, C.c_void_p(out.data_ptr()), sp, _cur_stream()),
+               "gen_features_build_ex")
         return out
+
+    def player_series(self, series, g: int, p: int):
+        """[T][2] (army, land) view of game g, player p inside a series output."""
+        s = int(self.env.player_off[g]) + p
+        return series[s * 2 * self.window:(s + 1) * 2 * self.window].view(self.window, 2)
 
     def player_view(self, out, g: int, p: int):
         """[C][H_g * W_g] view of game g, player p inside a build() output."""

@@ -30,6 +30,20 @@ def _built():
     build_library()
 
 
+def compare_series(env, fb, series, want, tag, games=None):
+    """Temporal tokens: exact int32 equality per player slot."""
+    import torch
+    torch.cuda.synchronize()
+    got = series.cpu().numpy()
+    games = range(env.G) if games is None else games
+    T = fb.window
+    for k, g in enumerate(games):
+        for p in range(int(env.P[g])):
+            s = int(env.player_off[g]) + p
+            np.testing.assert_array_equal(got[s * 2 * T:(s + 1) * 2 * T].reshape(T, 2), want[k][p],
+                                          err_msg=f"{tag} game {g} player {p}: temporal tokens")
+
+
 def compare_features(env, fb, out, want, tag, games=None, orc_index=None):
     import torch
     torch.cuda.synchronize()
@@ -57,9 +71,12 @@ def lockstep(env, orc, fb, ofb, frames, policy_seed, tag, every=1, subset_reset=
     out = env.new_outputs()
     acts = env.new_actions()
     fout = fb.new_output()
+    ser = fb.new_series() if fb.window else None
     env.observe(out)
-    fb.build(fout)
+    fb.build(fout, ser)
     compare_features(env, fb, fout, ofb.build(), f"{tag} create")
+    if ser is not None:
+        compare_series(env, fb, ser, ofb.series, f"{tag} create")
     env.policy(policy_seed, acts)
     for f in range(frames):
         a = orc.policy(policy_seed)
@@ -70,32 +87,34 @@ def lockstep(env, orc, fb, ofb, frames, policy_seed, tag, every=1, subset_reset=
             env.reset(out, torch.from_numpy(ids).cuda())
             orc.reset(ids)
             env.policy(policy_seed, acts)  # the reset games' actions come from their new maps
-        fb.build(fout)
+        fb.build(fout, ser)
         want = ofb.build()
         if (f + 1) % every == 0 or f == frames - 1:
             compare_features(env, fb, fout, want, f"{tag} frame {f + 1}")
+            if ser is not None:
+                compare_series(env, fb, ser, ofb.series, f"{tag} frame {f + 1}")
     return fout
 
 
-def pair(H, W, mode, P, hist=7, **kw):
+def pair(H, W, mode, P, hist=7, window=0, **kw):
     from paper_2606_23348_gb300.generals import GeneralsEnv
     env = GeneralsEnv(H, W, mode, P, **kw)
     orc = OracleEnv(H, W, mode, P, **kw)
-    return env, orc, env.features(hist), OracleFeatures(orc, hist)
+    return env, orc, env.features(hist, window), OracleFeatures(orc, hist, window)
 
 
 def test_features_mixed_modes_with_resets():
     """Ragged 1v1 / 2v2 / FFA boards, truncation resets every 25 turns, every frame compared."""
     G = 24
     H, W, mode, P = shapes(G, (4, 12), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=8)
-    env, orc, fb, ofb = pair(H, W, mode, P, seed=4, n_cities=2, max_turns=25)
+    env, orc, fb, ofb = pair(H, W, mode, P, window=32, seed=4, n_cities=2, max_turns=25)
     lockstep(env, orc, fb, ofb, 80, 6, "mixed")
 
 
-@pytest.mark.parametrize("hist", [1, 16])
-def test_features_history_lengths(hist):
+@pytest.mark.parametrize("hist,window", [(1, 512), (16, 1)])
+def test_features_history_lengths(hist, window):
     H, W, mode, P, gen, _ = workload("1v1-64x15x15")
-    env, orc, fb, ofb = pair(H[:16], W[:16], mode[:16], P[:16], hist=hist, seed=1, **gen)
+    env, orc, fb, ofb = pair(H[:16], W[:16], mode[:16], P[:16], hist=hist, window=window, seed=1, **gen)
     assert fb.channels == 24 + 2 * hist
     lockstep(env, orc, fb, ofb, 30, 3, f"hist {hist}", every=3)
 
@@ -104,7 +123,7 @@ def test_features_subset_reset_and_repeat_build():
     """A reset of some games clears their memory; a second build in one frame changes nothing."""
     G = 12
     H, W, mode, P = shapes(G, (6, 9), ((0, 0.5), (2, 0.5)), seed=2)
-    env, orc, fb, ofb = pair(H, W, mode, P, seed=3, n_cities=2)
+    env, orc, fb, ofb = pair(H, W, mode, P, window=7, seed=3, n_cities=2)
     fout = lockstep(env, orc, fb, ofb, 20, 5, "subset", subset_reset=[0, 5, 11])
     again = fb.build()
     import torch
@@ -114,7 +133,7 @@ def test_features_subset_reset_and_repeat_build():
 
 @pytest.mark.parametrize("H,W,mode,P", [(1, 2, 0, 2), (40, 1, 2, 3), (33, 5, 1, 4), (64, 64, 2, 8), (3, 3, 2, 8)])
 def test_features_edge_shapes(H, W, mode, P):
-    env, orc, fb, ofb = pair([H, H], [W, W], [mode, mode], [P, P], seed=5, n_cities=1, max_turns=15)
+    env, orc, fb, ofb = pair([H, H], [W, W], [mode, mode], [P, P], window=3, seed=5, n_cities=1, max_turns=15)
     lockstep(env, orc, fb, ofb, 20, 9, f"edge {H}x{W}", every=4)
 
 
@@ -138,14 +157,18 @@ def test_feature_golden_on_gpu(path):
     pad = lambda x, v: np.concatenate([x, np.full(npad - x.shape[0], v, x.dtype)])
     scal = np.array([[sc["turn"], 0, 0, (1 << P) - 1, 0, 0, 0, 0]], np.uint32)
     env.write_state(pad(army, 0), pad(owner, -1), pad(terrain, 0), scal)
-    fb = env.features(sc["hist"])
+    fb = env.features(sc["hist"], sc.get("window", 0))
     out = env.new_outputs()
+    ser = fb.new_series() if fb.window else None
     n = 0
     for fr in sc["frames"]:
         if fr["actions"] is not None:
             env.step(torch.from_numpy(fr["actions"][:P].copy()).cuda(), out)
-        f = fb.build()
+        f = fb.build(series=ser)
         torch.cuda.synchronize()
+        for p, k, army, land in fr["series"]:
+            assert tuple(fb.player_series(ser, 0, p)[k].tolist()) == (army, land)
+            n += 1
         for p, ch, want in fr["checks"]:
             got = fb.player_view(f, 0, p)[ch].cpu().numpy().astype(np.float64)
             np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9, err_msg=f"player {p} channel {ch}")
@@ -160,24 +183,26 @@ def test_features_full_size_24x24_65536_sampled():
     from paper_2606_23348_gb300.generals import GeneralsEnv
     H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
     env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
-    fb = env.features(7)
+    fb = env.features(7, 512)
     out = env.new_outputs()
     acts = env.new_actions()
     fout = fb.new_output()
+    ser = fb.new_series()
     env.policy(2, acts)
-    fb.build(fout)
+    fb.build(fout, ser)
     frames = 12
     for f in range(frames):
         env.step_policy(acts, out, 2, acts)
-        fb.build(fout)
+        fb.build(fout, ser)
     torch.cuda.synchronize()
     for start in (0, 40000, 65536 - 32):
         n = 32
         orc = OracleEnv(H[start:start + n], W[start:start + n], mode[start:start + n], P[start:start + n], seed=1,
                         game_id_base=start, **gen)
-        ofb = OracleFeatures(orc, 7)
+        ofb = OracleFeatures(orc, 7, 512)
         ofb.build()
         for f in range(frames):
             orc.step(orc.policy(2))
             want = ofb.build()
         compare_features(env, fb, fout, want, f"full size block {start}", games=range(start, start + n))
+        compare_series(env, fb, ser, ofb.series, f"full size block {start}", games=range(start, start + n))
