@@ -944,3 +944,97 @@ void orc_feat_build(orc_feat *f, float *out, int32_t *series) {
             soff += 2 * (size_t)f->window;
         }
 }
+
+/* ======================================================================
+ * Policy sampling over the H x W x 9 action space (Sec. IV-G; App. C: the
+ * policy head's H x W x 9 distribution).  Readings (Q35-Q37 in the design
+ * notes):
+ *   Q35 legal entries of player p: (c, 0) pass where p owns c; (c, 1 + d)
+ *       all-but-one and (c, 5 + d) half where the move is legal (as the
+ *       compact mask); a player with no legal entry passes (action 0);
+ *   Q36 the categorical is exp(logit) over legal entries, sampled exactly
+ *       with integer weights: m = max legal logit, w = floor(E(l - m) 2^24)
+ *       with E the exponential below, r = floor(d * S / 2^64) for the
+ *       64-bit draw d and S the sum of weights, and the first entry in
+ *       index order whose running weight sum exceeds r;
+ *   Q37 E(x) = 2^n * P(f) with t = x * log2(e) rounded to float, n =
+ *       floor(t), f = t - n, and P the degree-7 Taylor polynomial of 2^f,
+ *       sum of (f ln 2)^k / k!, in Horner form with fused multiply-adds;
+ *       E = 0 below t = -25 (the weight would be 0).  Every step is an
+ *       IEEE single-precision operation, so the result is reproducible.
+ * The draw: d = sm(key(seed, global game id, frame, p), 7), the frame of
+ * the step that consumes the action.
+ * ====================================================================== */
+static float orc_exp_q37(float x) {
+    const float t = x * 1.4426950408889634f;
+    if (t < -25.0f) return 0.0f;
+    const float n = floorf(t);
+    const float f = t - n;
+    float p = 1.5252733804059838e-05f;
+    p = fmaf(p, f, 0.00015403530393381606f);
+    p = fmaf(p, f, 0.0013333558146428441f);
+    p = fmaf(p, f, 0.009618129107628477f);
+    p = fmaf(p, f, 0.055504108664821576f);
+    p = fmaf(p, f, 0.2402265069591007f);
+    p = fmaf(p, f, 0.6931471805599453f);
+    p = fmaf(p, f, 1.0f);
+    return ldexpf(p, (int)n);
+}
+
+/* the exponential of Q37, for the pins */
+float orc_exp37(float x) { return orc_exp_q37(x); }
+
+static uint64_t orc_mulhi64(uint64_t a, uint64_t b) {
+    const uint64_t a0 = a & 0xFFFFFFFFu, a1 = a >> 32, b0 = b & 0xFFFFFFFFu, b1 = b >> 32;
+    const uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+    const uint64_t mid = (p00 >> 32) + (p01 & 0xFFFFFFFFu) + (p10 & 0xFFFFFFFFu);
+    return p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+/* legal entry (c, k) of player p (Q35) */
+static int orc_entry_legal(const orc_game *g, int p, int c, int k) {
+    if (k == 0) return g->owner[c] == p;
+    if (g->finished) return 0;
+    return orc_move_legal(g, p, c, (k - 1) & 3);
+}
+
+/* logits: per game and player (in order) N * 9 floats; actions [G][8];
+ * mask9 (may be NULL): per game and player N * 9 bytes of legal entries */
+void orc_sample_actions(const orc_env *e, const float *logits, uint64_t seed, int32_t *actions, uint8_t *mask9) {
+    size_t off = 0;
+    for (int g = 0; g < e->G; ++g) {
+        const orc_game *gm = &e->games[g];
+        const uint64_t gid = e->prm.game_id_base + (uint64_t)g;
+        for (int p = 0; p < 8; ++p) actions[8 * g + p] = 0;
+        for (int p = 0; p < gm->P; ++p) {
+            const float *l = logits + off;
+            const int n9 = 9 * gm->N;
+            int any = 0;
+            float m = 0.0f;
+            for (int i = 0; i < n9; ++i) {
+                const int legal = orc_entry_legal(gm, p, i / 9, i % 9);
+                if (mask9) mask9[off + i] = (uint8_t)legal;
+                if (legal && (!any || l[i] > m)) m = l[i];
+                if (legal) any = 1;
+            }
+            if (any) {
+                uint64_t S = 0;
+                for (int i = 0; i < n9; ++i)
+                    if (orc_entry_legal(gm, p, i / 9, i % 9))
+                        S += (uint64_t)floorf(orc_exp_q37(l[i] - m) * 16777216.0f);
+                const uint64_t d = orc_sm(orc_key(seed, gid, gm->frame, (uint64_t)p), 7);
+                const uint64_t r = orc_mulhi64(d, S);
+                uint64_t run = 0;
+                for (int i = 0; i < n9; ++i) {
+                    if (!orc_entry_legal(gm, p, i / 9, i % 9)) continue;
+                    run += (uint64_t)floorf(orc_exp_q37(l[i] - m) * 16777216.0f);
+                    if (run > r) {
+                        actions[8 * g + p] = i;
+                        break;
+                    }
+                }
+            }
+            off += (size_t)n9;
+        }
+    }
+}

@@ -81,6 +81,9 @@ def oracle_lib():
             lib.orc_feat_new.argtypes = [P(C.c_void_p), C.c_void_p, C.c_int32, C.c_int32]
             lib.orc_feat_free.argtypes = [C.c_void_p]
             lib.orc_feat_build.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.orc_sample_actions.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
+            lib.orc_exp37.restype = C.c_float
+            lib.orc_exp37.argtypes = [C.c_float]
             _lib = lib
     return _lib
 
@@ -194,6 +197,21 @@ class OracleEnv:
         self.lib.orc_get_scoreboard(self.h, g, _ptr(land), _ptr(army))
         return land, army
 
+    def sample_actions(self, logits, seed: int):
+        """Sample one action per player from per-game [P][N * 9] float32 logits
+        (a list over games).  Returns (actions [G][8] int32, list over games
+        of [P][N * 9] uint8 legal-entry masks)."""
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(l, np.float32).reshape(-1) for l in logits]))
+        mask = np.zeros(flat.shape[0], np.uint8)
+        acts = np.zeros((self.G, MAXP), np.int32)
+        self.lib.orc_sample_actions(self.h, _ptr(flat), int(seed), _ptr(acts), _ptr(mask))
+        res, off = [], 0
+        for P, N in zip(self.P, self.N):
+            n = int(P) * 9 * int(N)
+            res.append(mask[off:off + n].reshape(int(P), 9 * int(N)))
+            off += n
+        return acts, res
+
     def set_game(self, g: int, army, owner, terrain, *, turn=0, alive=None, frame=0, epoch=0):
         army = np.ascontiguousarray(army, np.int16)
         owner = np.ascontiguousarray(owner, np.int8)
@@ -248,3 +266,8 @@ class OracleFeatures:
             res.append(out[off:off + n].reshape(int(P), self.C, int(N)))
             off += n
         return res
+
+
+def exp37(x: float) -> float:
+    """The reproducible single-precision exponential used by the sampler."""
+    return float(oracle_lib().orc_exp37(float(x)))
