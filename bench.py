@@ -576,6 +576,71 @@ def run_features(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_sampling(args, rank, world, local):
+    """Device self-play shape: per frame, actions sampled from H x W x 9
+    logits (k_sample), then the step (k_generals without the fused policy)."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import shard, workload
+
+    torch.cuda.set_device(local)
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=args.games or None)
+    G = int(H.shape[0])
+    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
+    out = env.new_outputs()
+    acts = env.new_actions()
+    g = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    logits = torch.randn(int(env.layout.plane_cells) * 9, generator=g, device="cuda") * 2.0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        env.sample_actions(logits, POLICY_SEED, acts)
+        env.step(acts, out)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        t_all[0].record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            env.sample_actions(logits, POLICY_SEED, acts)
+            ev[k][1].record(stream)
+            env.step(acts, out)
+            ev[k][2].record(stream)
+        t_all[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    elapsed_ms = max_over_ranks(t_all[0].elapsed_time(t_all[1]), world)
+    samp_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    step_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    value = sum_over_ranks(float(G * K), world) / (elapsed_ms * 1e-3)
+    # logits 36 B per plane cell, board 4 B per cell (once per game), actions 4 B per player
+    nbytes = 36.0 * 2 * 576 * G + 4.0 * 576 * G + 4.0 * 2 * G
+    peak, peak_kind = peaks()
+    achieved = nbytes / (samp_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "game frames/s, actions sampled on the device from H x W x 9 logits", "value": value,
+            "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 logits, int16 state",
+            "data": "synthetic (seeded counter-hash maps, N(0, 2) logits, auto-reset)",
+            "config": {"workload": "sample-65536x24x24", "games_per_gpu": G,
+                       "l2": "inputs larger than L2 (logits 2.7 GB)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_launch": nbytes, "launch_ms": samp_ms,
+                         "kernel": "k_sample (H x W x 9 policy sampling)"},
+            "step_launch_ms": step_ms,
+            "gpu_launches": 2 * K,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_generator(args, rank, world, local):
     """Map generation throughput: gen_reset of every game of the default
     workload's shapes, for each generator option set."""
@@ -659,6 +724,8 @@ def main():
             run_generator(args, rank, world, local)
         elif args.workload == "features-65536x24x24":
             run_features(args, rank, world, local)
+        elif args.workload == "sample-65536x24x24":
+            run_sampling(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

@@ -325,6 +325,27 @@ typedef struct gen_sim_config {
 int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_server_stats *st);
 
 /* Reason for the last failure on this thread (never NULL). */
+/* ---- policy sampling over the H x W x 9 action space (Sec. IV-G, App. C) --
+ * Logits: player plane q = plane_off[g] + p * Npad_g holds 9 * Npad_g float32
+ * at q * 9, entry c * 9 + k for cell c and k = 0 pass, 1..4 all-but-one up,
+ * down, left, right, 5..8 half (the action encoding of gen_step); entries of
+ * padding cells are ignored.  Logits must be finite.
+ * Legal entries of player p: (c, 0) where p owns c; (c, 1 + d) and (c, 5 + d)
+ * where the move is legal (the compact mask's bits d and 4 + d).  The action
+ * is drawn from exp(logit) over the legal entries by an exact integer
+ * inverse CDF (weights floor(E(l - max) * 2^24) with a bit-reproducible
+ * single-precision exponential E), keyed by (seed, global game id, frame of
+ * the step that will consume it, p); a player without a legal entry gets 0
+ * (pass).  The same logits and seed give the same actions on every device.
+ * d_actions: player_slots int32 (the layout gen_step reads).  d_mask9
+ * (optional, 4-byte aligned): the expanded legal mask, 9 * Npad_g bytes per
+ * player plane at q * 9, 1 = legal.  With d_logits and d_actions NULL only
+ * the mask is written.  Asynchronous on `stream`; order it after the step
+ * that produced the state.  GEN_ERR_BAD_ARG for NULL env, inconsistent
+ * pointers or misaligned buffers. */
+int gen_sample_actions(gen_env *env, const float *d_logits, uint64_t seed, int32_t *d_actions, uint8_t *d_mask9,
+                       void *stream);
+
 /* ---- feature tensor (App. A, table of observation channels) -------------
  * Per player C = 24 + 2 * hist float32 planes of Npad_g cells each, in the
  * table's order: 0 armies, 1 own army, 2 enemy army, 3 neutral army,

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgenerals.so")
-SOURCES = ["gk_kernels.cu", "gk_capi.cu", "gk_server.cu", "gk_features.cu"]
+SOURCES = ["gk_kernels.cu", "gk_capi.cu", "gk_server.cu", "gk_features.cu", "gk_sample.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -903,6 +903,30 @@ void gen_features_destroy(gen_features* f) {
     delete f;
 }
 
+int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t* d_actions, uint8_t* d_mask9,
+                       void* stream) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (!d_logits && d_actions) return fail(GEN_ERR_BAD_ARG, "actions need logits");
+    if (d_logits && !d_actions) return fail(GEN_ERR_BAD_ARG, "logits need an actions buffer");
+    if (!d_logits && !d_mask9) return fail(GEN_ERR_BAD_ARG, "nothing to compute");
+    if ((reinterpret_cast<uintptr_t>(d_logits) & 15u) || (reinterpret_cast<uintptr_t>(d_mask9) & 3u))
+        return fail(GEN_ERR_BAD_ARG, "logits must be 16-byte and mask9 4-byte aligned");
+    gk::SArgs a{};
+    a.info = e->d_info;
+    a.army = e->d_army;
+    a.owner = e->d_owner;
+    a.terrain = e->d_terrain;
+    a.scal = e->d_scal;
+    a.n_games = e->G;
+    a.logits = d_logits;
+    a.seed = seed;
+    a.actions = d_actions;
+    a.mask9 = d_mask9;
+    const int rc = gk::launch_sample(a, stream);
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "sampler launch");
+    return GEN_OK;
+}
+
 int gen_set_launch(gen_env* e, int warps_per_cta) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)

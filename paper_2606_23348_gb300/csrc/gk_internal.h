@@ -115,6 +115,23 @@ struct FArgs {
 // Launch the feature builder over every game on `stream`.  Returns a cudaError_t.
 int launch_features(const FArgs& f, void* stream);
 
+// Policy sampling over the H x W x 9 action space: one warp per game.
+struct SArgs {
+    const GameInfo* info;
+    const int16_t* army;
+    const int8_t* owner;
+    const int8_t* terrain;  // type | passable-neighbour bits << 2
+    const GameScalars* scal;
+    int32_t n_games;
+    const float* logits;    // player plane q: 9 * Npad floats at q * 9 (NULL: mask only)
+    uint64_t seed;
+    int32_t* actions;       // [player slots] (NULL with logits NULL)
+    uint8_t* mask9;         // optional: 9 * Npad legal-entry bytes per player plane at q * 9
+};
+
+// Launch the sampler over every game on `stream`.  Returns a cudaError_t.
+int launch_sample(const SArgs& a, void* stream);
+
 // Bytes of shared memory one warp needs for games up to npad_max cells and
 // pmax players; also returns the bitset stride in words.
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride);

@@ -60,7 +60,7 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
            "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
            "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
-           "gen_features_build_ex")
+           "gen_features_build_ex", "gen_sample_actions")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
             "gen_features_create_ex": (C.c_int, [C.POINTER(vp), vp, C.c_int, C.c_int]),
             "gen_features_series_layout": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int64)]),
             "gen_features_build_ex": (C.c_int, [vp, vp, vp, vp]),
+            "gen_sample_actions": (C.c_int, [vp, vp, u64, vp, vp, vp]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
         }
@@ -276,6 +277,31 @@ class GeneralsEnv:
     def set_spawn_range(self, min_dist: int, max_dist: int):
         _check(self.lib.gen_set_spawn_range(self.h, int(min_dist), int(max_dist)), "gen_set_spawn_range")
 
+    def new_logits(self):
+        """Zero logits: 9 float32 per cell of every player plane."""
+        import torch
+        return torch.zeros(int(self.layout.plane_cells) * 9, dtype=torch.float32, device="cuda")
+
+    def sample_actions(self, logits, seed: int, actions=None, mask9=None):
+        """Draw one action per player from `logits` (9 per plane cell) into
+        `actions` (allocated when None); `mask9` (uint8, 9 per plane cell)
+        receives the expanded legal mask when given."""
+        if actions is None:
+            actions = self.new_actions()
+        mp = C.c_void_p(mask9.data_ptr()) if mask9 is not None else None
+        _check(self.lib.gen_sample_actions(self.h, C.c_void_p(logits.data_ptr()), int(seed),
+                                           C.c_void_p(actions.data_ptr()), mp, _cur_stream()), "gen_sample_actions")
+        return actions
+
+    def expand_mask(self, mask9=None):
+        """The expanded H x W x 9 legal mask of every player (uint8, 9 per plane cell)."""
+        import torch
+        if mask9 is None:
+            mask9 = torch.empty(int(self.layout.plane_cells) * 9, dtype=torch.uint8, device="cuda")
+        _check(self.lib.gen_sample_actions(self.h, None, 0, None, C.c_void_p(mask9.data_ptr()), _cur_stream()),
+               "gen_sample_actions")
+        return mask9
+
     def features(self, hist: int = 7, window: int = 0) -> "Features":
         """Feature-tensor builder over this environment (App. A); window > 0
         adds the temporal tokens (opponents' army and land, newest first)."""
@@ -356,7 +382,7 @@ class Features:
             assert series.numel() >= self.n_series and series.dtype.itemsize == 4 and series.is_cuda
             sp = C.c_void_p(series.data_ptr())
         _check(self.lib.gen_features_build_ex(self.h, C.c_void_p(out.data_ptr()), sp, _cur_stream()),
-               "gen_features_build_ex")
+               "gen_features_build_ex", "gen_sample_actions")
         return out
 
     def player_series(self, series, g: int, p: int):

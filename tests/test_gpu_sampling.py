@@ -1,0 +1,157 @@
+"""Policy sampling over the H x W x 9 action space and the expanded legal
+mask on the GPU vs the oracle, through the C-ABI.  Both sides draw with an
+exact integer inverse CDF over a bit-reproducible exponential, so actions
+and masks must agree exactly."""
+import numpy as np
+import pytest
+
+from gpu_helpers import compare_frame, flat_to_rows
+from oracle import OracleEnv
+from paper_2606_23348_gb300.workloads import shapes, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2606_23348_gb300.build import build_library
+    build_library()
+
+
+def oracle_logits(env, flat, games=None):
+    """Per game [P][N * 9] slices of the library's logits layout."""
+    games = range(env.G) if games is None else games
+    res = []
+    for g in games:
+        npad, N, P = int(env.npad[g]), int(env.N[g]), int(env.P[g])
+        rows = []
+        for p in range(P):
+            q = int(env.plane_off[g]) + p * npad
+            rows.append(flat[q * 9:q * 9 + 9 * N])
+        res.append(np.stack(rows))
+    return res
+
+
+def check_sample(env, orc, logits, seed, tag, games=None):
+    import torch
+    acts = env.new_actions()
+    mask9 = torch.full((int(env.layout.plane_cells) * 9,), 7, dtype=torch.uint8, device="cuda")
+    env.sample_actions(logits, seed, acts, mask9)
+    torch.cuda.synchronize()
+    flat = logits.cpu().numpy()
+    want_a, want_m = orc.sample_actions(oracle_logits(env, flat, games), seed)
+    got_a = flat_to_rows(env, acts.cpu().numpy())
+    m9 = mask9.cpu().numpy()
+    games = range(env.G) if games is None else games
+    for k, g in enumerate(games):
+        P, N, npad = int(env.P[g]), int(env.N[g]), int(env.npad[g])
+        np.testing.assert_array_equal(got_a[g, :P], want_a[k, :P], err_msg=f"{tag} game {g}: actions")
+        for p in range(P):
+            q = int(env.plane_off[g]) + p * npad
+            np.testing.assert_array_equal(m9[q * 9:q * 9 + 9 * N], want_m[k][p], err_msg=f"{tag} game {g} p {p}")
+            assert not m9[q * 9 + 9 * N:(q + npad) * 9].any(), f"{tag} game {g}: padding entries"
+    return acts
+
+
+def pair(H, W, mode, P, **kw):
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    return GeneralsEnv(H, W, mode, P, **kw), OracleEnv(H, W, mode, P, **kw)
+
+
+@pytest.mark.parametrize("scale", [0.0, 3.0, 40.0])
+def test_sampling_matches_oracle_mixed_modes(scale):
+    import torch
+    G = 30
+    H, W, mode, P = shapes(G, (3, 14), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=5)
+    env, orc = pair(H, W, mode, P, seed=8, n_cities=2)
+    acts = env.new_actions()
+    out = env.new_outputs()
+    env.policy(3, acts)
+    for f in range(15):
+        a = orc.policy(3)
+        env.step_policy(acts, out, 3, acts)
+        orc.step(a)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    for s in range(4):
+        logits = torch.randn(int(env.layout.plane_cells) * 9, generator=gen, device="cuda") * scale
+        check_sample(env, orc, logits, 100 + s, f"scale {scale} seed {s}")
+
+
+def test_device_rollout_from_logits():
+    """Self-play shape: logits -> sampled actions -> step, all on the device; the
+    oracle replays the same logits; every state and output compared."""
+    import torch
+    G = 20
+    H, W, mode, P = shapes(G, (5, 12), ((0, 0.5), (2, 0.5)), seed=6)
+    env, orc = pair(H, W, mode, P, seed=4, n_cities=2, max_turns=30)
+    out = env.new_outputs()
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    for f in range(60):
+        logits = torch.randn(int(env.layout.plane_cells) * 9, generator=gen, device="cuda") * 2.0
+        acts = check_sample(env, orc, logits, 7, f"frame {f}")
+        a_orc, _ = orc.sample_actions(oracle_logits(env, logits.cpu().numpy()), 7)
+        env.step(acts, out)
+        orc.step(a_orc)
+        compare_frame(env, out, orc, f"frame {f}")
+
+
+@pytest.mark.parametrize("H,W,mode,P", [(1, 2, 0, 2), (40, 1, 2, 3), (64, 64, 2, 8), (3, 3, 2, 8)])
+def test_sampling_edge_shapes(H, W, mode, P):
+    import torch
+    env, orc = pair([H, H], [W, W], [mode, mode], [P, P], seed=5, n_cities=1)
+    acts = env.new_actions()
+    out = env.new_outputs()
+    env.policy(1, acts)
+    for f in range(6):
+        a = orc.policy(1)
+        env.step_policy(acts, out, 1, acts)
+        orc.step(a)
+    logits = torch.randn(int(env.layout.plane_cells) * 9, device="cuda")
+    check_sample(env, orc, logits, 9, f"edge {H}x{W}")
+
+
+def test_expand_mask_only_and_errors():
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsError
+    env, orc = pair([6, 7], [6, 9], [0, 2], [2, 3], seed=1)
+    m9 = env.expand_mask()
+    torch.cuda.synchronize()
+    logits = env.new_logits()
+    m9b = torch.empty_like(m9)
+    env.sample_actions(logits, 1, None, m9b)
+    torch.cuda.synchronize()
+    assert torch.equal(m9, m9b)
+    assert env.lib.gen_sample_actions(env.h, None, 0, None, None, None) != 0  # nothing to compute
+    with pytest.raises(GeneralsError):
+        env.sample_actions(logits[1:], 1)  # misaligned logits
+
+
+def test_sampling_full_size_24x24_65536_sampled():
+    """The 65,536-game workload: every player sampled on the GPU; three blocks of
+    32 games replayed by the oracle."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
+    env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
+    acts = env.new_actions()
+    out = env.new_outputs()
+    env.policy(2, acts)
+    for f in range(5):
+        env.step_policy(acts, out, 2, acts)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    logits = torch.randn(int(env.layout.plane_cells) * 9, generator=g, device="cuda") * 2.0
+    got = env.sample_actions(logits, 77)
+    torch.cuda.synchronize()
+    flat = logits.cpu().numpy()
+    ga = got.cpu().numpy()
+    for start in (0, 30000, 65536 - 32):
+        n = 32
+        orc = OracleEnv(H[start:start + n], W[start:start + n], mode[start:start + n], P[start:start + n], seed=1,
+                        game_id_base=start, **gen)
+        for f in range(5):
+            orc.step(orc.policy(2))
+        want, _ = orc.sample_actions(oracle_logits(env, flat, range(start, start + n)), 77)
+        np.testing.assert_array_equal(ga[2 * start:2 * (start + n)], want[:, :2].reshape(-1))
