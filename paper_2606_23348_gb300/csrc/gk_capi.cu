@@ -922,6 +922,7 @@ int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t
     a.seed = seed;
     a.actions = d_actions;
     a.mask9 = d_mask9;
+    a.npad_max = e->npad_max;
     const int rc = gk::launch_sample(a, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, "sampler launch");
     return GEN_OK;

@@ -127,6 +127,7 @@ struct SArgs {
     uint64_t seed;
     int32_t* actions;       // [player slots] (NULL with logits NULL)
     uint8_t* mask9;         // optional: 9 * Npad legal-entry bytes per player plane at q * 9
+    int32_t npad_max;       // largest board (cells, multiple of 16)
 };
 
 // Launch the sampler over every game on `stream`.  Returns a cudaError_t.

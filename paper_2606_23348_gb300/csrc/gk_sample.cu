@@ -17,10 +17,14 @@
 // single-precision operation with round-to-nearest written out explicitly
 // (no contraction), so the weights are bit-reproducible.
 //
-// One warp per game, players in turn; three passes over the player's logits
-// (maximum with the mask, weight sum, selection by a warp scan per 128
-// entries), the second and third from L2.  HBM-bound: 36 bytes of logits per
-// cell (plus 9 mask bytes when the expanded mask is written).
+// One warp per game, players in turn, 32 cells per round with the round's
+// 288 logits staged in shared memory by 16-byte loads: pass 1 derives each
+// cell's nine legal bits once (and writes the expanded mask) and takes the
+// maximum; pass 2 (from L2) sums each cell's weights, computing every
+// exponential once; pass 3 scans the per-cell sums in shared memory and
+// resolves the entry inside the chosen cell.  Rounds without a legal entry
+// read no logits.  HBM-bound at most 36 bytes of logits per cell (plus 9 mask
+// bytes when the expanded mask is written).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,12 +48,14 @@ __device__ __forceinline__ uint64_t hkey(uint64_t s, uint64_t a, uint64_t b, uin
     return stream_out(stream_out(stream_out(s, a), b), c);
 }
 
-// the reproducible exponential (see the file comment)
-__device__ __forceinline__ float exp_r(float x) {
-    const float t = __fmul_rn(x, 1.4426950408889634f);
-    if (t < -25.0f) return 0.0f;
-    const float n = floorf(t);
-    const float f = __fsub_rn(t, n);
+// weight of a legal entry: floor(E(l - m) * 2^24).  E = P * 2^n exactly
+// (n >= -25, P in [1, 2)), so the floor is P's 24-bit significand shifted
+// right by -(n + 1) bits; equal to the float floor of the exact product.
+__device__ __forceinline__ uint32_t weight_shift(float l, float m) {
+    const float t = __fmul_rn(__fsub_rn(l, m), 1.4426950408889634f);
+    if (t < -25.0f) return 0u;
+    const float nf = floorf(t);
+    const float f = __fsub_rn(t, nf);
     float p = 1.5252733804059838e-05f;
     p = __fmaf_rn(p, f, 0.00015403530393381606f);
     p = __fmaf_rn(p, f, 0.0013333558146428441f);
@@ -58,116 +64,122 @@ __device__ __forceinline__ float exp_r(float x) {
     p = __fmaf_rn(p, f, 0.2402265069591007f);
     p = __fmaf_rn(p, f, 0.6931471805599453f);
     p = __fmaf_rn(p, f, 1.0f);
-    return __fmul_rn(p, __int_as_float((127 + (int)n) << 23));  // exact: n >= -25
-}
-__device__ __forceinline__ uint32_t weight(float l, float m) {
-    return (uint32_t)floorf(__fmul_rn(exp_r(__fsub_rn(l, m)), 16777216.0f));
+    const int n = (int)nf;                                          // -25 .. 0
+    const uint32_t sig = (__float_as_uint(p) & 0x7FFFFFu) | 0x800000u;  // P * 2^23
+    return n >= 0 ? sig << 1 : sig >> (-(n + 1));
 }
 
-struct Player {
-    const int16_t* army;
-    const int8_t* owner;
-    const int8_t* terrain;
-    int N, p;
-    bool moves;  // alive and the game not finished
-};
-
-// legality of the four entries e0 .. e0 + 3 as bits 0..3
-__device__ __forceinline__ uint32_t legal4(const Player& q, int e0) {
-    uint32_t bits = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int e = e0 + i;
-        const int c = e / 9, k = e - 9 * c;
-        if (c >= q.N) continue;
-        const bool own = q.owner[c] == q.p;
-        bool ok;
-        if (k == 0)
-            ok = own;
-        else
-            ok = q.moves && own && q.army[c] >= 2 && ((q.terrain[c] >> (2 + ((k - 1) & 3))) & 1);
-        bits |= (ok ? 1u : 0u) << i;
+// legal entries of one cell for player p as bits 0..8 (entry k of the cell)
+__device__ __forceinline__ uint32_t legal9(int own_p, int army, uint32_t terrain, bool moves) {
+    if (!own_p) return 0u;
+    uint32_t b = 1u;  // pass
+    if (moves && army >= 2) {
+        const uint32_t dirs = (terrain >> 2) & 0xFu;  // neighbour exists and is not a mountain
+        b |= (dirs << 1) | (dirs << 5);
     }
-    return bits;
+    return b;
+}
+
+// shared memory of one warp, sized for boards up to npad_max cells
+__host__ __device__ __forceinline__ int sample_warp_bytes(int npad_max) {
+    return 4 * npad_max + 2 * npad_max + 4 * 288 + 288;  // weights, legal bits, logits and mask staging
+}
+
+// warp copy of `cells` cells x 9 logits (a multiple of 144 floats) to shared memory
+__device__ __forceinline__ void stage_logits(float* dst, const float* src, int cells, int lane) {
+    const int n4 = (9 * cells) >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int v = lane; v < n4; v += 32) d4[v] = __ldcg(s4 + v);
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(256) k_sample(const SArgs a) {
+    extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gidx = blockIdx.x * kWarps + wid;
     if (gidx >= a.n_games) return;
+    char* base_s = smem + (size_t)wid * sample_warp_bytes(a.npad_max);
+    uint32_t* s_w = reinterpret_cast<uint32_t*>(base_s);                              // [npad_max]
+    float* s_stage = reinterpret_cast<float*>(base_s + 4 * a.npad_max);               // [288]
+    uint16_t* s_legal = reinterpret_cast<uint16_t*>(base_s + 4 * a.npad_max + 1152);  // [npad_max]
+    uint8_t* s_mask = reinterpret_cast<uint8_t*>(base_s + 6 * a.npad_max + 1152);     // [288]
+
     const GameInfo gi = a.info[gidx];
     const GameScalars sc = a.scal[gidx];
     const int N = gi.N, Npad = gi.Npad;
-    const int E = 9 * Npad;  // entries of one player plane (a multiple of 4)
+    const int16_t* army = a.army + gi.cell_off;
+    const int8_t* owner = a.owner + gi.cell_off;
+    const int8_t* terrain = a.terrain + gi.cell_off;
     for (int p = 0; p < gi.P; ++p) {
-        Player q;
-        q.army = a.army + gi.cell_off;
-        q.owner = a.owner + gi.cell_off;
-        q.terrain = a.terrain + gi.cell_off;
-        q.N = N;
-        q.p = p;
-        q.moves = ((sc.alive >> p) & 1u) && !sc.finished;
+        const bool moves = ((sc.alive >> p) & 1u) && !sc.finished;
         const int64_t base = (gi.plane_off + (int64_t)p * Npad) * 9;
         const float* lg = a.logits ? a.logits + base : nullptr;
 
-        // pass 1: legal mask (written when asked) and the maximum legal logit
+        // pass 1: legal bits per cell, the expanded mask, the maximum legal logit
         float m = -3.402823466e38f;
-        bool any = false;
-        for (int e0 = 4 * lane; e0 < E; e0 += 128) {
-            const uint32_t bits = legal4(q, e0);
-            if (a.mask9)
-                *reinterpret_cast<uchar4*>(a.mask9 + base + e0) =
-                    make_uchar4(bits & 1u, (bits >> 1) & 1u, (bits >> 2) & 1u, (bits >> 3) & 1u);
-            if (lg && bits) {
-                const float4 v = __ldg(reinterpret_cast<const float4*>(lg + e0));
-                if (bits & 1u) m = fmaxf(m, v.x);
-                if (bits & 2u) m = fmaxf(m, v.y);
-                if (bits & 4u) m = fmaxf(m, v.z);
-                if (bits & 8u) m = fmaxf(m, v.w);
-                any = true;
+        bool any_all = false;
+        for (int r0 = 0; r0 < Npad; r0 += 32) {
+            const int cells = min(32, Npad - r0);
+            const int c = r0 + lane;
+            uint32_t lb = 0u;
+            if (c < N) lb = legal9(owner[c] == p, army[c], (uint32_t)(uint8_t)terrain[c], moves);
+            if (c < Npad) s_legal[c] = (uint16_t)lb;
+            if (a.mask9) {
+                if (lane < cells)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) s_mask[9 * lane + k] = (uint8_t)((lb >> k) & 1u);
+                __syncwarp();
+                const int n16 = (9 * cells) >> 4;
+                if (lane < n16)
+                    reinterpret_cast<uint4*>(a.mask9 + base + 9 * r0)[lane] = reinterpret_cast<const uint4*>(s_mask)[lane];
+                __syncwarp();
             }
+            const bool any = __any_sync(kAll, lb != 0u);
+            if (!lg || !any) continue;
+            any_all = true;
+            stage_logits(s_stage, lg + 9 * r0, cells, lane);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if ((lb >> k) & 1u) m = fmaxf(m, s_stage[9 * lane + k]);
+            __syncwarp();
         }
         if (!lg) continue;
-        any = __any_sync(kAll, any);
         int32_t action = 0;
-        if (any) {
+        if (any_all) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
-            // pass 2: the exact sum of the weights
+            // pass 2: weight of each cell (sum of its legal entries' weights), exact total
             uint64_t S = 0;
-            for (int e0 = 4 * lane; e0 < E; e0 += 128) {
-                const uint32_t bits = legal4(q, e0);
-                if (!bits) continue;
-                const float4 v = *reinterpret_cast<const float4*>(lg + e0);
-                if (bits & 1u) S += weight(v.x, m);
-                if (bits & 2u) S += weight(v.y, m);
-                if (bits & 4u) S += weight(v.z, m);
-                if (bits & 8u) S += weight(v.w, m);
+            for (int r0 = 0; r0 < Npad; r0 += 32) {
+                const int cells = min(32, Npad - r0);
+                const int c = r0 + lane;
+                const uint32_t lb = c < Npad ? s_legal[c] : 0u;
+                uint32_t w = 0u;
+                if (__any_sync(kAll, lb != 0u)) {
+                    stage_logits(s_stage, lg + 9 * r0, cells, lane);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k)
+                        if ((lb >> k) & 1u) w += weight_shift(s_stage[9 * lane + k], m);
+                    __syncwarp();
+                }
+                if (c < Npad) s_w[c] = w;
+                S += w;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(kAll, S, o);
+            __syncwarp();
             const uint64_t d = stream_out(hkey(a.seed, gi.game_id, sc.frame, (uint64_t)p), 7);
             const uint64_t r = __umul64hi(d, S);
-            // pass 3: first entry whose running weight sum exceeds r, 128 entries per round
+            // pass 3: the cell whose running weight sum first exceeds r, then the entry within it
             uint64_t run = 0;
-            for (int r0 = 0; r0 < E; r0 += 128) {
-                const int e0 = r0 + 4 * lane;
-                uint32_t w[4] = {0u, 0u, 0u, 0u};
-                if (e0 < E) {
-                    const uint32_t bits = legal4(q, e0);
-                    if (bits) {
-                        const float4 v = *reinterpret_cast<const float4*>(lg + e0);
-                        if (bits & 1u) w[0] = weight(v.x, m);
-                        if (bits & 2u) w[1] = weight(v.y, m);
-                        if (bits & 4u) w[2] = weight(v.z, m);
-                        if (bits & 8u) w[3] = weight(v.w, m);
-                    }
-                }
-                const uint32_t mine = w[0] + w[1] + w[2] + w[3];  // <= 2^26
-                uint32_t incl = mine;
+            for (int r0 = 0; r0 < Npad; r0 += 32) {
+                const int c = r0 + lane;
+                const uint64_t w = c < Npad ? s_w[c] : 0u;
+                uint64_t incl = w;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kAll, incl, o);
+                    const uint64_t y = __shfl_up_sync(kAll, incl, o);
                     if (lane >= o) incl += y;
                 }
                 const unsigned hit = __ballot_sync(kAll, run + incl > r);
@@ -175,11 +187,13 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a) {
                     const int L = __ffs(hit) - 1;
                     int pick = 0;
                     if (lane == L) {
-                        uint64_t acc = run + (incl - mine);
-                        for (int i = 0; i < 4; ++i) {
-                            acc += w[i];
+                        uint64_t acc = run + (incl - w);
+                        const uint32_t lb = s_legal[c];
+                        for (int k = 0; k < 9; ++k) {
+                            if (!((lb >> k) & 1u)) continue;
+                            acc += weight_shift(__ldcg(lg + 9 * c + k), m);
                             if (acc > r) {
-                                pick = e0 + i;
+                                pick = 9 * c + k;
                                 break;
                             }
                         }
@@ -191,6 +205,7 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a) {
             }
         }
         if (lane == 0 && a.actions) a.actions[gi.player_off + p] = action;
+        __syncwarp();
     }
 }
 
@@ -198,8 +213,15 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a) {
 
 int launch_sample(const SArgs& a, void* stream) {
     if (a.n_games <= 0) return 0;
+    const int smem = kWarps * sample_warp_bytes(a.npad_max);
+    static int configured = 48 * 1024;
+    if (smem > configured) {
+        const cudaError_t e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return (int)e;
+        configured = smem;
+    }
     const int blocks = (a.n_games + kWarps - 1) / kWarps;
-    k_sample<<<blocks, 32 * kWarps, 0, (cudaStream_t)stream>>>(a);
+    k_sample<<<blocks, 32 * kWarps, smem, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 
