@@ -44,7 +44,7 @@ MAP_SEED = 1
 # it was taken on.
 NCU_TRAFFIC = {"kernel_sha1": "70fd9db3fc4e", "bytes_per_launch": 2 * 365316864.0,
                "captured": "32,768 games (x2)", "games": 65536}
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "67b218310e74", "bytes_per_launch": 8 * 1837613224.0,
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "726f62340a7d", "bytes_per_launch": 8 * 1911564864.0,
                        "captured": "8,192 games (x8)", "games": 65536}
 
 
@@ -576,6 +576,16 @@ def run_features(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+SAMPLE_PREROLL = 256  # frames of the benchmark policy before the sampler is timed
+
+
+def owned_player_cells(env) -> float:
+    """Sum over games and players of the cells the player owns."""
+    st = env.read_state()
+    owner = st[1]
+    return float(np.count_nonzero(owner >= 0))
+
+
 def run_sampling(args, rank, world, local):
     """Device self-play shape: per frame, actions sampled from H x W x 9
     logits (k_sample), then the step (k_generals without the fused policy)."""
@@ -593,10 +603,15 @@ def run_sampling(args, rank, world, local):
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     logits = torch.randn(int(env.layout.plane_cells) * 9, generator=g, device="cuda") * 2.0
     stream = torch.cuda.current_stream()
+    # pre-roll to mid-game (the benchmark policy), so players own territory
+    env.policy(POLICY_SEED, acts)
+    for _ in range(SAMPLE_PREROLL):
+        env.step_policy(acts, out, POLICY_SEED, acts)
     for _ in range(max(3, args.warmup)):
         env.sample_actions(logits, POLICY_SEED, acts)
         env.step(acts, out)
     torch.cuda.synchronize()
+    owned0 = owned_player_cells(env)
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -617,8 +632,11 @@ def run_sampling(args, rank, world, local):
     samp_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     step_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     value = sum_over_ranks(float(G * K), world) / (elapsed_ms * 1e-3)
-    # logits 36 B per plane cell, board 4 B per cell (once per game), actions 4 B per player
-    nbytes = 36.0 * 2 * 576 * G + 4.0 * 576 * G + 4.0 * 2 * G
+    # the logits a sampler must read (36 B per cell each player owns: legal entries lie only
+    # there), board 4 B per cell once per game, actions 4 B per player; owned cells averaged
+    # over the start and the end of the timed region
+    owned = 0.5 * (owned0 + owned_player_cells(env))
+    nbytes = 36.0 * owned + 4.0 * 576 * G + 4.0 * 2 * G
     peak, peak_kind = peaks()
     achieved = nbytes / (samp_ms * 1e-3) / 1e9
     if rank == 0:
@@ -628,7 +646,8 @@ def run_sampling(args, rank, world, local):
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 logits, int16 state",
             "data": "synthetic (seeded counter-hash maps, N(0, 2) logits, auto-reset)",
-            "config": {"workload": "sample-65536x24x24", "games_per_gpu": G,
+            "config": {"workload": "sample-65536x24x24", "games_per_gpu": G, "preroll_frames": SAMPLE_PREROLL,
+                       "owned_cells_per_player": owned / (2 * G),
                        "l2": "inputs larger than L2 (logits 2.7 GB)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",

@@ -17,16 +17,21 @@
 // single-precision operation with round-to-nearest written out explicitly
 // (no contraction), so the weights are bit-reproducible.
 //
-// One warp per game, players in turn, 32 cells per round with the round's
-// 288 logits staged in shared memory by 16-byte loads: pass 1 derives each
-// cell's nine legal bits once (and writes the expanded mask) and takes the
-// maximum; pass 2 (from L2) sums each cell's weights, computing every
-// exponential once; pass 3 scans the per-cell sums in shared memory and
-// resolves the entry inside the chosen cell.  Rounds without a legal entry
-// read no logits.  HBM-bound at most 36 bytes of logits per cell (plus 9 mask
-// bytes when the expanded mask is written).
+// One warp per game, players in turn.  The board is staged in shared memory
+// (every 16-byte load in flight at once); legal entries lie only on the
+// player's own cells, so the warp first lists those cells in index order (a
+// ballot per 32 cells, no global load) and the passes run over the list, 32
+// own cells at a time: pass 1 derives each cell's nine legal bits and takes
+// the maximum; pass 2 (logits again, from L1/L2) sums each cell's weights,
+// computing every exponential once, and keeps the sums per cell and per 32
+// cells; pass 3 finds the group, the cell and the entry where the running sum
+// first exceeds r.  Only the own cells' logits are read (36 bytes each).  The
+// expanded mask, when asked for, is a dense pass over every cell (a cell's
+// entries belong to its owner) written through shared memory with 16-byte
+// stores.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "gk_internal.h"
@@ -80,129 +85,186 @@ __device__ __forceinline__ uint32_t legal9(int own_p, int army, uint32_t terrain
     return b;
 }
 
-// shared memory of one warp, sized for boards up to npad_max cells
+// shared memory of one warp, sized for boards up to npad_max cells: the
+// board (4 B per cell), the player's own cells in index order (2 B), their
+// legal bits (2 B) and weight sums (4 B), the weight sum of every 32 of
+// them (8 B), mask staging (288 B); a multiple of 16 bytes
 __host__ __device__ __forceinline__ int sample_warp_bytes(int npad_max) {
-    return 4 * npad_max + 2 * npad_max + 4 * 288 + 288;  // weights, legal bits, logits and mask staging
+    const int rounds = (npad_max + 31) >> 5;
+    return 12 * npad_max + 8 * ((rounds + 1) & ~1) + 288;
 }
 
-// warp copy of `cells` cells x 9 logits (a multiple of 144 floats) to shared memory
-__device__ __forceinline__ void stage_logits(float* dst, const float* src, int cells, int lane) {
-    const int n4 = (9 * cells) >> 2;
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int v = lane; v < n4; v += 32) d4[v] = __ldcg(s4 + v);
-    __syncwarp();
+// the nine logits of one cell, every load issued before any is used
+__device__ __forceinline__ void load9(float (&v)[9], const float* x) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = __ldcg(x + k);
 }
 
-__global__ void __launch_bounds__(256) k_sample(const SArgs a) {
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kAll, x, o);
+    return x;
+}
+__device__ __forceinline__ uint64_t warp_incl64(uint64_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(kAll, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int gidx = blockIdx.x * kWarps + wid;
+    const int gidx = blockIdx.x * warps_per_cta + wid;
     if (gidx >= a.n_games) return;
-    char* base_s = smem + (size_t)wid * sample_warp_bytes(a.npad_max);
-    uint32_t* s_w = reinterpret_cast<uint32_t*>(base_s);                              // [npad_max]
-    float* s_stage = reinterpret_cast<float*>(base_s + 4 * a.npad_max);               // [288]
-    uint16_t* s_legal = reinterpret_cast<uint16_t*>(base_s + 4 * a.npad_max + 1152);  // [npad_max]
-    uint8_t* s_mask = reinterpret_cast<uint8_t*>(base_s + 6 * a.npad_max + 1152);     // [288]
+    const int np = a.npad_max;
+    const int rounds_max = (np + 31) >> 5;
+    char* b = smem + (size_t)wid * sample_warp_bytes(np);
+    int16_t* s_army = reinterpret_cast<int16_t*>(b);
+    int8_t* s_owner = reinterpret_cast<int8_t*>(b + 2 * np);
+    uint8_t* s_terrain = reinterpret_cast<uint8_t*>(b + 3 * np);
+    uint32_t* s_w = reinterpret_cast<uint32_t*>(b + 4 * np);          // [np] per own cell
+    uint16_t* s_list = reinterpret_cast<uint16_t*>(b + 8 * np);       // [np] own cells
+    uint16_t* s_legal = reinterpret_cast<uint16_t*>(b + 10 * np);     // [np] per own cell
+    uint64_t* s_round = reinterpret_cast<uint64_t*>(b + 12 * np);     // [rounds]
+    uint8_t* s_mask = reinterpret_cast<uint8_t*>(s_round + ((rounds_max + 1) & ~1));  // [288]
 
     const GameInfo gi = a.info[gidx];
     const GameScalars sc = a.scal[gidx];
-    const int N = gi.N, Npad = gi.Npad;
-    const int16_t* army = a.army + gi.cell_off;
-    const int8_t* owner = a.owner + gi.cell_off;
-    const int8_t* terrain = a.terrain + gi.cell_off;
-    for (int p = 0; p < gi.P; ++p) {
-        const bool moves = ((sc.alive >> p) & 1u) && !sc.finished;
-        const int64_t base = (gi.plane_off + (int64_t)p * Npad) * 9;
-        const float* lg = a.logits ? a.logits + base : nullptr;
+    const int N = gi.N, Npad = gi.Npad, P = gi.P;
+    {  // board to shared memory, every 16-byte load in flight at once
+        const uint4* ga = reinterpret_cast<const uint4*>(a.army + gi.cell_off);
+        const uint4* go = reinterpret_cast<const uint4*>(a.owner + gi.cell_off);
+        const uint4* gt = reinterpret_cast<const uint4*>(a.terrain + gi.cell_off);
+        const int n16 = Npad >> 4;
+        for (int v = lane; v < 2 * n16; v += 32) reinterpret_cast<uint4*>(s_army)[v] = __ldcg(ga + v);
+        for (int v = lane; v < n16; v += 32) {
+            reinterpret_cast<uint4*>(s_owner)[v] = __ldcg(go + v);
+            reinterpret_cast<uint4*>(s_terrain)[v] = __ldcg(gt + v);
+        }
+        __syncwarp();
+    }
 
-        // pass 1: legal bits per cell, the expanded mask, the maximum legal logit
-        float m = -3.402823466e38f;
-        bool any_all = false;
+    // expanded mask: a cell's legal entries belong to its owner only
+    if (a.mask9) {
         for (int r0 = 0; r0 < Npad; r0 += 32) {
-            const int cells = min(32, Npad - r0);
-            const int c = r0 + lane;
+            const int cells = min(32, Npad - r0), c = r0 + lane;
+            int o = -1;
             uint32_t lb = 0u;
-            if (c < N) lb = legal9(owner[c] == p, army[c], (uint32_t)(uint8_t)terrain[c], moves);
-            if (c < Npad) s_legal[c] = (uint16_t)lb;
-            if (a.mask9) {
+            if (c < N) {
+                o = s_owner[c];
+                if (o >= 0) {
+                    const bool moves = ((sc.alive >> o) & 1u) && !sc.finished;
+                    lb = legal9(true, s_army[c], s_terrain[c], moves);
+                }
+            }
+            const int n16 = (9 * cells) >> 4;
+            for (int p = 0; p < P; ++p) {
+                const uint32_t bits = o == p ? lb : 0u;
                 if (lane < cells)
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) s_mask[9 * lane + k] = (uint8_t)((lb >> k) & 1u);
+                    for (int k = 0; k < 9; ++k) s_mask[9 * lane + k] = (uint8_t)((bits >> k) & 1u);
                 __syncwarp();
-                const int n16 = (9 * cells) >> 4;
+                const int64_t base = (gi.plane_off + (int64_t)p * Npad) * 9;
                 if (lane < n16)
                     reinterpret_cast<uint4*>(a.mask9 + base + 9 * r0)[lane] = reinterpret_cast<const uint4*>(s_mask)[lane];
                 __syncwarp();
             }
-            const bool any = __any_sync(kAll, lb != 0u);
-            if (!lg || !any) continue;
-            any_all = true;
-            stage_logits(s_stage, lg + 9 * r0, cells, lane);
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                if ((lb >> k) & 1u) m = fmaxf(m, s_stage[9 * lane + k]);
-            __syncwarp();
         }
-        if (!lg) continue;
+    }
+    if (!a.logits) return;
+
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int p = 0; p < P; ++p) {
+        const bool moves = ((sc.alive >> p) & 1u) && !sc.finished;
+        const float* lg = a.logits + (gi.plane_off + (int64_t)p * Npad) * 9;
+        // the player's cells in index order (legal entries lie only there)
+        int n = 0;
+        for (int r0 = 0; r0 < N; r0 += 32) {
+            const int c = r0 + lane;
+            const bool mine = c < N && s_owner[c] == p;
+            const unsigned bal = __ballot_sync(kAll, mine);
+            if (mine) s_list[n + __popc(bal & lt_mask)] = (uint16_t)c;
+            n += __popc(bal);
+        }
+        __syncwarp();
         int32_t action = 0;
-        if (any_all) {
+        if (n > 0) {
+            // pass 1: legal bits and the maximum legal logit
+            float m = -3.402823466e38f;
+            for (int i = lane; i < n; i += 32) {
+                const int c = s_list[i];
+                const uint32_t lb = legal9(true, s_army[c], s_terrain[c], moves);
+                s_legal[i] = (uint16_t)lb;
+                float v[9];
+                load9(v, lg + 9 * c);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
-            // pass 2: weight of each cell (sum of its legal entries' weights), exact total
-            uint64_t S = 0;
-            for (int r0 = 0; r0 < Npad; r0 += 32) {
-                const int cells = min(32, Npad - r0);
-                const int c = r0 + lane;
-                const uint32_t lb = c < Npad ? s_legal[c] : 0u;
-                uint32_t w = 0u;
-                if (__any_sync(kAll, lb != 0u)) {
-                    stage_logits(s_stage, lg + 9 * r0, cells, lane);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        if ((lb >> k) & 1u) w += weight_shift(s_stage[9 * lane + k], m);
-                    __syncwarp();
-                }
-                if (c < Npad) s_w[c] = w;
-                S += w;
+                for (int k = 0; k < 9; ++k)
+                    if ((lb >> k) & 1u) m = fmaxf(m, v[k]);
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(kAll, S, o);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
+            __syncwarp();
+            // pass 2: weight sums per own cell and per 32 of them (every exponential once)
+            uint64_t S = 0;
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                uint32_t w = 0u;
+                if (i < n) {
+                    const int c = s_list[i];
+                    const uint32_t lb = s_legal[i];
+                    float v[9];
+                    load9(v, lg + 9 * c);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k)
+                        if ((lb >> k) & 1u) w += weight_shift(v[k], m);
+                    s_w[i] = w;
+                }
+                const uint64_t rs = warp_sum64(w);
+                if (lane == 0) s_round[i0 >> 5] = rs;
+                S += rs;
+            }
             __syncwarp();
             const uint64_t d = stream_out(hkey(a.seed, gi.game_id, sc.frame, (uint64_t)p), 7);
             const uint64_t r = __umul64hi(d, S);
-            // pass 3: the cell whose running weight sum first exceeds r, then the entry within it
+            // pass 3: the group of 32, then the cell, then the entry where the running sum first exceeds r
+            const int groups = (n + 31) >> 5;
             uint64_t run = 0;
-            for (int r0 = 0; r0 < Npad; r0 += 32) {
-                const int c = r0 + lane;
-                const uint64_t w = c < Npad ? s_w[c] : 0u;
-                uint64_t incl = w;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint64_t y = __shfl_up_sync(kAll, incl, o);
-                    if (lane >= o) incl += y;
-                }
+            int jr = -1;
+            for (int j0 = 0; j0 < groups && jr < 0; j0 += 32) {
+                const uint64_t rs = j0 + lane < groups ? s_round[j0 + lane] : 0u;
+                const uint64_t incl = warp_incl64(rs, lane);
                 const unsigned hit = __ballot_sync(kAll, run + incl > r);
                 if (hit) {
                     const int L = __ffs(hit) - 1;
-                    int pick = 0;
-                    if (lane == L) {
-                        uint64_t acc = run + (incl - w);
-                        const uint32_t lb = s_legal[c];
-                        for (int k = 0; k < 9; ++k) {
-                            if (!((lb >> k) & 1u)) continue;
-                            acc += weight_shift(__ldcg(lg + 9 * c + k), m);
-                            if (acc > r) {
-                                pick = 9 * c + k;
-                                break;
-                            }
-                        }
-                    }
-                    action = __shfl_sync(kAll, pick, L);
-                    break;
+                    jr = j0 + L;
+                    run += __shfl_sync(kAll, incl - rs, L);
+                } else {
+                    run += __shfl_sync(kAll, incl, 31);
                 }
-                run += __shfl_sync(kAll, incl, 31);
             }
+            const int i = 32 * jr + lane;
+            const uint64_t w = i < n ? s_w[i] : 0u;
+            const uint64_t incl = warp_incl64(w, lane);
+            const unsigned hit = __ballot_sync(kAll, run + incl > r);
+            const int L = __ffs(hit) - 1;
+            int pick = 0;
+            if (lane == L) {
+                uint64_t acc = run + (incl - w);
+                const int c = s_list[i];
+                const uint32_t lb = s_legal[i];
+                for (int k = 0; k < 9; ++k) {
+                    if (!((lb >> k) & 1u)) continue;
+                    acc += weight_shift(__ldcg(lg + 9 * c + k), m);
+                    if (acc > r) {
+                        pick = 9 * c + k;
+                        break;
+                    }
+                }
+            }
+            action = __shfl_sync(kAll, pick, L);
         }
         if (lane == 0 && a.actions) a.actions[gi.player_off + p] = action;
         __syncwarp();
@@ -213,15 +275,17 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a) {
 
 int launch_sample(const SArgs& a, void* stream) {
     if (a.n_games <= 0) return 0;
-    const int smem = kWarps * sample_warp_bytes(a.npad_max);
+    const int per_warp = sample_warp_bytes(a.npad_max);
+    const int wpc = std::max(1, std::min(kWarps, (200 * 1024) / per_warp));
+    const int smem = wpc * per_warp;
     static int configured = 48 * 1024;
     if (smem > configured) {
         const cudaError_t e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return (int)e;
         configured = smem;
     }
-    const int blocks = (a.n_games + kWarps - 1) / kWarps;
-    k_sample<<<blocks, 32 * kWarps, smem, (cudaStream_t)stream>>>(a);
+    const int blocks = (a.n_games + wpc - 1) / wpc;
+    k_sample<<<blocks, 32 * wpc, smem, (cudaStream_t)stream>>>(a, wpc);
     return (int)cudaGetLastError();
 }
 

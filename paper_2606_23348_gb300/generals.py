@@ -382,7 +382,7 @@ class Features:
             assert series.numel() >= self.n_series and series.dtype.itemsize == 4 and series.is_cuda
             sp = C.c_void_p(series.data_ptr())
         _check(self.lib.gen_features_build_ex(self.h, C.c_void_p(out.data_ptr()), sp, _cur_stream()),
-               "gen_features_build_ex", "gen_sample_actions")
+               "gen_features_build_ex")
         return out
 
     def player_series(self, series, g: int, p: int):
