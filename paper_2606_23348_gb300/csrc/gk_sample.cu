@@ -24,8 +24,9 @@
 // own cells at a time: pass 1 derives each cell's nine legal bits and takes
 // the maximum; pass 2 (logits again, from L1/L2) sums each cell's weights,
 // computing every exponential once, and keeps the sums per cell and per 32
-// cells; pass 3 finds the group, the cell and the entry where the running sum
-// first exceeds r.  Only the own cells' logits are read (36 bytes each).  The
+// cells; pass 3 finds the group, the cell and (nine lanes weighing the cell's
+// entries at once) the entry where the running sum first exceeds r.  Only the
+// own cells' logits are read (36 bytes each).  The
 // expanded mask, when asked for, is a dense pass over every cell (a cell's
 // entries belong to its owner) written through shared memory with 16-byte
 // stores.
@@ -250,21 +251,15 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta
             const uint64_t incl = warp_incl64(w, lane);
             const unsigned hit = __ballot_sync(kAll, run + incl > r);
             const int L = __ffs(hit) - 1;
-            int pick = 0;
-            if (lane == L) {
-                uint64_t acc = run + (incl - w);
-                const int c = s_list[i];
-                const uint32_t lb = s_legal[i];
-                for (int k = 0; k < 9; ++k) {
-                    if (!((lb >> k) & 1u)) continue;
-                    acc += weight_shift(__ldcg(lg + 9 * c + k), m);
-                    if (acc > r) {
-                        pick = 9 * c + k;
-                        break;
-                    }
-                }
-            }
-            action = __shfl_sync(kAll, pick, L);
+            // the entry inside the chosen cell: lanes 0..8 take one entry each
+            const uint64_t before = run + __shfl_sync(kAll, incl - w, L);
+            const int cL = s_list[32 * jr + L];
+            const uint32_t lbL = s_legal[32 * jr + L];
+            uint64_t we = 0;
+            if (lane < 9 && ((lbL >> lane) & 1u)) we = weight_shift(__ldcg(lg + 9 * cL + lane), m);
+            const uint64_t ein = warp_incl64(we, lane);
+            const unsigned ehit = __ballot_sync(kAll, lane < 9 && before + ein > r);
+            action = 9 * cL + (__ffs(ehit) - 1);
         }
         if (lane == 0 && a.actions) a.actions[gi.player_off + p] = action;
         __syncwarp();
