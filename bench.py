@@ -43,9 +43,28 @@ MAP_SEED = 1
 # processes (traffic grows in proportion); valid only for the kernel source
 # it was taken on.
 NCU_TRAFFIC = {"kernel_sha1": "70fd9db3fc4e", "bytes_per_launch": 2 * 365316864.0,
-               "captured": "32,768 games (x2)", "games": 65536}
+               "warp_inst_per_launch": 2 * 91789969.0, "captured": "32,768 games (x2)", "games": 65536}
+SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
 FEATURE_NCU_TRAFFIC = {"kernel_sha1": "726f62340a7d", "bytes_per_launch": 8 * 1911564864.0,
                        "captured": "8,192 games (x8)", "games": 65536}
+
+
+def issue_roofline(launch_ms: float, G: int, clk) -> dict | None:
+    """The step kernel is issue-bound: warp instructions per launch (ncu
+    smsp__inst_executed.sum on the captured case, scaled by games) over the
+    launch time, against SMs x schedulers x the SM clock sampled during the
+    timed region."""
+    if NCU_TRAFFIC["kernel_sha1"] != kernel_sha1() or G != NCU_TRAFFIC["games"]:
+        return None
+    mhz = (clk.summary() or {}).get("sm_mhz")
+    if not mhz:
+        return None
+    inst = NCU_TRAFFIC["warp_inst_per_launch"]
+    achieved = inst / (launch_ms * 1e-3)
+    peak = SM_COUNT * SCHEDULERS_PER_SM * mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_inst_per_launch": inst, "warp_inst_per_frame": inst / G,
+            "source": f"ncu smsp__inst_executed.sum, {NCU_TRAFFIC['captured']}; peak at the sampled {mhz} MHz"}
 
 
 def kernel_sha1(name: str = "gk_kernels.cu") -> str:
@@ -354,6 +373,7 @@ def run_ours(args, rank, world, local):
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "own_copy_kernel_gbps": own_peak, "algorithmic_bytes_per_launch": nbytes,
                          "launch_ms": launch_ms, "kernel": "k_generals (fused step + policy)"},
+            "issue_roofline": issue_roofline(launch_ms, G, clk),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "resident_rollout_form": resident,
