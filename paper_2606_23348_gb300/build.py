@@ -1,6 +1,7 @@
 """Build libgenerals.so in-tree for sm_103a with nvcc (no cmake).
 
-The two translation units compile in parallel, then link into
+The translation units (step kernels, C-ABI, server, feature builder,
+sampler) compile in parallel, then link into
 ``paper_2606_23348_gb300/_build/libgenerals.so``.
 """
 from __future__ import annotations
