@@ -267,3 +267,33 @@ def test_spawn_range_curriculum_update():
     orc = OracleEnv(H, W, mode, P, max_general_dist=9, min_general_dist=2, **kw)
     orc.reset()
     compare_frame(env, out, orc, "after widening", check_reward=False)
+
+
+def test_full_size_every_game_matches_oracle():
+    """All 65,536 games of the 24x24 workload after 12 frames of the fused step +
+    policy, every board byte and the scalars, against the oracle run by a spawn
+    pool over disjoint game-id ranges on the host cores."""
+    import torch
+    from oracle.pool import replay_workload
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    name = "1v1-65536x24x24"
+    H, W, mode, P, gen, _ = workload(name)
+    env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
+    out = env.new_outputs()
+    acts = env.new_actions()
+    env.policy(2, acts)
+    frames = 12
+    for f in range(frames):
+        env.step_policy(acts, out, 2, acts)
+    torch.cuda.synchronize()
+    st = env.read_state()
+    boards, scal = replay_workload(name, env.G, 1, 2, frames)
+    bad = []
+    for g in range(env.G):
+        got = env.board(st, g)
+        if not all(np.array_equal(x, y) for x, y in zip(got, boards[g])):
+            bad.append(g)
+        s = st[3][g]
+        if (int(s[0]), int(s[1]), int(s[2]), int(s[3])) != tuple(int(x) for x in scal[g]):
+            bad.append(g)
+    assert not bad, f"{len(bad)} games differ, first {bad[:5]}"
