@@ -297,3 +297,47 @@ def test_full_size_every_game_matches_oracle():
         if (int(s[0]), int(s[1]), int(s[2]), int(s[3])) != tuple(int(x) for x in scal[g]):
             bad.append(g)
     assert not bad, f"{len(bad)} games differ, first {bad[:5]}"
+
+
+EXHAUSTIVE_POSITIONS = [
+    (3, ("6@0G 3@0 0", "M 4@1 2@1", "0 0 5@1G")),
+    (3, ("5@0G 45C 0", "3@0 M 9@1", "2@1 0 4@1G")),
+    (3, ("2@0G 7@1 3@1G", "2@0 1@1 0", "0 0 M")),
+    (4, ("5@0G 3@0 0 M", "2@0 4@1 0 0", "0 M 6@1 2@1", "0 0 3@1 7@1G")),
+    (4, ("3@0G 45C 2@0 0", "M 9@1 0 1@0", "4@1 0 M 0", "2@1 0 0 5@1G")),
+]
+
+
+@pytest.mark.parametrize("side,rows", EXHAUSTIVE_POSITIONS, ids=[f"{s}x{s}-{i}" for i, (s, _) in enumerate(
+    EXHAUSTIVE_POSITIONS)])
+def test_exhaustive_joint_actions_on_gpu(side, rows):
+    """Every joint action of both players on a hand-built position, one game
+    per joint action in a single launch (81^2 games on 3x3, 144^2 on 4x4),
+    at an even and an odd turn, with auto-reset on: every state and output
+    byte against the oracle."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    N = side * side
+    army, owner, terrain = golden_io.parse_board(list(rows), side, side)
+    A = np.arange(9 * N, dtype=np.int32)
+    a0, a1 = np.meshgrid(A, A, indexing="ij")
+    acts = np.stack([a0.reshape(-1), a1.reshape(-1)], axis=1)
+    G = acts.shape[0]
+    for turn in (0, 1):
+        kw = dict(seed=9, n_cities=1, min_general_dist=1)
+        env = GeneralsEnv(np.full(G, side), np.full(G, side), np.zeros(G), np.full(G, 2), **kw)
+        orc = OracleEnv(np.full(G, side), np.full(G, side), np.zeros(G), np.full(G, 2), **kw)
+        npad = int(env.npad[0])
+        pad = lambda x, v: np.concatenate([x, np.full(npad - N, v, x.dtype)])
+        scal = np.zeros((G, 8), np.uint32)
+        scal[:, 0] = turn
+        scal[:, 3] = 3
+        env.write_state(np.tile(pad(army, 0), G), np.tile(pad(owner, -1), G), np.tile(pad(terrain, 0), G), scal)
+        for g in range(G):
+            orc.set_game(g, army, owner, terrain, turn=turn)
+        out = env.new_outputs()
+        env.step(torch.from_numpy(acts.reshape(-1).copy()).cuda(), out)
+        rows8 = np.zeros((G, 8), np.int32)
+        rows8[:, :2] = acts
+        orc.step(rows8)
+        compare_frame(env, out, orc, f"{side}x{side} turn {turn}")
