@@ -123,6 +123,18 @@ __device__ __forceinline__ Game load_game(const GameInfo* gi) {
     return g;
 }
 
+__device__ __forceinline__ Game game_of(const KArgs& a, int gidx) {
+    if (!a.uniform) return load_game(a.info + gidx);
+    Game g = load_game(&a.ushape);
+    g.cell_off = gidx * g.Npad;
+    g.player_off = gidx * g.P;
+    g.plane_off = (int64_t)gidx * g.P * g.Npad;
+    return g;
+}
+__device__ __forceinline__ uint64_t game_id_of(const KArgs& a, int gidx) {
+    return a.uniform ? a.game_id_base + (uint64_t)gidx : a.info[gidx].game_id;
+}
+
 __device__ __forceinline__ uint32_t valid_bits(int N, int w) {
     int rem = N - 32 * w;
     if (rem >= 32) return kFull;
@@ -132,7 +144,7 @@ __device__ __forceinline__ uint32_t valid_bits(int N, int w) {
 
 // passable-neighbour bits of every cell (bits 2..5 of the terrain byte),
 // from a mountain bitset so that no lane reads a byte another lane writes
-__device__ __noinline__ void derive_passable(const Game& g, const Smem& s, int lane) {
+__device__ __forceinline__ void derive_passable(const Game& g, const Smem& s, int lane) {
     const int N = g.N, W = g.W, H = g.H;
     for (int w = 0; w < g.nw; ++w) {
         const int c = 32 * w + lane;
@@ -411,8 +423,8 @@ __device__ __noinline__ void castle_guarantee(const KArgs& a, const Game& g, con
 // castle_radius).  It is a separate function of a separate kernel
 // instantiation so that the options' register pressure never reaches the
 // step kernel that runs without them.
-__device__ __noinline__ void generate_spawn(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
-                                           uint32_t epoch, int lane) {
+__device__ __forceinline__ void generate_spawn_body(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
+                                                   uint32_t epoch, int lane) {
     const int N = g.N, W = g.W, P = g.P;
     const uint64_t kmtn = hkey(a.seed, gid, epoch, 1);
     for (int c = lane; c < g.Npad; c += 32) {
@@ -541,8 +553,8 @@ __device__ __noinline__ void generate_spawn(const KArgs& a, const Game& g, const
 }
 
 // ---- map generator (Sec. IV-A) ----------------------------------------------
-__device__ __noinline__ void generate(const KArgs& a, const Game& g, const Smem& s, uint64_t gid, uint32_t epoch,
-                                     int lane) {
+__device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
+                                             uint32_t epoch, int lane) {
     const int N = g.N, W = g.W, P = g.P;
     const uint64_t kmtn = hkey(a.seed, gid, epoch, 1);
     for (int c = lane; c < g.Npad; c += 32) {
@@ -656,6 +668,21 @@ __device__ __noinline__ void generate(const KArgs& a, const Game& g, const Smem&
         }
     }
     derive_passable(g, s, lane);
+}
+
+// Out-of-line entry points of the cold paths take plain arguments and rebuild
+// the game and shared-memory views themselves, so that the step kernel never
+// materialises those structures in local memory for a call it rarely makes.
+__device__ __noinline__ void generate(const KArgs& a, int gidx, char* warp_base, uint64_t gid, uint32_t epoch,
+                                     int lane) {
+    generate_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, lane);
+}
+__device__ __noinline__ void generate_spawn(const KArgs& a, int gidx, char* warp_base, uint64_t gid,
+                                           uint32_t epoch, int lane) {
+    generate_spawn_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, lane);
+}
+__device__ __noinline__ void derive_passable_at(const KArgs& a, int gidx, char* warp_base, int lane) {
+    derive_passable(game_of(a, gidx), carve(warp_base, a), lane);
 }
 
 // ---- one move on lane 0 (Sec. IV-D, IV-E) ----------------------------------
@@ -1075,20 +1102,10 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
 
 namespace {
 
-__device__ __forceinline__ Game game_of(const KArgs& a, int gidx) {
-    if (!a.uniform) return load_game(a.info + gidx);
-    Game g = load_game(&a.ushape);
-    g.cell_off = gidx * g.Npad;
-    g.player_off = gidx * g.P;
-    g.plane_off = (int64_t)gidx * g.P * g.Npad;
-    return g;
-}
-__device__ __forceinline__ uint64_t game_id_of(const KArgs& a, int gidx) {
-    return a.uniform ? a.game_id_base + (uint64_t)gidx : a.info[gidx].game_id;
-}
 
 template <bool MULTI, bool SPAWN>
-__device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const int gidx, const int lane) {
+__device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const int gidx,
+                                         const int lane) {
     const Game g = game_of(a, gidx);
     GameScalars* sc = a.scal + gidx;
 
@@ -1121,15 +1138,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
         if constexpr (SPAWN)
-            generate_spawn(a, g, s, game_id_of(a, gidx), epoch, lane);
+            generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
         else
-            generate(a, g, s, game_id_of(a, gidx), epoch, lane);
+            generate(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
     } else if (a.op == OP_DERIVE) {
-        derive_passable(g, s, lane);
+        derive_passable_at(a, gidx, warp_base, lane);
         wrote_state = true;
     }
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
@@ -1188,9 +1205,9 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, const in
                 if (a.auto_reset) {
                     epoch += 1;
                     if constexpr (SPAWN)
-                        generate_spawn(a, g, s, game_id_of(a, gidx), epoch, lane);
+                        generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
                     else
-                        generate(a, g, s, game_id_of(a, gidx), epoch, lane);
+                        generate(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, lane);
@@ -1250,20 +1267,21 @@ __global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
-    const Smem s = carve(smem_raw + wid * a.warp_smem, a);
+    char* warp_base = smem_raw + wid * a.warp_smem;
+    const Smem s = carve(warp_base, a);
     if (!MULTI) {  // the grid covers every item
         const int item = blockIdx.x * wpc + wid;
         if (item >= a.n_items) return;
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) return;
-        run_game<MULTI, SPAWN>(a, s, gidx, lane);
+        run_game<MULTI, SPAWN>(a, s, warp_base, gidx, lane);
         return;
     }
     for (int item = blockIdx.x * wpc + wid; item < a.n_items; item += gridDim.x * wpc) {
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) continue;
         __syncwarp();
-        run_game<MULTI, SPAWN>(a, s, gidx, lane);
+        run_game<MULTI, SPAWN>(a, s, warp_base, gidx, lane);
     }
 }
 
