@@ -378,12 +378,10 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
 int launch_features(const FArgs& f, void* stream) {
     if (f.n_games <= 0) return 0;
     const int smem = kWarps * warp_bytes(f.npad_max);
-    static int configured = 48 * 1024;
-    if (smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return (int)e;
-        configured = smem;
-    }
+    static SmemLimit limit;
+    const void* fn = (const void*)k_features;
+    const int e = limit.raise(&fn, 1, smem);
+    if (e != 0) return e;
     const int blocks = (f.n_games + kWarps - 1) / kWarps;
     k_features<<<blocks, 32 * kWarps, smem, (cudaStream_t)stream>>>(f);
     return (int)cudaGetLastError();

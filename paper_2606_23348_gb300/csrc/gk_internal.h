@@ -1,8 +1,11 @@
 // Internal structures shared by the kernels and the C-ABI layer of
 // libgenerals.  Not part of the public interface (include/generals.h).
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 namespace gk {
 
@@ -88,6 +91,28 @@ struct KArgs {
     int32_t spawn_dmax;     // cap on a general's distance to every earlier one (0: none)
     int32_t spawn_bfs;      // 1: spacing in BFS steps around mountains
     int32_t castle_radius;  // > 0: a neutral castle within this many steps of every general
+};
+
+// Dynamic shared memory above 48 KiB needs a per-kernel opt-in on each
+// device.  raise() lifts the limit of n kernels to `want` bytes on the current
+// device the first time a launch needs it; limits only grow, so launches
+// sized earlier stay legal.  Thread-safe.  Returns a cudaError_t.
+struct SmemLimit {
+    std::mutex mu;
+    int bytes[64] = {};
+    int raise(const void* const* fns, int n, int want) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return (int)e;
+        if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        if (want <= 48 * 1024 || want <= bytes[dev]) return 0;
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e != cudaSuccess) return (int)e;
+        bytes[dev] = want;
+        return 0;
+    }
 };
 
 // Feature-tensor builder (App. A): one warp per game, players in turn.

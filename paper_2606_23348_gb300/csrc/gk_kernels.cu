@@ -1314,16 +1314,11 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
 }
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
-    static int configured = 48 * 1024;  // only ever raised, so every env's launches stay legal
-    cudaError_t e = cudaSuccess;
-    if (smem_bytes > configured) {
-        const void* fns[4] = {(const void*)k_generals<false, false>, (const void*)k_generals<true, false>,
-                              (const void*)k_generals<false, true>, (const void*)k_generals<true, true>};
-        for (const void* f : fns)
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e != cudaSuccess) return (int)e;
-        configured = smem_bytes;
-    }
+    static SmemLimit limit;  // per device, only ever raised
+    const void* fns[4] = {(const void*)k_generals<false, false>, (const void*)k_generals<true, false>,
+                          (const void*)k_generals<false, true>, (const void*)k_generals<true, true>};
+    cudaError_t e = (cudaError_t)limit.raise(fns, 4, smem_bytes);
+    if (e != cudaSuccess) return (int)e;
     int per_sm = 0, dev = 0, sms = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false>, 32 * warps_per_cta,
                                                            smem_bytes)) != cudaSuccess)

@@ -273,12 +273,10 @@ int launch_sample(const SArgs& a, void* stream) {
     const int per_warp = sample_warp_bytes(a.npad_max);
     const int wpc = std::max(1, std::min(kWarps, (200 * 1024) / per_warp));
     const int smem = wpc * per_warp;
-    static int configured = 48 * 1024;
-    if (smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return (int)e;
-        configured = smem;
-    }
+    static SmemLimit limit;
+    const void* fn = (const void*)k_sample;
+    const int e = limit.raise(&fn, 1, smem);
+    if (e != 0) return e;
     const int blocks = (a.n_games + wpc - 1) / wpc;
     k_sample<<<blocks, 32 * wpc, smem, (cudaStream_t)stream>>>(a, wpc);
     return (int)cudaGetLastError();
