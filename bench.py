@@ -45,7 +45,7 @@ MAP_SEED = 1
 NCU_TRAFFIC = {"kernel_sha1": "e18bf723f508", "bytes_per_launch": 2 * 330900224.0,
                "warp_inst_per_launch": 2 * 90097229.0, "captured": "32,768 games (x2)", "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "726f62340a7d", "bytes_per_launch": 8 * 1911564864.0,
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "6473b2b9435c", "bytes_per_launch": 8 * 1911564864.0,
                        "captured": "8,192 games (x8)", "games": 65536}
 
 
