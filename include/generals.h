@@ -173,7 +173,11 @@ int gen_policy(gen_env *env, uint64_t policy_seed, int32_t *d_actions, void *str
  * steps, copies every non-NULL output of `h_out` back into host memory (same
  * sizes as the device outputs) and synchronises the stream.  When
  * h_next_actions is non-NULL the benchmark policy of gen_step_policy runs in
- * the same launch and its actions are copied back too. */
+ * the same launch and its actions are copied back too.  Host buffers should
+ * be pinned (page-locked) for the copies to overlap.  A batch of 8,192 games
+ * or more launched as one size bucket runs as four chunks of games whose
+ * outputs are copied out on an internal stream while the later chunks step;
+ * the results are the same bytes as gen_step_policy's. */
 int gen_step_host(gen_env *env, const int32_t *h_actions, const gen_outputs *h_out, uint64_t policy_seed,
                   int32_t *h_next_actions, void *stream);
 

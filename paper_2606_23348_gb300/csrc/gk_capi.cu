@@ -92,6 +92,11 @@ struct gen_env {
     int32_t* d_actions = nullptr;
     gen_outputs d_out{};
     bool have_out = false;
+    // gen_step_host pipeline: game ids 0..G-1, a copy stream, one event per chunk
+    int32_t* d_iota = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t chunk_ev[8] = {};
+    cudaEvent_t copy_done = nullptr;
     // cached rollout graph
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
@@ -112,6 +117,11 @@ void free_env(gen_env* e) {
     cudaFree(e->d_owner);
     cudaFree(e->d_terrain);
     cudaFree(e->d_actions);
+    cudaFree(e->d_iota);
+    if (e->copy) cudaStreamDestroy(e->copy);
+    for (auto v : e->chunk_ev)
+        if (v) cudaEventDestroy(v);
+    if (e->copy_done) cudaEventDestroy(e->copy_done);
     if (e->have_out) {
         cudaFree(e->d_out.obs_army);
         cudaFree(e->d_out.obs_owner);
@@ -616,6 +626,68 @@ int gen_rollout(gen_env* e, int K, uint64_t policy_seed, int32_t* d_actions, con
     return GEN_OK;
 }
 
+// The outputs of games [g0, g1) copied device -> host on stream t: every
+// per-game range is contiguous because offsets grow in game order.
+static int copy_out_range(gen_env* e, const gen_outputs& h, int32_t* h_next, int g0, int g1, cudaStream_t t) {
+    const gen_outputs& d = e->d_out;
+    const size_t p0 = (size_t)e->h_info[g0].plane_off;
+    const size_t p1 = g1 < e->G ? (size_t)e->h_info[g1].plane_off : (size_t)e->plane_cells;
+    const size_t s0 = (size_t)e->h_info[g0].player_off;
+    const size_t s1 = g1 < e->G ? (size_t)e->h_info[g1].player_off : (size_t)e->player_slots;
+    const size_t np = p1 - p0, ns = s1 - s0;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, t);
+    };
+    if (h_next) CUDA_TRY(cp(h_next + s0, e->d_actions + s0, ns * 4), "copy actions out");
+    if (h.obs_army) CUDA_TRY(cp(h.obs_army + p0, d.obs_army + p0, np * 2), "copy out");
+    if (h.obs_owner) CUDA_TRY(cp(h.obs_owner + p0, d.obs_owner + p0, np), "copy out");
+    if (h.obs_terrain) CUDA_TRY(cp(h.obs_terrain + p0, d.obs_terrain + p0, np), "copy out");
+    if (h.obs_vis) CUDA_TRY(cp(h.obs_vis + p0, d.obs_vis + p0, np), "copy out");
+    if (h.mask) CUDA_TRY(cp(h.mask + p0, d.mask + p0, np), "copy out");
+    if (h.reward) CUDA_TRY(cp(h.reward + s0, d.reward + s0, ns * 4), "copy out");
+    if (h.scoreboard) CUDA_TRY(cp(h.scoreboard + 2 * s0, d.scoreboard + 2 * s0, ns * 8), "copy out");
+    if (h.done) CUDA_TRY(cp(h.done + g0, d.done + g0, (size_t)(g1 - g0)), "copy out");
+    return GEN_OK;
+}
+
+// Pipelined host step for a batch launched as one bucket in game order: the
+// batch runs as K chunks of games on `s`, and each chunk's outputs leave on a
+// copy stream as soon as its launch ends, so the copies (bound by the host
+// link) overlap the remaining launches.
+static int step_host_pipelined(gen_env* e, const gen_outputs& h, uint64_t policy_seed, int32_t* h_next,
+                               cudaStream_t s, int K) {
+    if (!e->d_iota) {
+        std::vector<int32_t> iota((size_t)e->G);
+        for (int g = 0; g < e->G; ++g) iota[(size_t)g] = g;
+        CUDA_TRY(cudaMalloc(&e->d_iota, sizeof(int32_t) * (size_t)e->G), "cudaMalloc game ids");
+        CUDA_TRY(cudaMemcpy(e->d_iota, iota.data(), sizeof(int32_t) * (size_t)e->G, cudaMemcpyHostToDevice),
+                 "upload game ids");
+        CUDA_TRY(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking), "copy stream");
+        for (auto& v : e->chunk_ev) CUDA_TRY(cudaEventCreateWithFlags(&v, cudaEventDisableTiming), "chunk event");
+        CUDA_TRY(cudaEventCreateWithFlags(&e->copy_done, cudaEventDisableTiming), "copy event");
+    }
+    const Bucket& b = e->buckets[0];
+    for (int c = 0; c < K; ++c) {
+        const int g0 = (int)((int64_t)e->G * c / K), g1 = (int)((int64_t)e->G * (c + 1) / K);
+        KArgs a = base_args(e, b, gk::OP_STEP);
+        a.list = e->d_iota + g0;
+        a.n_items = g1 - g0;
+        a.actions = e->d_actions;
+        set_outputs(a, &e->d_out);
+        a.next_actions = h_next ? e->d_actions : nullptr;
+        a.policy_seed = policy_seed;
+        int rc = launch_one(b, a, s, "step launch");
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(e->chunk_ev[c], s), "chunk record");
+        CUDA_TRY(cudaStreamWaitEvent(e->copy, e->chunk_ev[c], 0), "chunk wait");
+        rc = copy_out_range(e, h, h_next, g0, g1, e->copy);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(e->copy_done, e->copy), "copy record");
+    CUDA_TRY(cudaStreamWaitEvent(s, e->copy_done, 0), "copy join");
+    return GEN_OK;
+}
+
 int gen_step_host(gen_env* e, const int32_t* h_actions, const gen_outputs* h_out, uint64_t policy_seed,
                   int32_t* h_next_actions, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
@@ -625,6 +697,12 @@ int gen_step_host(gen_env* e, const int32_t* h_actions, const gen_outputs* h_out
     cudaStream_t s = (cudaStream_t)stream;
     const size_t pc = (size_t)e->plane_cells, ps = (size_t)e->player_slots;
     CUDA_TRY(cudaMemcpyAsync(e->d_actions, h_actions, ps * 4, cudaMemcpyHostToDevice, s), "copy actions in");
+    if (e->buckets.size() == 1 && !e->d_order && e->G >= 8192) {
+        rc = step_host_pipelined(e, *h_out, policy_seed, h_next_actions, s, 4);
+        if (rc) return rc;
+        CUDA_TRY(cudaStreamSynchronize(s), "step_host sync");
+        return GEN_OK;
+    }
     rc = gen_step_policy(e, e->d_actions, &e->d_out, policy_seed, h_next_actions ? e->d_actions : nullptr, stream);
     if (rc) return rc;
     if (h_next_actions)

@@ -341,3 +341,30 @@ def test_exhaustive_joint_actions_on_gpu(side, rows):
         rows8[:, :2] = acts
         orc.step(rows8)
         compare_frame(env, out, orc, f"{side}x{side} turn {turn}")
+
+
+def test_host_step_pipelined_matches_device_step():
+    """gen_step_host on a batch large enough for its pipelined form (chunks of
+    games launched on the caller's stream, outputs copied out on a second
+    stream) gives the same bytes as the device-buffer step of a twin batch."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv, Outputs
+    G = 16384 + 7  # chunks of unequal size
+    kw = dict(seed=21, n_cities=4)
+    host = GeneralsEnv(17, 19, 0, 2, batch=G, **kw)
+    dev = GeneralsEnv(17, 19, 0, 2, batch=G, **kw)
+    h_out = Outputs(host.layout, pin_host=True)
+    d_out = dev.new_outputs()
+    acts = dev.new_actions()
+    dev.policy(4, acts)
+    h_act = acts.cpu().pin_memory()
+    h_next = torch.empty_like(h_act).pin_memory()
+    for f in range(6):
+        host.step_host(h_act, h_out, 4, h_next)
+        dev.step_policy(acts, d_out, 4, acts)
+        torch.cuda.synchronize()
+        for name, ht, dt in zip(("army", "owner", "terrain", "vis", "mask", "reward", "scoreboard", "done"),
+                                h_out.tensors(), d_out.tensors()):
+            assert torch.equal(ht, dt.cpu()), f"frame {f}: {name}"
+        assert torch.equal(h_next, acts.cpu()), f"frame {f}: next actions"
+        h_act.copy_(h_next)
