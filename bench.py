@@ -45,26 +45,29 @@ MAP_SEED = 1
 NCU_TRAFFIC = {"kernel_sha1": "e18bf723f508", "bytes_per_launch": 2 * 330900224.0,
                "warp_inst_per_launch": 2 * 90097229.0, "captured": "32,768 games (x2)", "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
+SAMPLE_NCU = {"kernel_sha1": "d7499ce12f09", "bytes_per_launch": 4 * 138351104.0,
+              "warp_inst_per_launch": 4 * 47394660.0, "captured": "16,384 games (x4)", "games": 65536}
 FEATURE_NCU_TRAFFIC = {"kernel_sha1": "6473b2b9435c", "bytes_per_launch": 8 * 1911564864.0,
                        "captured": "8,192 games (x8)", "games": 65536}
 
 
-def issue_roofline(launch_ms: float, G: int, clk) -> dict | None:
-    """The step kernel is issue-bound: warp instructions per launch (ncu
-    smsp__inst_executed.sum on the captured case, scaled by games) over the
-    launch time, against SMs x schedulers x the SM clock sampled during the
-    timed region."""
-    if NCU_TRAFFIC["kernel_sha1"] != kernel_sha1() or G != NCU_TRAFFIC["games"]:
+def issue_roofline(launch_ms: float, G: int, clk, rec=None, source="gk_kernels.cu") -> dict | None:
+    """An issue-bound kernel's second roofline: warp instructions per launch
+    (ncu smsp__inst_executed.sum on the captured case, scaled by games) over
+    the launch time, against SMs x schedulers x the SM clock sampled during
+    the timed region."""
+    rec = rec or NCU_TRAFFIC
+    if rec["kernel_sha1"] != kernel_sha1(source) or G != rec["games"]:
         return None
     mhz = (clk.summary() or {}).get("sm_mhz")
     if not mhz:
         return None
-    inst = NCU_TRAFFIC["warp_inst_per_launch"]
+    inst = rec["warp_inst_per_launch"]
     achieved = inst / (launch_ms * 1e-3)
     peak = SM_COUNT * SCHEDULERS_PER_SM * mhz * 1e6
     return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
             "frac": achieved / peak, "warp_inst_per_launch": inst, "warp_inst_per_frame": inst / G,
-            "source": f"ncu smsp__inst_executed.sum, {NCU_TRAFFIC['captured']}; peak at the sampled {mhz} MHz"}
+            "source": f"ncu smsp__inst_executed.sum, {rec['captured']}; peak at the sampled {mhz} MHz"}
 
 
 def kernel_sha1(name: str = "gk_kernels.cu") -> str:
@@ -677,9 +680,13 @@ def run_sampling(args, rank, world, local):
                        "owned_cells_per_player": owned / (2 * G),
                        "l2": "inputs larger than L2 (logits 2.7 GB)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "traffic": (SAMPLE_NCU["bytes_per_launch"]
+                                     if SAMPLE_NCU["kernel_sha1"] == kernel_sha1("gk_sample.cu")
+                                     and G == SAMPLE_NCU["games"] else None),
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": samp_ms,
                          "kernel": "k_sample (H x W x 9 policy sampling)"},
+            "issue_roofline": issue_roofline(samp_ms, G, clk, SAMPLE_NCU, "gk_sample.cu"),
             "step_launch_ms": step_ms,
             "gpu_launches": 2 * K,
             "clocks": clk.summary(),
