@@ -1,7 +1,9 @@
 """The N-rank path on CPU (gloo, world size 2): ranks step disjoint game-id
 ranges with no exchange; together they reproduce one process stepping every
-game, and the benchmark's reductions over ranks (max time, summed frames)
-behave as stated.  The oracle stands in for each rank's GPU here."""
+game (boards, scalars, feature tensors, temporal tokens and sampled actions,
+all keyed by the global game id), and the benchmark's reductions over ranks
+(max time, summed frames) behave as stated.  The oracle stands in for each
+rank's GPU here."""
 import hashlib
 import os
 import socket
@@ -27,10 +29,25 @@ def digest(env, g):
 
 
 def run_games(base, H, W, mode, P):
+    """Boards, scalars, the feature tensor with temporal tokens, and an action
+    sampled from logits seeded by the global game id, per game."""
+    from oracle.orc import OracleFeatures
     env = OracleEnv(H, W, mode, P, game_id_base=base, **KW)
+    feats = OracleFeatures(env, hist=3, window=8)
     for _ in range(FRAMES):
         env.step(env.policy(3))
-    return [digest(env, g) for g in range(env.G)]
+        f = feats.build()
+    logits = [np.random.default_rng(base + g).normal(0, 2, (int(env.P[g]), 9 * int(env.N[g]))).astype(np.float32)
+              for g in range(env.G)]
+    acts, _ = env.sample_actions(logits, 17)
+    out = []
+    for g in range(env.G):
+        h = hashlib.sha1(digest(env, g).encode())
+        h.update(f[g].tobytes())
+        h.update(feats.series[g].tobytes())
+        h.update(acts[g].tobytes())
+        out.append(h.hexdigest())
+    return out
 
 
 def rank_main(rank, world, port, H, W, mode, P, q):
