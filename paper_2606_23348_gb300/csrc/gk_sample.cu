@@ -22,7 +22,8 @@
 // player's own cells, so the warp first lists those cells in index order (a
 // ballot per 32 cells, no global load) and the passes run over the list, 32
 // own cells at a time: pass 1 derives each cell's nine legal bits and takes
-// the maximum; pass 2 (logits again, from L1/L2) sums each cell's weights,
+// the maximum; pass 2 (logits held in registers for the first 64 own cells,
+// read again from L1/L2 beyond) sums each cell's weights,
 // computing every exponential once, and keeps the sums per cell and per 32
 // cells; pass 3 finds the group, the cell and (nine lanes weighing the cell's
 // entries at once) the entry where the running sum first exceeds r.  Only the
@@ -193,8 +194,10 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta
         __syncwarp();
         int32_t action = 0;
         if (n > 0) {
-            // pass 1: legal bits and the maximum legal logit
+            // pass 1: legal bits and the maximum legal logit; the first two
+            // groups' logits stay in registers for pass 2
             float m = -3.402823466e38f;
+            float v0[9], v1[9];
             for (int i = lane; i < n; i += 32) {
                 const int c = s_list[i];
                 const uint32_t lb = legal9(true, s_army[c], s_terrain[c], moves);
@@ -204,6 +207,13 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
                     if ((lb >> k) & 1u) m = fmaxf(m, v[k]);
+                if (i < 32) {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) v0[k] = v[k];
+                } else if (i < 64) {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) v1[k] = v[k];
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
@@ -217,7 +227,15 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta
                     const int c = s_list[i];
                     const uint32_t lb = s_legal[i];
                     float v[9];
-                    load9(v, lg + 9 * c);
+                    if (i0 == 0) {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) v[k] = v0[k];
+                    } else if (i0 == 32) {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) v[k] = v1[k];
+                    } else {
+                        load9(v, lg + 9 * c);
+                    }
 #pragma unroll
                     for (int k = 0; k < 9; ++k)
                         if ((lb >> k) & 1u) w += weight_shift(v[k], m);
