@@ -1261,8 +1261,11 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
 // One warp per game; warps walk the item list with a grid stride.  MULTI:
 // several frames per launch (rollouts) with the board kept in shared memory.
 // SPAWN: the map generator with spawn options.
+// Register budget: 64 per thread (4 CTAs of 8 warps per SM) for the per-frame
+// form; the multi-frame form keeps more state live across frames and runs
+// best with 85 (3 CTAs).
 template <bool MULTI, bool SPAWN>
-__global__ void __launch_bounds__(256, 4) k_generals(const KArgs a) {
+__global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) {
     extern __shared__ __align__(16) char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
