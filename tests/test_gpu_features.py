@@ -206,3 +206,24 @@ def test_features_full_size_24x24_65536_sampled():
             want = ofb.build()
         compare_features(env, fb, fout, want, f"full size block {start}", games=range(start, start + n))
         compare_series(env, fb, ser, ofb.series, f"full size block {start}", games=range(start, start + n))
+
+
+def test_feature_builder_argument_errors():
+    """Bad arguments are refused with an error code and a message, not a fault."""
+    import ctypes as C
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv, GeneralsError
+    env = GeneralsEnv(6, 7, 0, 2, batch=3, seed=1)
+    lib = env.lib
+    h = C.c_void_p()
+    for hist, window in ((0, 0), (17, 0), (7, -1), (7, 4097)):
+        assert lib.gen_features_create_ex(C.byref(h), env.h, hist, window) != 0
+        assert lib.gen_last_error()
+    fb = env.features(3)
+    out = fb.new_output()
+    with pytest.raises(GeneralsError):
+        fb.build(out, torch.zeros(16, dtype=torch.int32, device="cuda"))  # no temporal window
+    assert lib.gen_features_build(fb.h, C.c_void_p(out.data_ptr() + 4), None) != 0  # misaligned
+    assert lib.gen_features_build(fb.h, None, None) != 0
+    fb.build(out)  # still usable
+    torch.cuda.synchronize()
