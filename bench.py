@@ -694,6 +694,72 @@ def run_sampling(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_selfplay(args, rank, world, local):
+    """The paper's rollout shape (512 environments x 512 steps) as a device
+    self-play loop: per frame, actions sampled from H x W x 9 logits, the
+    step, and the feature tensor with temporal tokens, with no host round
+    trip; plain launches and the same 512 frames replayed as one CUDA graph."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import shard, workload
+
+    torch.cuda.set_device(local)
+    G, T = 512, 512
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=G)
+    env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
+    fb = env.features(7, 512)
+    out, acts = env.new_outputs(), env.new_actions()
+    x, tok = fb.new_output(), fb.new_series()
+    g = torch.Generator(device="cuda").manual_seed(99 + rank)
+    logits = torch.randn(int(env.layout.plane_cells) * 9, generator=g, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def frame():
+        env.sample_actions(logits, POLICY_SEED, acts)
+        env.step(acts, out)
+        fb.build(x, tok)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            frame()
+    torch.cuda.synchronize()
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(T):
+            frame()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    res["plain"] = e0.elapsed_time(e1)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for _ in range(T):
+            frame()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+    res["graph"] = e0.elapsed_time(e1)
+    best = min(res, key=res.get)
+    value = sum_over_ranks(float(G * T), world) / (max_over_ranks(res[best], world) * 1e-3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "game frames/s of a device self-play rollout (sample, step, features)", "value": value,
+            "unit": "frames/s", "n_gpus": world, "steps": T, "warmup": max(3, args.warmup),
+            "ms_per_step": res[best] / T, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 logits and features, int16 state",
+            "data": "synthetic (seeded counter-hash maps, N(0, 1) logits, auto-reset)",
+            "config": {"workload": "selfplay-512x512", "games_per_gpu": G, "frames": T, "hist": 7,
+                       "temporal_window": 512, "l2": "fits in L2 (small batch; latency-bound)"},
+            "forms": {k: {"ms_per_frame": v / T, "frames_per_s": G * T / (v * 1e-3)} for k, v in res.items()},
+            "gpu_launches": 3 * T, "clocks": clk.summary()}), flush=True)
+
+
 def run_generator(args, rank, world, local):
     """Map generation throughput: gen_reset of every game of the default
     workload's shapes, for each generator option set."""
@@ -779,6 +845,8 @@ def main():
             run_features(args, rank, world, local)
         elif args.workload == "sample-65536x24x24":
             run_sampling(args, rank, world, local)
+        elif args.workload == "selfplay-512x512":
+            run_selfplay(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

@@ -155,3 +155,44 @@ def test_sampling_full_size_24x24_65536_sampled():
             orc.step(orc.policy(2))
         want, _ = orc.sample_actions(oracle_logits(env, flat, range(start, start + n)), 77)
         np.testing.assert_array_equal(ga[2 * start:2 * (start + n)], want[:, :2].reshape(-1))
+
+
+def test_selfplay_loop_in_a_cuda_graph_matches_plain_launches():
+    """Sample -> step -> features, 8 frames captured as one CUDA graph and
+    replayed, gives the same actions, state and features as plain launches."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    outs = []
+    for use_graph in (False, True):
+        env = GeneralsEnv(11, 13, 0, 2, batch=96, seed=6, n_cities=3, max_turns=9)
+        fb = env.features(3, 8)
+        out, acts = env.new_outputs(), env.new_actions()
+        x, tok = fb.new_output(), fb.new_series()
+        logits = torch.randn(int(env.layout.plane_cells) * 9, generator=torch.Generator(device="cuda").manual_seed(3),
+                             device="cuda")
+        s = torch.cuda.Stream()
+
+        def frame():
+            env.sample_actions(logits, 5, acts)
+            env.step(acts, out)
+            fb.build(x, tok)
+
+        with torch.cuda.stream(s):
+            frame()  # first calls outside any capture
+        torch.cuda.synchronize()
+        if use_graph:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                for _ in range(8):
+                    frame()
+            graph.replay()
+        else:
+            with torch.cuda.stream(s):
+                for _ in range(8):
+                    frame()
+        torch.cuda.synchronize()
+        st = env.read_state()
+        outs.append((acts.cpu(), x.cpu(), tok.cpu(), [torch.from_numpy(a.copy()) for a in st]))
+    (a0, x0, t0, s0), (a1, x1, t1, s1) = outs
+    assert torch.equal(a0, a1) and torch.equal(x0, x1) and torch.equal(t0, t1)
+    assert all(torch.equal(u, v) for u, v in zip(s0, s1))
