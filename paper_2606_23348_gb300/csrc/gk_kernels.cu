@@ -37,6 +37,7 @@ namespace gk {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kPairMaxCells = 1024;  // boards up to this many padded cells run two games per warp
 constexpr int kPlain = 0, kMountain = 1, kCastle = 2, kGeneral = 3;
 constexpr int kArmyMax = 32767;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
@@ -56,6 +57,40 @@ __device__ __forceinline__ uint64_t hkey(uint64_t s, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ uint32_t hdraw(uint64_t k, uint64_t i) { return (uint32_t)(stream_out(k, i) >> 32); }
 // uniform integer in [0, n) by multiply-shift
 __device__ __forceinline__ int uniform_below(uint32_t u, uint32_t n) { return (int)__umulhi(u, n); }
+
+// ---- a group of W lanes working on one game ----------------------------------
+// The whole warp (W = 32) or one of its halves (W = 16, two games per warp).
+// Collectives name only the group's lanes, so the two halves of a warp run
+// their games independently (also through divergent branches).
+template <int W>
+struct Grp {
+    int lane;       // 0 .. W-1
+    int shift;      // the group's first lane in the warp
+    unsigned mask;  // the group's lanes
+    __device__ __forceinline__ explicit Grp(int warp_lane)
+        : lane(warp_lane & (W - 1)), shift(W == 32 ? 0 : (warp_lane & 16)),
+          mask(W == 32 ? kFull : (0xFFFFu << (warp_lane & 16))) {}
+    template <class T>
+    __device__ __forceinline__ T shfl(T v, int src) const { return __shfl_sync(mask, v, src, W); }
+    template <class T>
+    __device__ __forceinline__ T shfl_up(T v, int d) const { return __shfl_up_sync(mask, v, d, W); }
+    // bit i = lane i of the group (the other half's lanes are masked off)
+    __device__ __forceinline__ unsigned ballot(bool pr) const {
+        if (W == 32) return __ballot_sync(kFull, pr);
+        return (__ballot_sync(mask, pr) & mask) >> shift;
+    }
+    __device__ __forceinline__ unsigned reduce_add(unsigned v) const {
+        if (W == 32) return __reduce_add_sync(kFull, v);
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
+        return v;
+    }
+    __device__ __forceinline__ bool any(bool pr) const {
+        if (W == 32) return __any_sync(kFull, pr);
+        return ballot(pr) != 0u;
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+};
 
 // ---- per-warp shared-memory view --------------------------------------------
 struct Smem {
@@ -144,15 +179,19 @@ __device__ __forceinline__ uint32_t valid_bits(int N, int w) {
 
 // passable-neighbour bits of every cell (bits 2..5 of the terrain byte),
 // from a mountain bitset so that no lane reads a byte another lane writes
-__device__ __forceinline__ void derive_passable(const Game& g, const Smem& s, int lane) {
+template <int LW>
+__device__ __forceinline__ void derive_passable(const Game& g, const Smem& s, const Grp<LW>& t) {
     const int N = g.N, W = g.W, H = g.H;
     for (int w = 0; w < g.nw; ++w) {
-        const int c = 32 * w + lane;
-        const unsigned m = __ballot_sync(kFull, c < N && (s.terrain[c] & 3) == kMountain);
-        if (lane == 0) s.tmp[w] = m;
+        unsigned m = 0;
+        for (int h = 0; h < 32; h += LW) {
+            const int c = 32 * w + h + t.lane;
+            m |= t.ballot(c < N && (s.terrain[c] & 3) == kMountain) << h;
+        }
+        if (t.lane == 0) s.tmp[w] = m;
     }
-    __syncwarp();
-    for (int c = lane; c < N; c += 32) {
+    t.sync();
+    for (int c = t.lane; c < N; c += LW) {
         const int r = c / W, col = c - r * W;
         auto mtn = [&](int x) { return (s.tmp[x >> 5] >> (x & 31)) & 1u; };
         uint32_t b = 0;
@@ -162,7 +201,7 @@ __device__ __forceinline__ void derive_passable(const Game& g, const Smem& s, in
         if (col < W - 1 && !mtn(c + 1)) b |= 8u;
         s.terrain[c] = (uint8_t)((s.terrain[c] & 3) | (b << 2));
     }
-    __syncwarp();
+    t.sync();
 }
 
 // ---- board geometry: first and last column bitsets -------------------------
@@ -171,14 +210,15 @@ __device__ __forceinline__ void derive_passable(const Game& g, const Smem& s, in
 constexpr int kColWords = (kMaxSide * kMaxSide) / 32;
 __device__ uint32_t g_columns[kMaxSide][2][kColWords];
 
-__device__ __forceinline__ void column_pass(const Game& g, const Smem& s, int lane) {
+template <int LW>
+__device__ __forceinline__ void column_pass(const Game& g, const Smem& s, const Grp<LW>& t) {
     const uint32_t* c0 = g_columns[g.W - 1][0];
     const uint32_t* cl = g_columns[g.W - 1][1];
-    for (int w = lane; w < g.nw; w += 32) {
+    for (int w = t.lane; w < g.nw; w += LW) {
         s.col0[w] = c0[w];
         s.colL[w] = cl[w];
     }
-    __syncwarp();
+    t.sync();
 }
 
 // ---- bitset BFS (generator options) ----------------------------------------
@@ -311,7 +351,7 @@ __device__ __forceinline__ GenScratch gen_scratch(const Smem& s) {
 __device__ __noinline__ int place_generals_bfs(const Game& g, const Smem& s, uint64_t kgen, int dmax, int lane) {
     const int N = g.N, P = g.P;
     const GenScratch z = gen_scratch(s);
-    column_pass(g, s, lane);
+    column_pass(g, s, Grp<32>(lane));
     cell_bits(z.pass, g, s, lane, [](int t, int) { return t != kMountain; });
     for (int w = lane; w < g.nw; w += 32) z.gens[w] = 0u;
     __syncwarp();
@@ -390,7 +430,7 @@ __device__ __noinline__ int place_generals_bfs(const Game& g, const Smem& s, uin
 __device__ __noinline__ void castle_guarantee(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
                                               uint32_t epoch, int radius, int lane) {
     const GenScratch z = gen_scratch(s);
-    column_pass(g, s, lane);
+    column_pass(g, s, Grp<32>(lane));
     uint32_t* free_plain = z.gens;
     cell_bits(z.pass, g, s, lane, [](int t, int) { return t != kMountain; });
     cell_bits(free_plain, g, s, lane, [](int t, int o) { return t == kPlain && o == -1; });
@@ -549,23 +589,24 @@ __device__ __forceinline__ void generate_spawn_body(const KArgs& a, const Game& 
     }
 
     if (a.castle_radius > 0) castle_guarantee(a, g, s, gid, epoch, a.castle_radius, lane);
-    derive_passable(g, s, lane);
+    derive_passable(g, s, Grp<32>(lane));
 }
 
 // ---- map generator (Sec. IV-A) ----------------------------------------------
+template <int LW>
 __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, const Smem& s, uint64_t gid,
-                                             uint32_t epoch, int lane) {
+                                             uint32_t epoch, const Grp<LW>& t) {
     const int N = g.N, W = g.W, P = g.P;
     const uint64_t kmtn = hkey(a.seed, gid, epoch, 1);
-    for (int c = lane; c < g.Npad; c += 32) {
+    for (int c = t.lane; c < g.Npad; c += LW) {
         bool m = c < N && hdraw(kmtn, (uint64_t)c) < a.mtn_thresh;
         s.army[c] = 0;
         s.owner[c] = -1;
         s.terrain[c] = m ? kMountain : kPlain;
     }
-    __syncwarp();
+    t.sync();
 
-    // generals: 32 candidate draws evaluated at once; the first accepted in
+    // generals: LW candidate draws evaluated at once; the first accepted in
     // draw order wins, so the draw counter advances exactly as one by one
     const uint64_t kgen = hkey(a.seed, gid, epoch, 2);
     uint32_t i = 0;
@@ -576,21 +617,21 @@ __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, con
         while (placed < 0) {
             if (D >= 1) {
                 int found = -1;
-                for (int base = 0; base < kGenAttempts; base += 32) {
-                    int t = base + lane;
-                    int c = uniform_below(hdraw(kgen, (uint64_t)(i + t)), (uint32_t)N);
-                    bool ok = (t < kGenAttempts) && s.terrain[c] != kMountain;
+                for (int base = 0; base < kGenAttempts; base += LW) {
+                    const int dr = base + t.lane;  // draw index
+                    int c = uniform_below(hdraw(kgen, (uint64_t)(i + dr)), (uint32_t)N);
+                    bool ok = (dr < kGenAttempts) && s.terrain[c] != kMountain;
                     int rc = c / W, cc = c - rc * W;
                     for (int q = 0; q < p; ++q) {
-                        int gq = __shfl_sync(kFull, my_gpos, q);
+                        int gq = t.shfl(my_gpos, q);
                         int rq = gq / W, cq = gq - rq * W;
                         if (abs(rc - rq) + abs(cc - cq) < D) ok = false;
                     }
-                    unsigned b = __ballot_sync(kFull, ok);
+                    unsigned b = t.ballot(ok);
                     if (b) {
                         int l = __ffs(b) - 1;
                         found = base + l;
-                        placed = __shfl_sync(kFull, c, l);
+                        placed = t.shfl(c, l);
                         break;
                     }
                 }
@@ -601,28 +642,28 @@ __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, con
                     D -= 1;
                 }
             } else {
-                for (int base = 0; base < N && placed < 0; base += 32) {
-                    int c = base + lane;
+                for (int base = 0; base < N && placed < 0; base += LW) {
+                    int c = base + t.lane;
                     bool ok = c < N;
                     for (int q = 0; q < p; ++q)
-                        if (__shfl_sync(kFull, my_gpos, q) == c) ok = false;
-                    unsigned b = __ballot_sync(kFull, ok);
+                        if (t.shfl(my_gpos, q) == c) ok = false;
+                    unsigned b = t.ballot(ok);
                     if (b) placed = base + __ffs(b) - 1;
                 }
             }
         }
-        if (lane == p) my_gpos = placed;
+        if (t.lane == p) my_gpos = placed;
     }
-    if (lane < P) {
+    if (t.lane < P) {
         s.terrain[my_gpos] = kGeneral;
-        s.owner[my_gpos] = (int8_t)lane;
+        s.owner[my_gpos] = (int8_t)t.lane;
         s.army[my_gpos] = 1;
-        s.misc[lane] = my_gpos;
+        s.misc[t.lane] = my_gpos;
     }
-    __syncwarp();
+    t.sync();
 
     // connectivity: L-path rows first, then columns, between consecutive generals
-    if (lane == 0) {
+    if (t.lane == 0) {
         for (int p = 0; p + 1 < P; ++p) {
             int r = s.misc[p] / W, c = s.misc[p] % W;
             int r1 = s.misc[p + 1] / W, c1 = s.misc[p + 1] % W;
@@ -636,7 +677,7 @@ __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, con
             }
         }
     }
-    __syncwarp();
+    t.sync();
 
     // neutral castles on neutral plain cells
     const uint64_t kpos = hkey(a.seed, gid, epoch, 3);
@@ -644,45 +685,47 @@ __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, con
     uint32_t j = 0;
     for (int k = 0; k < g.n_cities; ++k) {
         int found = -1, cell = 0;
-        for (int base = 0; base < kGenAttempts; base += 32) {
-            int t = base + lane;
-            int c = uniform_below(hdraw(kpos, (uint64_t)(j + t)), (uint32_t)N);
-            bool ok = (t < kGenAttempts) && s.terrain[c] == kPlain && s.owner[c] == -1;
-            unsigned b = __ballot_sync(kFull, ok);
+        for (int base = 0; base < kGenAttempts; base += LW) {
+            const int dr = base + t.lane;  // draw index
+            int c = uniform_below(hdraw(kpos, (uint64_t)(j + dr)), (uint32_t)N);
+            bool ok = (dr < kGenAttempts) && s.terrain[c] == kPlain && s.owner[c] == -1;
+            unsigned b = t.ballot(ok);
             if (b) {
                 int l = __ffs(b) - 1;
                 found = base + l;
-                cell = __shfl_sync(kFull, c, l);
+                cell = t.shfl(c, l);
                 break;
             }
         }
         if (found >= 0) {
             j += (uint32_t)found + 1;
-            if (lane == 0) {
+            if (t.lane == 0) {
                 s.terrain[cell] = kCastle;
                 s.army[cell] = (int16_t)(a.city_min + uniform_below(hdraw(karm, (uint64_t)k), (uint32_t)a.city_span));
             }
-            __syncwarp();
+            t.sync();
         } else {
             j += kGenAttempts;
         }
     }
-    derive_passable(g, s, lane);
+    derive_passable(g, s, t);
 }
 
 // Out-of-line entry points of the cold paths take plain arguments and rebuild
 // the game and shared-memory views themselves, so that the step kernel never
 // materialises those structures in local memory for a call it rarely makes.
+template <int LW>
 __device__ __noinline__ void generate(const KArgs& a, int gidx, char* warp_base, uint64_t gid, uint32_t epoch,
-                                     int lane) {
-    generate_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, lane);
+                                     int warp_lane) {
+    generate_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, Grp<LW>(warp_lane));
 }
 __device__ __noinline__ void generate_spawn(const KArgs& a, int gidx, char* warp_base, uint64_t gid,
                                            uint32_t epoch, int lane) {
     generate_spawn_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, lane);
 }
-__device__ __noinline__ void derive_passable_at(const KArgs& a, int gidx, char* warp_base, int lane) {
-    derive_passable(game_of(a, gidx), carve(warp_base, a), lane);
+template <int LW>
+__device__ __noinline__ void derive_passable_at(const KArgs& a, int gidx, char* warp_base, int warp_lane) {
+    derive_passable(game_of(a, gidx), carve(warp_base, a), Grp<LW>(warp_lane));
 }
 
 // ---- one move on lane 0 (Sec. IV-D, IV-E) ----------------------------------
@@ -744,8 +787,8 @@ __device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
 // bits 7, 15, 23, 31 of x -> bits 0..3
 __device__ __forceinline__ uint32_t gather4(uint32_t x80) { return (x80 * 0x00204081u) >> 28; }
 
-template <int PT>
-__device__ uint32_t chunk_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, int lane) {
+template <int PT, int LW>
+__device__ uint32_t chunk_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, const Grp<LW>& t) {
     const int P = g.P, nch = g.nch, st2 = 2 * s.stride;
     const bool grow = grow_s || grow_p;
     uint32_t sat = 0;
@@ -754,7 +797,7 @@ __device__ uint32_t chunk_pass(const Game& g, const Smem& s, bool grow_s, bool g
     for (int p = 0; p < PT; ++p) arm[p] = 0;
     uint16_t* own16 = reinterpret_cast<uint16_t*>(s.own);
     uint16_t* big16 = reinterpret_cast<uint16_t*>(s.big);
-    for (int ch = lane; ch < nch; ch += 32) {
+    for (int ch = t.lane; ch < nch; ch += LW) {
         const int c0 = ch << 4;
         const uint4 O = *reinterpret_cast<const uint4*>(s.owner + c0);
         const uint4 A0 = *reinterpret_cast<const uint4*>(s.army + c0);
@@ -826,30 +869,32 @@ __device__ uint32_t chunk_pass(const Game& g, const Smem& s, bool grow_s, bool g
                 if (p < P) own16[p * st2 + nch] = 0;
         }
     }
-    if (lane == 0) {
+    if (t.lane == 0) {
 #pragma unroll
         for (int p = 0; p < kMaxPlayers; ++p) s.misc[16 + p] = 0;
     }
 #pragma unroll
     for (int p = 0; p < PT; ++p) {
         if (p < P) {
-            const int tot = (int)__reduce_add_sync(kFull, (unsigned)arm[p]);
-            if (lane == 0) s.misc[16 + p] = tot;
+            const int tot = (int)t.reduce_add((unsigned)arm[p]);
+            if (t.lane == 0) s.misc[16 + p] = tot;
         }
     }
-    __syncwarp();
-    return __reduce_add_sync(kFull, sat);
+    t.sync();
+    return t.reduce_add(sat);
 }
 
-__device__ __forceinline__ uint32_t cell_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, int lane) {
-    if (g.P <= 2) return chunk_pass<2>(g, s, grow_s, grow_p, lane);
-    if (g.P <= 4) return chunk_pass<4>(g, s, grow_s, grow_p, lane);
-    return chunk_pass<8>(g, s, grow_s, grow_p, lane);
+template <int LW>
+__device__ __forceinline__ uint32_t cell_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, const Grp<LW>& t) {
+    if (g.P <= 2) return chunk_pass<2, LW>(g, s, grow_s, grow_p, t);
+    if (g.P <= 4) return chunk_pass<4, LW>(g, s, grow_s, grow_p, t);
+    return chunk_pass<8, LW>(g, s, grow_s, grow_p, t);
 }
 
 // ---- fog: 3x3 dilation of the (team) ownership bitset (Sec. IV-B) ----------
 // Also counts each player's land for the scoreboard.
-__device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane) {
+template <int LW>
+__device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, const Grp<LW>& t) {
     const int N = g.N, W = g.W, nw = g.nw, st = s.stride;
     const int q = W >> 5, sh = W & 31;
     const bool team = g.mode == 1;
@@ -857,7 +902,7 @@ __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane)
         const uint32_t* own = s.own + p * st;
         const uint32_t* ally = s.own + (p ^ 1) * st;
         int land = 0;
-        for (int w = lane; w < nw; w += 32) {
+        for (int w = t.lane; w < nw; w += LW) {
             const uint32_t mine = own[w];
             land += __popc(mine);
             const uint32_t T = mine | (team ? ally[w] : 0u);
@@ -867,11 +912,11 @@ __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane)
             const uint32_t R = (T >> 1) | (Tp << 31);  // bit c <- cell c+1
             s.tmp[w] = (T | (L & ~s.col0[w]) | (R & ~s.colL[w])) & valid_bits(N, w);
         }
-        land = (int)__reduce_add_sync(kFull, (unsigned)land);
-        if (lane == 0) s.misc[8 + p] = land;
-        __syncwarp();
+        land = (int)t.reduce_add((unsigned)land);
+        if (t.lane == 0) s.misc[8 + p] = land;
+        t.sync();
         const bool seeing = (alive >> p) & 1u;
-        for (int w = lane; w < nw; w += 32) {
+        for (int w = t.lane; w < nw; w += LW) {
             const uint32_t h = s.tmp[w];
             // bit c <- cell c - W (row above) and cell c + W (row below)
             const int wa = w - q;
@@ -882,7 +927,7 @@ __device__ void fog_pass(const Game& g, const Smem& s, uint32_t alive, int lane)
             if (sh && wb + 1 < nw) dn |= s.tmp[wb + 1] << (32 - sh);
             s.vis[p * st + w] = seeing ? ((h | up | dn) & valid_bits(N, w)) : 0u;
         }
-        __syncwarp();
+        t.sync();
     }
 }
 
@@ -897,11 +942,11 @@ __device__ __forceinline__ uint32_t nibbles16(uint32_t x) {
 
 // ---- observation + mask chunks of 16 cells (Sec. IV-B, App. A, Sec. IV-G) --
 // WRITE: store the planes; COUNT: legal (cell, direction) pairs per chunk.
-template <bool WRITE, bool COUNT>
-__device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished, int lane,
+template <bool WRITE, bool COUNT, int LW>
+__device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished, const Grp<LW>& t,
                             int64_t frame_off) {
     const int nch = g.nch, st = s.stride, P = g.P;
-    int p = 0, ch = lane;
+    int p = 0, ch = t.lane;
     while (p < P && ch >= nch) {
         ch -= nch;
         ++p;
@@ -954,20 +999,21 @@ __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32
             __stcs(reinterpret_cast<uint4*>(a.obs_vis + off), make_uint4(ov[0], ov[1], ov[2], ov[3]));
             __stcs(reinterpret_cast<uint4*>(a.mask + off), make_uint4(om[0], om[1], om[2], om[3]));
         }
-        ch += 32;
+        ch += LW;
         while (p < P && ch >= nch) {
             ch -= nch;
             ++p;
         }
     }
-    __syncwarp();
+    t.sync();
 }
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+template <int LW>
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, const Grp<LW>& t) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
+    for (int o = 1; o < LW; o <<= 1) {
+        const uint32_t y = t.shfl_up(x, o);
+        if (t.lane >= o) x += y;
     }
     return x;
 }
@@ -978,18 +1024,18 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 // 4 x 4096 legal pairs); the lane holding pair j walks its chunks and selects
 // the bit by popcount bisection.
 // Returns, on lane p < P, player p's action; DIRECT also stores it.
-template <bool DIRECT>
+template <bool DIRECT, int LW>
 __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uint32_t alive, bool finished,
-                               uint32_t frame, uint64_t gid, int lane) {
+                               uint32_t frame, uint64_t gid, const Grp<LW>& t) {
     int32_t mine_action = 0;
     const int nch = g.nch;
-    const int cpl = (nch + 31) >> 5;  // consecutive chunks per lane
-    const int c_lo = lane * cpl;
+    const int cpl = (nch + LW - 1) / LW;  // consecutive chunks per lane
+    const int c_lo = t.lane * cpl;
     const int c_hi = min(c_lo + cpl, nch);
     // lane p hashes player p's two draws
     uint32_t u1 = 0, u2 = 0;
-    if (lane < g.P) {
-        const uint64_t K = hkey(a.policy_seed, gid, frame, (uint64_t)lane);
+    if (t.lane < g.P) {
+        const uint64_t K = hkey(a.policy_seed, gid, frame, (uint64_t)t.lane);
         u1 = hdraw(K, 0);
         u2 = hdraw(K, 1);
     }
@@ -1000,20 +1046,20 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
             mine += __popcll(m0);
             if (p0 + 1 < g.P) mine += (uint32_t)__popcll(s.legal[(p0 + 1) * nch + c]) << 16;
         }
-        const uint32_t incl2 = warp_incl_scan(mine, lane);
-        const uint32_t total2 = __shfl_sync(kFull, incl2, 31);
+        const uint32_t incl2 = warp_incl_scan(mine, t);
+        const uint32_t total2 = t.shfl(incl2, LW - 1);
         for (int q = 0; q < 2 && p0 + q < g.P; ++q) {
             const int p = p0 + q;
             const uint32_t total = (total2 >> (16 * q)) & 0xFFFFu;
             const uint32_t incl = (incl2 >> (16 * q)) & 0xFFFFu;
-            const uint32_t pu1 = __shfl_sync(kFull, u1, p);
-            const uint32_t pu2 = __shfl_sync(kFull, u2, p);
+            const uint32_t pu1 = t.shfl(u1, p);
+            const uint32_t pu2 = t.shfl(u2, p);
             int32_t action = 0;
             if (total > 0 && !finished && ((alive >> p) & 1u)) {
                 const uint32_t j = (uint32_t)uniform_below(pu1, total);
-                const int L = __ffs(__ballot_sync(kFull, incl > j)) - 1;
+                const int L = __ffs(t.ballot(incl > j)) - 1;
                 int32_t found = 0;
-                if (lane == L) {
+                if (t.lane == L) {
                     uint32_t jj = j - (incl - ((mine >> (16 * q)) & 0xFFFFu));
                     for (int c = c_lo; c < c_hi; ++c) {
                         const uint64_t m = s.legal[p * nch + c];
@@ -1044,11 +1090,11 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
                         break;
                     }
                 }
-                action = __shfl_sync(kFull, found, L);
+                action = t.shfl(found, L);
             }
             if (DIRECT) {
-                if (lane == 0) a.next_actions[g.player_off + p] = action;
-            } else if (lane == p) {
+                if (t.lane == 0) a.next_actions[g.player_off + p] = action;
+            } else if (t.lane == p) {
                 mine_action = action;
             }
         }
@@ -1064,7 +1110,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
                  "l"(gmem)
                  : "memory");
 }
-__device__ __forceinline__ void board_issue(const KArgs& a, const Game& g, const Smem& s, int lane) {
+template <int LW>
+__device__ __forceinline__ void board_issue(const KArgs& a, const Game& g, const Smem& s, const Grp<LW>& t) {
     const int n16 = g.Npad >> 4;  // 16-byte vectors per int8 plane
     const uint4* ga = reinterpret_cast<const uint4*>(a.army + g.cell_off);
     const uint4* go = reinterpret_cast<const uint4*>(a.owner + g.cell_off);
@@ -1072,18 +1119,20 @@ __device__ __forceinline__ void board_issue(const KArgs& a, const Game& g, const
     uint4* sa = reinterpret_cast<uint4*>(s.army);
     uint4* so = reinterpret_cast<uint4*>(s.owner);
     uint4* st = reinterpret_cast<uint4*>(s.terrain);
-    for (int v = lane; v < 2 * n16; v += 32) cp_async16(sa + v, ga + v);
-    for (int v = lane; v < n16; v += 32) {
+    for (int v = t.lane; v < 2 * n16; v += LW) cp_async16(sa + v, ga + v);
+    for (int v = t.lane; v < n16; v += LW) {
         cp_async16(so + v, go + v);
         cp_async16(st + v, gt + v);
     }
 }
-__device__ __forceinline__ void board_wait() {
+template <int LW>
+__device__ __forceinline__ void board_wait(const Grp<LW>& t) {
     asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncwarp();
+    t.sync();
 }
 
-__device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const Smem& s, int lane) {
+template <int LW>
+__device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const Smem& s, const Grp<LW>& t) {
     const int n16 = g.Npad >> 4;
     uint4* ga = reinterpret_cast<uint4*>(a.army + g.cell_off);
     uint4* go = reinterpret_cast<uint4*>(a.owner + g.cell_off);
@@ -1091,8 +1140,8 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
     const uint4* sa = reinterpret_cast<const uint4*>(s.army);
     const uint4* so = reinterpret_cast<const uint4*>(s.owner);
     const uint4* st = reinterpret_cast<const uint4*>(s.terrain);
-    for (int v = lane; v < 2 * n16; v += 32) ga[v] = sa[v];
-    for (int v = lane; v < n16; v += 32) {
+    for (int v = t.lane; v < 2 * n16; v += LW) ga[v] = sa[v];
+    for (int v = t.lane; v < n16; v += LW) {
         go[v] = so[v];
         gt[v] = st[v];
     }
@@ -1103,23 +1152,23 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
 namespace {
 
 
-template <bool MULTI, bool SPAWN>
+template <bool MULTI, bool SPAWN, int LW>
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const int gidx,
-                                         const int lane) {
+                                         const Grp<LW>& t) {
     const Game g = game_of(a, gidx);
     GameScalars* sc = a.scal + gidx;
 
     // every global load of the step is issued here, before any is used
     const bool board = a.op != OP_CREATE && a.op != OP_RESET;
-    if (board) board_issue(a, g, s, lane);
+    if (board) board_issue(a, g, s, t);
     uint4 s0 = make_uint4(0, 0, 0, 0), s1 = make_uint4(0, 0, 0, 0);
     if (a.op != OP_CREATE) {
         s0 = *reinterpret_cast<const uint4*>(sc);
         s1 = *(reinterpret_cast<const uint4*>(sc) + 1);
     }
     // player `lane`'s action for the next step (frame 0: from the caller)
-    int32_t my_act = (a.op == OP_STEP && lane < g.P) ? a.actions[g.player_off + lane] : 0;
-    if (board) board_wait();
+    int32_t my_act = (a.op == OP_STEP && t.lane < g.P) ? a.actions[g.player_off + t.lane] : 0;
+    if (board) board_wait(t);
 
     uint32_t turn = 0, frame = 0, epoch = 0, alive = 0, finished = 0, invalid = 0, saturated = 0, err = 0;
     if (a.op != OP_CREATE) {
@@ -1138,15 +1187,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
         if constexpr (SPAWN)
-            generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
+            generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
         else
-            generate(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
+            generate<LW>(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
     } else if (a.op == OP_DERIVE) {
-        derive_passable_at(a, gidx, warp_base, lane);
+        derive_passable_at<LW>(a, gidx, warp_base, t.lane + t.shift);
         wrote_state = true;
     }
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
@@ -1154,50 +1203,50 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
         float my_reward = 0.0f;
         uint32_t done = 0;
         if (a.op == OP_STEP && !finished) {
-            if (MULTI && a.action_log && lane < g.P)
-                a.action_log[(int64_t)f * a.slot_stride + g.player_off + lane] = my_act;
+            if (MULTI && a.action_log && t.lane < g.P)
+                a.action_log[(int64_t)f * a.slot_stride + g.player_off + t.lane] = my_act;
             // moves in rotating priority, each checked when it runs (Q1)
             uint32_t eliminated = 0;
             uint32_t inv0 = 0, sat0 = 0;
             for (int k = 0; k < g.P; ++k) {
                 const int p = (int)((turn + (uint32_t)k) % (uint32_t)g.P);
-                const int32_t act = __shfl_sync(kFull, my_act, p);
+                const int32_t act = t.shfl(my_act, p);
                 int cap = 0;
-                if (lane == 0 && ((alive >> p) & 1u)) cap = resolve_move(g, s, p, act, alive, inv0, sat0);
-                cap = __shfl_sync(kFull, cap, 0);
-                alive = __shfl_sync(kFull, alive, 0);
-                __syncwarp();
+                if (t.lane == 0 && ((alive >> p) & 1u)) cap = resolve_move(g, s, p, act, alive, inv0, sat0);
+                cap = t.shfl(cap, 0);
+                alive = t.shfl(alive, 0);
+                t.sync();
                 if (cap) {
                     // land transfer: every other cell of the loser, army - army/2 (Q7)
                     const int dst = cap & 0xFFFF, q = (cap >> 16) - 1;
                     eliminated |= 1u << q;
-                    for (int c = lane; c < g.N; c += 32) {
+                    for (int c = t.lane; c < g.N; c += LW) {
                         if (c != dst && s.owner[c] == q) {
                             s.owner[c] = (int8_t)p;
                             const int av = s.army[c];
                             s.army[c] = (int16_t)(av - (av >> 1));
                         }
                     }
-                    __syncwarp();
+                    t.sync();
                 }
             }
-            invalid += __shfl_sync(kFull, inv0, 0);
-            saturated += __shfl_sync(kFull, sat0, 0);
+            invalid += t.shfl(inv0, 0);
+            saturated += t.shfl(sat0, 0);
             turn += 1;
-            saturated += cell_pass(g, s, (turn % 2u) == 0u, (turn % 50u) == 0u, lane);
+            saturated += cell_pass(g, s, (turn % 2u) == 0u, (turn % 50u) == 0u, t);
             // termination and reward (Sec. III, IV-D, IV-E; Q17, Q21)
             if (g.mode == 1) {
                 const bool dead0 = (alive & 0x3u) == 0u, dead1 = (alive & 0xCu) == 0u;
                 if (dead0 || dead1) {
                     done = 1;
-                    const bool mine_dead = ((lane >> 1) == 0) ? dead0 : dead1;
+                    const bool mine_dead = ((t.lane >> 1) == 0) ? dead0 : dead1;
                     my_reward = mine_dead ? -1.0f : 1.0f;
                 }
             } else {
-                if ((eliminated >> lane) & 1u) my_reward = -1.0f;
+                if ((eliminated >> t.lane) & 1u) my_reward = -1.0f;
                 if (__popc(alive) <= 1) {
                     done = 1;
-                    if ((alive >> lane) & 1u) my_reward = 1.0f;
+                    if ((alive >> t.lane) & 1u) my_reward = 1.0f;
                 }
             }
             if (!done && a.max_turns > 0 && turn >= (uint32_t)a.max_turns) done = 2;
@@ -1205,12 +1254,12 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
                 if (a.auto_reset) {
                     epoch += 1;
                     if constexpr (SPAWN)
-                        generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
+                        generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
                     else
-                        generate(a, gidx, warp_base, game_id_of(a, gidx), epoch, lane);
+                        generate<LW>(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
                     turn = 0;
                     alive = all_alive;
-                    cell_pass(g, s, false, false, lane);
+                    cell_pass(g, s, false, false, t);
                 } else {
                     finished = 1;
                 }
@@ -1218,7 +1267,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
             wrote_state = true;
         } else {
             // create, reset, observe, policy, or a frozen game
-            saturated += cell_pass(g, s, false, false, lane);
+            saturated += cell_pass(g, s, false, false, t);
         }
         if (a.op == OP_STEP) frame += 1;
 
@@ -1226,29 +1275,29 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
         if (a.do_outputs) {
             const int64_t poff = (int64_t)f * a.plane_stride;
             const int64_t soff = (int64_t)f * a.slot_stride;
-            column_pass(g, s, lane);
-            fog_pass(g, s, alive, lane);
+            column_pass(g, s, t);
+            fog_pass(g, s, alive, t);
             if (a.next_actions)
-                output_pass<true, true>(a, g, s, alive, fin, lane, poff);
+                output_pass<true, true, LW>(a, g, s, alive, fin, t, poff);
             else
-                output_pass<true, false>(a, g, s, alive, fin, lane, poff);
-            if (lane < g.P) {
-                a.reward[soff + g.player_off + lane] = my_reward;
-                a.scoreboard[2 * (soff + g.player_off + lane) + 0] = s.misc[8 + lane];
-                a.scoreboard[2 * (soff + g.player_off + lane) + 1] = s.misc[16 + lane];
+                output_pass<true, false, LW>(a, g, s, alive, fin, t, poff);
+            if (t.lane < g.P) {
+                a.reward[soff + g.player_off + t.lane] = my_reward;
+                a.scoreboard[2 * (soff + g.player_off + t.lane) + 0] = s.misc[8 + t.lane];
+                a.scoreboard[2 * (soff + g.player_off + t.lane) + 1] = s.misc[16 + t.lane];
             }
-            if (lane == 0) a.done[(int64_t)f * a.game_stride + gidx] = (uint8_t)done;
+            if (t.lane == 0) a.done[(int64_t)f * a.game_stride + gidx] = (uint8_t)done;
         } else if (a.next_actions) {
-            output_pass<false, true>(a, g, s, alive, fin, lane, 0);
+            output_pass<false, true, LW>(a, g, s, alive, fin, t, 0);
         }
-        if (a.next_actions) my_act = policy_pass<!MULTI>(a, g, s, alive, fin, frame, game_id_of(a, gidx), lane);
+        if (a.next_actions) my_act = policy_pass<!MULTI, LW>(a, g, s, alive, fin, frame, game_id_of(a, gidx), t);
     }
-    if (MULTI && a.next_actions && lane < g.P) a.next_actions[g.player_off + lane] = my_act;
+    if (MULTI && a.next_actions && t.lane < g.P) a.next_actions[g.player_off + t.lane] = my_act;
     if (wrote_state) {
-        __syncwarp();
-        store_board(a, g, s, lane);
+        t.sync();
+        store_board(a, g, s, t);
     }
-    if (lane == 0 && a.op != OP_OBSERVE && a.op != OP_POLICY) {
+    if (t.lane == 0 && a.op != OP_OBSERVE && a.op != OP_POLICY) {
         uint4* dst = reinterpret_cast<uint4*>(sc);
         dst[0] = make_uint4(turn, frame, epoch, alive);
         dst[1] = make_uint4(finished, invalid, saturated, a.op == OP_CREATE ? 0u : err);
@@ -1258,33 +1307,36 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
 
 }  // namespace
 
-// One warp per game; warps walk the item list with a grid stride.  MULTI:
-// several frames per launch (rollouts) with the board kept in shared memory.
-// SPAWN: the map generator with spawn options.
+// One game per group of W lanes (W = 32: a warp; W = 16: two games per warp);
+// groups walk the item list with a grid stride.  MULTI: several frames per
+// launch (rollouts) with the board kept in shared memory.  SPAWN: the map
+// generator with spawn options (W = 32 only).
 // Register budget: 64 per thread (4 CTAs of 8 warps per SM) for the per-frame
 // form; the multi-frame form keeps more state live across frames and runs
 // best with 85 (3 CTAs).
-template <bool MULTI, bool SPAWN>
+template <bool MULTI, bool SPAWN, int LW>
 __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) {
     extern __shared__ __align__(16) char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int wpc = blockDim.x >> 5;
-    char* warp_base = smem_raw + wid * a.warp_smem;
+    constexpr int kGroups = 32 / LW;  // games per warp
+    const int wl = threadIdx.x & 31;
+    const Grp<LW> t(wl);
+    const int grp = (threadIdx.x >> 5) * kGroups + (wl >> 4) * (kGroups - 1);  // group in the CTA
+    const int gpc = (blockDim.x >> 5) * kGroups;                                // groups per CTA
+    char* warp_base = smem_raw + grp * a.warp_smem;
     const Smem s = carve(warp_base, a);
     if (!MULTI) {  // the grid covers every item
-        const int item = blockIdx.x * wpc + wid;
+        const int item = blockIdx.x * gpc + grp;
         if (item >= a.n_items) return;
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) return;
-        run_game<MULTI, SPAWN>(a, s, warp_base, gidx, lane);
+        run_game<MULTI, SPAWN, LW>(a, s, warp_base, gidx, t);
         return;
     }
-    for (int item = blockIdx.x * wpc + wid; item < a.n_items; item += gridDim.x * wpc) {
+    for (int item = blockIdx.x * gpc + grp; item < a.n_items; item += gridDim.x * gpc) {
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) continue;
-        __syncwarp();
-        run_game<MULTI, SPAWN>(a, s, warp_base, gidx, lane);
+        t.sync();
+        run_game<MULTI, SPAWN, LW>(a, s, warp_base, gidx, t);
     }
 }
 
@@ -1318,12 +1370,12 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
     static SmemLimit limit;  // per device, only ever raised
-    const void* fns[4] = {(const void*)k_generals<false, false>, (const void*)k_generals<true, false>,
-                          (const void*)k_generals<false, true>, (const void*)k_generals<true, true>};
+    const void* fns[4] = {(const void*)k_generals<false, false, 32>, (const void*)k_generals<true, false, 32>,
+                          (const void*)k_generals<false, true, 32>, (const void*)k_generals<true, true, 32>};
     cudaError_t e = (cudaError_t)limit.raise(fns, 4, smem_bytes);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0, dev = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false>, 32 * warps_per_cta,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false, 32>, 32 * warps_per_cta,
                                                            smem_bytes)) != cudaSuccess)
         return (int)e;
     cudaGetDevice(&dev);
@@ -1350,22 +1402,35 @@ int init_tables() {
 int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     if (a.n_items <= 0) return 0;
 
-    const int smem = a.warp_smem * warps_per_cta;
-    int blocks = (a.n_items + warps_per_cta - 1) / warps_per_cta;
-    const bool multi = a.frames > 1 || a.action_log;
-    // multi-frame launches: a grid of many waves, warps stride over any items beyond it
-    if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
     const bool spawn = a.spawn_dmax > 0 || a.spawn_bfs || a.castle_radius > 0;
-    const dim3 grid(blocks), block(32 * warps_per_cta);
+    const bool multi = a.frames > 1 || a.action_log;
     const cudaStream_t st = (cudaStream_t)stream;
-    if (multi && spawn)
-        k_generals<true, true><<<grid, block, smem, st>>>(a);
-    else if (multi)
-        k_generals<true, false><<<grid, block, smem, st>>>(a);
-    else if (spawn)
-        k_generals<false, true><<<grid, block, smem, st>>>(a);
-    else
-        k_generals<false, false><<<grid, block, smem, st>>>(a);
+    // two games per warp for small boards (16 lanes each), plain generator only
+    const bool pair = !spawn && a.npad_max <= kPairMaxCells && 2 * warps_per_cta * a.warp_smem <= 227 * 1024;
+    const int games_per_cta = (pair ? 2 : 1) * warps_per_cta;
+    const int smem = a.warp_smem * games_per_cta;
+    int blocks = (a.n_items + games_per_cta - 1) / games_per_cta;
+    // multi-frame launches: a grid of many waves, groups stride over any items beyond it
+    if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
+    const dim3 grid(blocks), block(32 * warps_per_cta);
+    if (pair) {
+        static SmemLimit limit;
+        const void* fns[2] = {(const void*)k_generals<false, false, 16>, (const void*)k_generals<true, false, 16>};
+        const int e = limit.raise(fns, 2, smem);
+        if (e != 0) return e;
+        if (multi)
+            k_generals<true, false, 16><<<grid, block, smem, st>>>(a);
+        else
+            k_generals<false, false, 16><<<grid, block, smem, st>>>(a);
+    } else if (multi && spawn) {
+        k_generals<true, true, 32><<<grid, block, smem, st>>>(a);
+    } else if (multi) {
+        k_generals<true, false, 32><<<grid, block, smem, st>>>(a);
+    } else if (spawn) {
+        k_generals<false, true, 32><<<grid, block, smem, st>>>(a);
+    } else {
+        k_generals<false, false, 32><<<grid, block, smem, st>>>(a);
+    }
     return (int)cudaGetLastError();
 }
 
