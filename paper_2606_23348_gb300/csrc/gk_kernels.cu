@@ -37,7 +37,9 @@ namespace gk {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kPairMaxCells = 1024;  // boards up to this many padded cells run two games per warp
+// games with at most this many padded cells and players run two per warp
+constexpr int kPairMaxCells = 1024;
+constexpr int kPairMaxPlayers = 2;
 constexpr int kPlain = 0, kMountain = 1, kCastle = 2, kGeneral = 3;
 constexpr int kArmyMax = 32767;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
@@ -1406,7 +1408,8 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     const bool multi = a.frames > 1 || a.action_log;
     const cudaStream_t st = (cudaStream_t)stream;
     // two games per warp for small boards (16 lanes each), plain generator only
-    const bool pair = !spawn && a.npad_max <= kPairMaxCells && 2 * warps_per_cta * a.warp_smem <= 227 * 1024;
+    const bool pair = !spawn && a.npad_max <= kPairMaxCells && a.pmax <= kPairMaxPlayers &&
+                      2 * warps_per_cta * a.warp_smem <= 227 * 1024;
     const int games_per_cta = (pair ? 2 : 1) * warps_per_cta;
     const int smem = a.warp_smem * games_per_cta;
     int blocks = (a.n_items + games_per_cta - 1) / games_per_cta;
