@@ -129,7 +129,7 @@ __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
     w += pm * st;
     s.tmp = w;
     w += st;
-    s.legal = reinterpret_cast<uint64_t*>(w);  // 16-byte aligned: every region above is
+    s.legal = reinterpret_cast<uint64_t*>(w);  // 8-byte aligned: every region above is
     w += (2 * pm * (np >> 4) + 3) & ~3;
     s.misc = reinterpret_cast<int32_t*>(w);
     s.stride = st;
@@ -1364,7 +1364,7 @@ __global__ void k_copy(const uint4* __restrict__ src, uint4* __restrict__ dst, s
 
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
     int nw = (npad_max + 31) / 32;
-    nw = (nw + 3) & ~3;
+    nw = (nw + 1) & ~1;  // even: the carve stays a multiple of 16 bytes
     if (nw_stride) *nw_stride = nw;
     const int legal_words = (2 * pmax * (npad_max >> 4) + 3) & ~3;
     return 4 * npad_max + 4 * nw * (2 * pmax + 4) + 4 * legal_words + 4 * 24;
