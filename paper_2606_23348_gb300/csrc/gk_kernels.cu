@@ -37,7 +37,11 @@ namespace gk {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-// games with at most this many padded cells and players run two per warp
+// games with at most two players share a warp: two (16 lanes each) up to
+// kPairMaxCells padded cells, and in multi-frame launches four (8 lanes each)
+// up to kQuadMaxCells (measured: per-frame launches of small boards lose with
+// four, resident rollouts gain)
+constexpr int kQuadMaxCells = 576;
 constexpr int kPairMaxCells = 1024;
 constexpr int kPairMaxPlayers = 2;
 constexpr int kPlain = 0, kMountain = 1, kCastle = 2, kGeneral = 3;
@@ -70,8 +74,8 @@ struct Grp {
     int shift;      // the group's first lane in the warp
     unsigned mask;  // the group's lanes
     __device__ __forceinline__ explicit Grp(int warp_lane)
-        : lane(warp_lane & (W - 1)), shift(W == 32 ? 0 : (warp_lane & 16)),
-          mask(W == 32 ? kFull : (0xFFFFu << (warp_lane & 16))) {}
+        : lane(warp_lane & (W - 1)), shift(W == 32 ? 0 : (warp_lane & (32 - W))),
+          mask(W == 32 ? kFull : (((1u << W) - 1u) << (warp_lane & (32 - W)))) {}
     template <class T>
     __device__ __forceinline__ T shfl(T v, int src) const { return __shfl_sync(mask, v, src, W); }
     template <class T>
@@ -1322,7 +1326,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) 
     constexpr int kGroups = 32 / LW;  // games per warp
     const int wl = threadIdx.x & 31;
     const Grp<LW> t(wl);
-    const int grp = (threadIdx.x >> 5) * kGroups + (wl >> 4) * (kGroups - 1);  // group in the CTA
+    const int grp = (threadIdx.x >> 5) * kGroups + wl / LW;  // group in the CTA
     const int gpc = (blockDim.x >> 5) * kGroups;                                // groups per CTA
     char* warp_base = smem_raw + grp * a.warp_smem;
     const Smem s = carve(warp_base, a);
@@ -1407,16 +1411,29 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     const bool spawn = a.spawn_dmax > 0 || a.spawn_bfs || a.castle_radius > 0;
     const bool multi = a.frames > 1 || a.action_log;
     const cudaStream_t st = (cudaStream_t)stream;
-    // two games per warp for small boards (16 lanes each), plain generator only
-    const bool pair = !spawn && a.npad_max <= kPairMaxCells && a.pmax <= kPairMaxPlayers &&
-                      2 * warps_per_cta * a.warp_smem <= 227 * 1024;
-    const int games_per_cta = (pair ? 2 : 1) * warps_per_cta;
+    // several games per warp for small two-player boards, plain generator only
+    const bool small = !spawn && a.pmax <= kPairMaxPlayers;
+    int per_warp = 1;
+    if (small && multi && a.npad_max <= kQuadMaxCells && 4 * warps_per_cta * a.warp_smem <= 227 * 1024)
+        per_warp = 4;
+    else if (small && a.npad_max <= kPairMaxCells && 2 * warps_per_cta * a.warp_smem <= 227 * 1024)
+        per_warp = 2;
+    const int games_per_cta = per_warp * warps_per_cta;
     const int smem = a.warp_smem * games_per_cta;
     int blocks = (a.n_items + games_per_cta - 1) / games_per_cta;
     // multi-frame launches: a grid of many waves, groups stride over any items beyond it
     if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
     const dim3 grid(blocks), block(32 * warps_per_cta);
-    if (pair) {
+    if (per_warp == 4) {
+        static SmemLimit limit;
+        const void* fns[2] = {(const void*)k_generals<false, false, 8>, (const void*)k_generals<true, false, 8>};
+        const int e = limit.raise(fns, 2, smem);
+        if (e != 0) return e;
+        if (multi)
+            k_generals<true, false, 8><<<grid, block, smem, st>>>(a);
+        else
+            k_generals<false, false, 8><<<grid, block, smem, st>>>(a);
+    } else if (per_warp == 2) {
         static SmemLimit limit;
         const void* fns[2] = {(const void*)k_generals<false, false, 16>, (const void*)k_generals<true, false, 16>};
         const int e = limit.raise(fns, 2, smem);
