@@ -86,10 +86,13 @@ struct Grp {
         return (__ballot_sync(mask, pr) & mask) >> shift;
     }
     __device__ __forceinline__ unsigned reduce_add(unsigned v) const {
-        if (W == 32) return __reduce_add_sync(kFull, v);
+        if constexpr (W == 32) {
+            return __reduce_add_sync(kFull, v);
+        } else {
 #pragma unroll
-        for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
-        return v;
+            for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
+            return v;
+        }
     }
     __device__ __forceinline__ bool any(bool pr) const {
         if (W == 32) return __any_sync(kFull, pr);
@@ -164,16 +167,21 @@ __device__ __forceinline__ Game load_game(const GameInfo* gi) {
     return g;
 }
 
+// UNI: the launch's games all have the launch's shape (a.uniform), so every
+// field is a kernel parameter or follows from gidx; a kernel compiled for it
+// keeps none of them in registers.
+template <bool UNI = false>
 __device__ __forceinline__ Game game_of(const KArgs& a, int gidx) {
-    if (!a.uniform) return load_game(a.info + gidx);
+    if (!UNI && !a.uniform) return load_game(a.info + gidx);
     Game g = load_game(&a.ushape);
     g.cell_off = gidx * g.Npad;
     g.player_off = gidx * g.P;
     g.plane_off = (int64_t)gidx * g.P * g.Npad;
     return g;
 }
+template <bool UNI = false>
 __device__ __forceinline__ uint64_t game_id_of(const KArgs& a, int gidx) {
-    return a.uniform ? a.game_id_base + (uint64_t)gidx : a.info[gidx].game_id;
+    return (UNI || a.uniform) ? a.game_id_base + (uint64_t)gidx : a.info[gidx].game_id;
 }
 
 __device__ __forceinline__ uint32_t valid_bits(int N, int w) {
@@ -720,18 +728,18 @@ __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, con
 // Out-of-line entry points of the cold paths take plain arguments and rebuild
 // the game and shared-memory views themselves, so that the step kernel never
 // materialises those structures in local memory for a call it rarely makes.
-template <int LW>
+template <int LW, bool UNI>
 __device__ __noinline__ void generate(const KArgs& a, int gidx, char* warp_base, uint64_t gid, uint32_t epoch,
                                      int warp_lane) {
-    generate_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, Grp<LW>(warp_lane));
+    generate_body(a, game_of<UNI>(a, gidx), carve(warp_base, a), gid, epoch, Grp<LW>(warp_lane));
 }
 __device__ __noinline__ void generate_spawn(const KArgs& a, int gidx, char* warp_base, uint64_t gid,
                                            uint32_t epoch, int lane) {
     generate_spawn_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, lane);
 }
-template <int LW>
+template <int LW, bool UNI>
 __device__ __noinline__ void derive_passable_at(const KArgs& a, int gidx, char* warp_base, int warp_lane) {
-    derive_passable(game_of(a, gidx), carve(warp_base, a), Grp<LW>(warp_lane));
+    derive_passable(game_of<UNI>(a, gidx), carve(warp_base, a), Grp<LW>(warp_lane));
 }
 
 // ---- one move on lane 0 (Sec. IV-D, IV-E) ----------------------------------
@@ -1158,10 +1166,10 @@ __device__ __forceinline__ void store_board(const KArgs& a, const Game& g, const
 namespace {
 
 
-template <bool MULTI, bool SPAWN, int LW>
+template <bool MULTI, bool SPAWN, int LW, bool UNI>
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const int gidx,
                                          const Grp<LW>& t) {
-    const Game g = game_of(a, gidx);
+    const Game g = game_of<UNI>(a, gidx);
     GameScalars* sc = a.scal + gidx;
 
     // every global load of the step is issued here, before any is used
@@ -1193,15 +1201,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
         if constexpr (SPAWN)
-            generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
+            generate_spawn(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         else
-            generate<LW>(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
+            generate<LW, UNI>(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
     } else if (a.op == OP_DERIVE) {
-        derive_passable_at<LW>(a, gidx, warp_base, t.lane + t.shift);
+        derive_passable_at<LW, UNI>(a, gidx, warp_base, t.lane + t.shift);
         wrote_state = true;
     }
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
@@ -1260,9 +1268,9 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
                 if (a.auto_reset) {
                     epoch += 1;
                     if constexpr (SPAWN)
-                        generate_spawn(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
+                        generate_spawn(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     else
-                        generate<LW>(a, gidx, warp_base, game_id_of(a, gidx), epoch, t.lane + t.shift);
+                        generate<LW, UNI>(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, t);
@@ -1296,7 +1304,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
         } else if (a.next_actions) {
             output_pass<false, true, LW>(a, g, s, alive, fin, t, 0);
         }
-        if (a.next_actions) my_act = policy_pass<!MULTI, LW>(a, g, s, alive, fin, frame, game_id_of(a, gidx), t);
+        if (a.next_actions) my_act = policy_pass<!MULTI, LW>(a, g, s, alive, fin, frame, game_id_of<UNI>(a, gidx), t);
     }
     if (MULTI && a.next_actions && t.lane < g.P) a.next_actions[g.player_off + t.lane] = my_act;
     if (wrote_state) {
@@ -1313,14 +1321,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
 
 }  // namespace
 
-// One game per group of W lanes (W = 32: a warp; W = 16: two games per warp);
-// groups walk the item list with a grid stride.  MULTI: several frames per
-// launch (rollouts) with the board kept in shared memory.  SPAWN: the map
-// generator with spawn options (W = 32 only).
+// One game per group of LW lanes (32: a warp; 16 or 8: two or four games per
+// warp); groups walk the item list with a grid stride.  MULTI: several frames
+// per launch (rollouts) with the board kept in shared memory.  SPAWN: the map
+// generator with spawn options (LW = 32 only).  UNI: every game of the launch
+// has the launch's shape (uniform batches).
 // Register budget: 64 per thread (4 CTAs of 8 warps per SM) for the per-frame
 // form; the multi-frame form keeps more state live across frames and runs
 // best with 85 (3 CTAs).
-template <bool MULTI, bool SPAWN, int LW>
+template <bool MULTI, bool SPAWN, int LW, bool UNI>
 __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) {
     extern __shared__ __align__(16) char smem_raw[];
     constexpr int kGroups = 32 / LW;  // games per warp
@@ -1330,19 +1339,19 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) 
     const int gpc = (blockDim.x >> 5) * kGroups;                                // groups per CTA
     char* warp_base = smem_raw + grp * a.warp_smem;
     const Smem s = carve(warp_base, a);
-    if (!MULTI) {  // the grid covers every item
+    if constexpr (!MULTI) {  // the grid covers every item
         const int item = blockIdx.x * gpc + grp;
         if (item >= a.n_items) return;
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) return;
-        run_game<MULTI, SPAWN, LW>(a, s, warp_base, gidx, t);
-        return;
-    }
-    for (int item = blockIdx.x * gpc + grp; item < a.n_items; item += gridDim.x * gpc) {
-        const int gidx = a.list ? a.list[item] : item;
-        if (gidx < 0 || gidx >= a.n_games) continue;
-        t.sync();
-        run_game<MULTI, SPAWN, LW>(a, s, warp_base, gidx, t);
+        run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, gidx, t);
+    } else {
+        for (int item = blockIdx.x * gpc + grp; item < a.n_items; item += gridDim.x * gpc) {
+            const int gidx = a.list ? a.list[item] : item;
+            if (gidx < 0 || gidx >= a.n_games) continue;
+            t.sync();
+            run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, gidx, t);
+        }
     }
 }
 
@@ -1376,12 +1385,13 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
     static SmemLimit limit;  // per device, only ever raised
-    const void* fns[4] = {(const void*)k_generals<false, false, 32>, (const void*)k_generals<true, false, 32>,
-                          (const void*)k_generals<false, true, 32>, (const void*)k_generals<true, true, 32>};
-    cudaError_t e = (cudaError_t)limit.raise(fns, 4, smem_bytes);
+    const void* fns[6] = {(const void*)k_generals<false, false, 32, false>, (const void*)k_generals<true, false, 32, false>,
+                          (const void*)k_generals<false, false, 32, true>,  (const void*)k_generals<true, false, 32, true>,
+                          (const void*)k_generals<false, true, 32, false>,  (const void*)k_generals<true, true, 32, false>};
+    cudaError_t e = (cudaError_t)limit.raise(fns, 6, smem_bytes);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0, dev = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false, 32>, 32 * warps_per_cta,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false, 32, false>, 32 * warps_per_cta,
                                                            smem_bytes)) != cudaSuccess)
         return (int)e;
     cudaGetDevice(&dev);
@@ -1405,6 +1415,30 @@ int init_tables() {
     return 0;
 }
 
+// The plain-generator kernels of one lane-group width: per frame or
+// multi-frame, for uniform or per-game shapes.
+template <int LW>
+int launch_plain(const KArgs& a, bool multi, dim3 grid, dim3 block, int smem, cudaStream_t st) {
+    if (LW < 32) {  // more than 48 KB of shared memory per CTA for small games
+        static SmemLimit limit;
+        const void* fns[4] = {(const void*)k_generals<false, false, LW, false>,
+                              (const void*)k_generals<true, false, LW, false>,
+                              (const void*)k_generals<false, false, LW, true>,
+                              (const void*)k_generals<true, false, LW, true>};
+        const int e = limit.raise(fns, 4, smem);
+        if (e != 0) return e;
+    }
+    if (multi && a.uniform)
+        k_generals<true, false, LW, true><<<grid, block, smem, st>>>(a);
+    else if (multi)
+        k_generals<true, false, LW, false><<<grid, block, smem, st>>>(a);
+    else if (a.uniform)
+        k_generals<false, false, LW, true><<<grid, block, smem, st>>>(a);
+    else
+        k_generals<false, false, LW, false><<<grid, block, smem, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
 int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     if (a.n_items <= 0) return 0;
 
@@ -1424,34 +1458,16 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     // multi-frame launches: a grid of many waves, groups stride over any items beyond it
     if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
     const dim3 grid(blocks), block(32 * warps_per_cta);
-    if (per_warp == 4) {
-        static SmemLimit limit;
-        const void* fns[2] = {(const void*)k_generals<false, false, 8>, (const void*)k_generals<true, false, 8>};
-        const int e = limit.raise(fns, 2, smem);
-        if (e != 0) return e;
+    if (spawn) {  // one game per warp, shapes read per game
         if (multi)
-            k_generals<true, false, 8><<<grid, block, smem, st>>>(a);
+            k_generals<true, true, 32, false><<<grid, block, smem, st>>>(a);
         else
-            k_generals<false, false, 8><<<grid, block, smem, st>>>(a);
-    } else if (per_warp == 2) {
-        static SmemLimit limit;
-        const void* fns[2] = {(const void*)k_generals<false, false, 16>, (const void*)k_generals<true, false, 16>};
-        const int e = limit.raise(fns, 2, smem);
-        if (e != 0) return e;
-        if (multi)
-            k_generals<true, false, 16><<<grid, block, smem, st>>>(a);
-        else
-            k_generals<false, false, 16><<<grid, block, smem, st>>>(a);
-    } else if (multi && spawn) {
-        k_generals<true, true, 32><<<grid, block, smem, st>>>(a);
-    } else if (multi) {
-        k_generals<true, false, 32><<<grid, block, smem, st>>>(a);
-    } else if (spawn) {
-        k_generals<false, true, 32><<<grid, block, smem, st>>>(a);
-    } else {
-        k_generals<false, false, 32><<<grid, block, smem, st>>>(a);
+            k_generals<false, true, 32, false><<<grid, block, smem, st>>>(a);
+        return (int)cudaGetLastError();
     }
-    return (int)cudaGetLastError();
+    if (per_warp == 4) return launch_plain<8>(a, multi, grid, block, smem, st);
+    if (per_warp == 2) return launch_plain<16>(a, multi, grid, block, smem, st);
+    return launch_plain<32>(a, multi, grid, block, smem, st);
 }
 
 int launch_copy(const void* src, void* dst, size_t n16, int blocks, void* stream) {
