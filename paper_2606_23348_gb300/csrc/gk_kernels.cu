@@ -1,14 +1,16 @@
-// Device code of libgenerals: one warp advances one Generals.io game.
+// Device code of libgenerals: one group of lanes advances one Generals.io
+// game -- a warp, or for two-player games on small boards a half (two games
+// per warp) or, in multi-frame launches, a quarter of one (four per warp).
 //
-// Per game and step (paper Section IV) the warp
+// Per game and step (paper Section IV) the group
 //   1. stages the board (int16 armies, int8 owners, int8 terrain) in shared
-//      memory with 128-bit loads;
-//   2. resolves the players' moves one after another on lane 0 (Sec. IV-D,
-//      IV-E), with a warp-wide pass for the land transfer of a captured
-//      general;
-//   3. applies growth (Sec. IV-C) while __ballot_sync turns the board into
-//      32-cell bitsets (ownership per player, army >= 2) and
-//      __reduce_add_sync totals the armies;
+//      memory with cp.async 16-byte copies;
+//   2. resolves the players' moves one after another on its first lane
+//      (Sec. IV-D, IV-E), with a group-wide pass for the land transfer of a
+//      captured general;
+//   3. applies growth (Sec. IV-C) while ballots turn the board into 32-cell
+//      bitsets (ownership per player, army >= 2) and reductions total the
+//      armies;
 //   4. decides termination and reward (Sec. III) and regenerates finished
 //      games (Sec. IV-A);
 //   5. dilates the (team) ownership bitsets into fog-of-war visibility with
@@ -16,8 +18,8 @@
 //   6. expands bitsets and board bytes into 16-cell observation and mask
 //      chunks written with 128-bit streaming stores;
 //   7. optionally picks the next actions with the benchmark policy: legal
-//      (cell, direction) counts per chunk, a warp scan to find the chunk, a
-//      16-lane scan to find the cell.
+//      (cell, direction) counts per chunk, a group scan to find the chunk, a
+//      scan over its 16 cells to find the cell.
 //
 // Terrain bytes carry the cell type in bits 0-1 and, in bits 2-5, whether
 // the neighbour up / down / left / right exists and is not a mountain.  The
@@ -900,9 +902,14 @@ __device__ uint32_t chunk_pass(const Game& g, const Smem& s, bool grow_s, bool g
 
 template <int LW>
 __device__ __forceinline__ uint32_t cell_pass(const Game& g, const Smem& s, bool grow_s, bool grow_p, const Grp<LW>& t) {
-    if (g.P <= 2) return chunk_pass<2, LW>(g, s, grow_s, grow_p, t);
-    if (g.P <= 4) return chunk_pass<4, LW>(g, s, grow_s, grow_p, t);
-    return chunk_pass<8, LW>(g, s, grow_s, grow_p, t);
+    if constexpr (LW < 32) {  // groups narrower than a warp only run games of at most kPairMaxPlayers
+        static_assert(kPairMaxPlayers == 2, "narrow groups compile the two-player cell pass only");
+        return chunk_pass<2, LW>(g, s, grow_s, grow_p, t);
+    } else {
+        if (g.P <= 2) return chunk_pass<2, LW>(g, s, grow_s, grow_p, t);
+        if (g.P <= 4) return chunk_pass<4, LW>(g, s, grow_s, grow_p, t);
+        return chunk_pass<8, LW>(g, s, grow_s, grow_p, t);
+    }
 }
 
 // ---- fog: 3x3 dilation of the (team) ownership bitset (Sec. IV-B) ----------
@@ -1169,7 +1176,13 @@ namespace {
 template <bool MULTI, bool SPAWN, int LW, bool UNI>
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const int gidx,
                                          const Grp<LW>& t) {
-    const Game g = game_of<UNI>(a, gidx);
+    Game g = game_of<UNI>(a, gidx);
+    if constexpr (LW < 32) {
+        // narrow groups run only two-player games without teams: 1v1, or a
+        // two-player free-for-all, whose rules are the same
+        g.P = kPairMaxPlayers;
+        g.mode = 0;
+    }
     GameScalars* sc = a.scal + gidx;
 
     // every global load of the step is issued here, before any is used
@@ -1286,21 +1299,40 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
         if (a.op == OP_STEP) frame += 1;
 
         const bool fin = finished != 0;
+        if constexpr (MULTI) {
+            // reward and done before the output passes and the scoreboard
+            // as soon as the fog pass has counted the land: fewer values
+            // live through the passes (measured faster in multi-frame
+            // launches, slower per frame)
+            if (a.do_outputs) {
+                const int64_t soff = (int64_t)f * a.slot_stride;
+                if (t.lane < g.P) a.reward[soff + g.player_off + t.lane] = my_reward;
+                if (t.lane == 0) a.done[(int64_t)f * a.game_stride + gidx] = (uint8_t)done;
+            }
+        }
         if (a.do_outputs) {
             const int64_t poff = (int64_t)f * a.plane_stride;
             const int64_t soff = (int64_t)f * a.slot_stride;
             column_pass(g, s, t);
-            fog_pass(g, s, alive, t);
+            fog_pass(g, s, alive, t);  // counts the land
+            if constexpr (MULTI) {
+                if (t.lane < g.P) {
+                    a.scoreboard[2 * (soff + g.player_off + t.lane) + 0] = s.misc[8 + t.lane];
+                    a.scoreboard[2 * (soff + g.player_off + t.lane) + 1] = s.misc[16 + t.lane];
+                }
+            }
             if (a.next_actions)
                 output_pass<true, true, LW>(a, g, s, alive, fin, t, poff);
             else
                 output_pass<true, false, LW>(a, g, s, alive, fin, t, poff);
-            if (t.lane < g.P) {
-                a.reward[soff + g.player_off + t.lane] = my_reward;
-                a.scoreboard[2 * (soff + g.player_off + t.lane) + 0] = s.misc[8 + t.lane];
-                a.scoreboard[2 * (soff + g.player_off + t.lane) + 1] = s.misc[16 + t.lane];
+            if constexpr (!MULTI) {
+                if (t.lane < g.P) {
+                    a.reward[soff + g.player_off + t.lane] = my_reward;
+                    a.scoreboard[2 * (soff + g.player_off + t.lane) + 0] = s.misc[8 + t.lane];
+                    a.scoreboard[2 * (soff + g.player_off + t.lane) + 1] = s.misc[16 + t.lane];
+                }
+                if (t.lane == 0) a.done[(int64_t)f * a.game_stride + gidx] = (uint8_t)done;
             }
-            if (t.lane == 0) a.done[(int64_t)f * a.game_stride + gidx] = (uint8_t)done;
         } else if (a.next_actions) {
             output_pass<false, true, LW>(a, g, s, alive, fin, t, 0);
         }

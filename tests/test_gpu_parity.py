@@ -110,6 +110,21 @@ def test_no_mountains_and_all_mountains():
         rollout_policy(env, orc, 40, tag=f"mtn{thr}")
 
 
+def test_two_player_ffa_and_1v1_in_narrow_groups():
+    """Two-player free-for-all and 1v1 games step in the two-games-per-warp
+    kernels (ragged and uniform shapes) with captures, timeouts and resets."""
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    G = 40
+    H, W, mode, _ = shapes(G, (4, 24), ((0, 0.5), (2, 0.5)), seed=13)
+    P = np.full(G, 2, np.int32)
+    env, orc = pair(H, W, mode, P, seed=6, min_general_dist=1, n_cities=3, max_turns=50)
+    rollout_policy(env, orc, 120, policy_seed=3, tag="ffa2 ragged")
+    kw = dict(seed=9, min_general_dist=2, n_cities=4, max_turns=60)
+    env = GeneralsEnv(12, 12, 2, 2, batch=G, **kw)
+    orc = OracleEnv(np.full(G, 12), np.full(G, 12), np.full(G, 2), np.full(G, 2), **kw)
+    rollout_policy(env, orc, 130, policy_seed=5, tag="ffa2 uniform")
+
+
 def test_reset_subset_and_observe():
     import torch
     G = 20
