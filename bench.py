@@ -42,8 +42,8 @@ MAP_SEED = 1
 # of the same kernel with inputs larger than L2 and scaled by the games it
 # processes (traffic grows in proportion); valid only for the kernel source
 # it was taken on.
-NCU_TRAFFIC = {"kernel_sha1": "f62990500186", "bytes_per_launch": 2 * 327234048.0,
-               "warp_inst_per_launch": 2 * 58747896.0, "captured": "32,768 games (x2)", "games": 65536}
+NCU_TRAFFIC = {"kernel_sha1": "c8c074b3b410", "bytes_per_launch": 2 * 325580032.0,
+               "warp_inst_per_launch": 2 * 58977272.0, "captured": "32,768 games (x2)", "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
 SAMPLE_NCU = {"kernel_sha1": "d7499ce12f09", "bytes_per_launch": 4 * 138351104.0,
               "warp_inst_per_launch": 4 * 47394660.0, "captured": "16,384 games (x4)", "games": 65536}

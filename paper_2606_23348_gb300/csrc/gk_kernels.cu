@@ -224,7 +224,7 @@ __device__ __forceinline__ void derive_passable(const Game& g, const Smem& s, co
 // g_columns[W-1][0][w] has bit b set when cell 32w+b is in the first column
 // of a W-wide board, [1] the last column; filled once per device.
 constexpr int kColWords = (kMaxSide * kMaxSide) / 32;
-__device__ uint32_t g_columns[kMaxSide][2][kColWords];
+__device__ __align__(16) uint32_t g_columns[kMaxSide][2][kColWords];
 
 template <int LW>
 __device__ __forceinline__ void column_pass(const Game& g, const Smem& s, const Grp<LW>& t) {
@@ -1131,6 +1131,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
                  "l"(gmem)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
 template <int LW>
 __device__ __forceinline__ void board_issue(const KArgs& a, const Game& g, const Smem& s, const Grp<LW>& t) {
     const int n16 = g.Npad >> 4;  // 16-byte vectors per int8 plane
@@ -1144,6 +1149,17 @@ __device__ __forceinline__ void board_issue(const KArgs& a, const Game& g, const
     for (int v = t.lane; v < n16; v += LW) {
         cp_async16(so + v, go + v);
         cp_async16(st + v, gt + v);
+    }
+    if (a.do_outputs) {
+        // the board's first- and last-column bitsets for the fog pass, in
+        // the same group of copies (8-byte pairs of words: both regions and
+        // both table rows are 8-byte aligned, the region holds an even count)
+        const uint32_t* c0 = g_columns[g.W - 1][0];
+        const uint32_t* cl = g_columns[g.W - 1][1];
+        for (int v = t.lane; 2 * v < g.nw; v += LW) {
+            cp_async8(s.col0 + 2 * v, c0 + 2 * v);
+            cp_async8(s.colL + 2 * v, cl + 2 * v);
+        }
     }
 }
 template <int LW>
@@ -1313,7 +1329,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
         if (a.do_outputs) {
             const int64_t poff = (int64_t)f * a.plane_stride;
             const int64_t soff = (int64_t)f * a.slot_stride;
-            column_pass(g, s, t);
+            if (!board) column_pass(g, s, t);  // else copied with the board
             fog_pass(g, s, alive, t);  // counts the land
             if constexpr (MULTI) {
                 if (t.lane < g.P) {
