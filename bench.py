@@ -745,6 +745,23 @@ def run_selfplay(args, rank, world, local):
             e1.record(stream)
         torch.cuda.synchronize()
     res["graph"] = e0.elapsed_time(e1)
+
+    def per_frame_ms(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0.record(stream)
+            for _ in range(T):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / T
+
+    # where a plain frame's time goes: the sampler and the step alone (after
+    # the timed runs), the feature build as the rest
+    parts = {"sample": per_frame_ms(lambda: env.sample_actions(logits, POLICY_SEED, acts)),
+             "step": per_frame_ms(lambda: env.step(acts, out))}
+    parts["features (rest of a plain frame)"] = res["plain"] / T - parts["sample"] - parts["step"]
     best = min(res, key=res.get)
     value = sum_over_ranks(float(G * T), world) / (max_over_ranks(res[best], world) * 1e-3)
     if rank == 0:
@@ -757,7 +774,64 @@ def run_selfplay(args, rank, world, local):
             "config": {"workload": "selfplay-512x512", "games_per_gpu": G, "frames": T, "hist": 7,
                        "temporal_window": 512, "l2": "fits in L2 (small batch; latency-bound)"},
             "forms": {k: {"ms_per_frame": v / T, "frames_per_s": G * T / (v * 1e-3)} for k, v in res.items()},
+            "ms_per_frame_by_kernel": parts,
             "gpu_launches": 3 * T, "clocks": clk.summary()}), flush=True)
+
+
+def run_batch_sweep(args, rank, world, local):
+    """Frames/s of the default game shape (1v1, 24x24) at the environment
+    counts of the paper's throughput table (Sec. V: 1,024 to 32,768 parallel
+    environments) and at 65,536: one step + policy launch per frame, the same
+    frames as a CUDA graph, and one resident multi-frame launch."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import shard, workload
+
+    torch.cuda.set_device(local)
+    K = args.rollout
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    with ClockSampler(local) as clk:
+        for G in (1024, 2048, 4096, 8192, 16384, 32768, 65536):
+            H, W, mode, P, gen, _ = workload(WORKLOAD, G=G)
+            env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
+            acts, out1 = env.new_actions(), env.new_outputs()
+            env.policy(POLICY_SEED, acts)
+            for _ in range(args.warmup):
+                env.step_policy(acts, out1, POLICY_SEED, acts)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(K):
+                env.step_policy(acts, out1, POLICY_SEED, acts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row = {"envs": G, "plain": G * K / (e0.elapsed_time(e1) * 1e-3)}
+            del out1
+            outK = env.new_outputs(frames=K)
+            for name, form in (("graph", 1), ("resident", 0)):
+                for _ in range(2):
+                    env.rollout(K, POLICY_SEED, acts, outK, None, form)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                env.rollout(K, POLICY_SEED, acts, outK, None, form)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[name] = G * K / (e0.elapsed_time(e1) * 1e-3)
+            rows.append({k: (v if k == "envs" else sum_over_ranks(v, world)) for k, v in row.items()})
+            del env, outK
+    best = max(rows, key=lambda r: max(r["plain"], r["graph"], r["resident"]))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "frames/s by environment count (step + policy, 1v1 24x24)",
+            "value": max(best["plain"], best["graph"], best["resident"]), "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int16",
+            "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
+            "config": {"workload": "sweep-1024to65536x24x24", "frames_per_form": K,
+                       "l2": "small batches fit in L2 (latency-bound); the largest exceed it"},
+            "rows": rows, "gpu_launches": None, "clocks": clk.summary()}), flush=True)
 
 
 def run_generator(args, rank, world, local):
@@ -847,6 +921,8 @@ def main():
             run_sampling(args, rank, world, local)
         elif args.workload == "selfplay-512x512":
             run_selfplay(args, rank, world, local)
+        elif args.workload == "sweep-1024to65536x24x24":
+            run_batch_sweep(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

@@ -350,6 +350,12 @@ int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_serv
 int gen_sample_actions(gen_env *env, const float *d_logits, uint64_t seed, int32_t *d_actions, uint8_t *d_mask9,
                        void *stream);
 
+/* How gen_sample_actions spreads a game over the GPU (the results are the
+ * same): 1 = one warp per game, players in turn; 2 = one CTA per game with a
+ * warp per player (as many as fit in shared memory beside the board);
+ * 0 (default) = 2.  GEN_ERR_BAD_ARG for NULL env or a form outside 0..2. */
+int gen_set_sample_form(gen_env *env, int form);
+
 /* ---- feature tensor (App. A, table of observation channels) -------------
  * Per player C = 24 + 2 * hist float32 planes of Npad_g cells each, in the
  * table's order: 0 armies, 1 own army, 2 enemy army, 3 neutral army,
@@ -404,6 +410,13 @@ int gen_features_build(gen_features *f, float *d_out, void *stream);
  * first), 0 before the episode.  GEN_ERR_BAD_ARG when d_series is given to a
  * builder created without a window. */
 int gen_features_build_ex(gen_features *f, float *d_out, int32_t *d_series, void *stream);
+
+/* How the builder spreads a game over the GPU (the bytes written are the
+ * same): 1 = one warp per game, players in turn; 2 = one CTA per game, its
+ * warps sharing the (player, 128-cell chunk) items, for batches too small to
+ * fill the GPU one warp per game; 0 (default) = 2 while the batch has fewer
+ * games than 16 x the SM count, else 1.  GEN_ERR_BAD_ARG outside 0..2. */
+int gen_features_set_form(gen_features *f, int form);
 
 void gen_features_destroy(gen_features *f);
 

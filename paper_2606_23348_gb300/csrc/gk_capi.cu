@@ -75,6 +75,7 @@ struct gen_env {
     int player_slots = 0;
     int pmax = 0;
     int npad_max = 0;
+    int sample_form = 0;  // gen_sample_actions: 0 by batch size, 1 warp per game, 2 CTA per game
     int nmax = 0;
     bool uniform = false;            // every game has the same board size and mode
     Bucket all;                      // every game, largest carve (used for game-id lists)
@@ -886,6 +887,7 @@ struct gen_features {
     gen_env* env = nullptr;
     int hist = 0;
     int window = 0;
+    int form = 0;  // 0 by batch size, 1 one warp per game, 2 one CTA per game
     void* d_mem = nullptr;  // one allocation: headers, masks, last army, last turn, ring
     gk::FArgs args{};
 };
@@ -970,8 +972,15 @@ int gen_features_build_ex(gen_features* f, float* d_out, int32_t* d_series, void
     gk::FArgs a = f->args;
     a.out = d_out;
     a.series_out = reinterpret_cast<int2*>(d_series);
-    const int rc = gk::launch_features(a, stream);
+    const int rc = gk::launch_features(a, f->env->pmax, f->form, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, "feature launch");
+    return GEN_OK;
+}
+
+int gen_features_set_form(gen_features* f, int form) {
+    if (!f) return fail(GEN_ERR_BAD_ARG, "features is NULL");
+    if (form < 0 || form > 2) return fail(GEN_ERR_BAD_ARG, "form %d outside [0, 2]", form);
+    f->form = form;
     return GEN_OK;
 }
 
@@ -1001,8 +1010,15 @@ int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t
     a.actions = d_actions;
     a.mask9 = d_mask9;
     a.npad_max = e->npad_max;
-    const int rc = gk::launch_sample(a, stream);
+    const int rc = gk::launch_sample(a, e->pmax, e->sample_form, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, "sampler launch");
+    return GEN_OK;
+}
+
+int gen_set_sample_form(gen_env* e, int form) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (form < 0 || form > 2) return fail(GEN_ERR_BAD_ARG, "form %d outside [0, 2]", form);
+    e->sample_form = form;
     return GEN_OK;
 }
 

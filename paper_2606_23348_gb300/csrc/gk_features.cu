@@ -14,14 +14,20 @@
 // 0 when visible or never seen; coordinates col / (W - 1), row / (H - 1);
 // frames before the episode count as zero planes.
 //
-// One warp per game: the board is staged in shared memory once, then each
-// player in turn gets a visibility bitset (3x3 dilation of its team's cells)
-// and a pass over the cells, four consecutive cells per lane, that reads the
-// memory, writes the 24 + 2K channels with 16-byte streaming stores and
-// writes the folded memory back.  HBM-bound: per player and cell it moves
-// 4 (24 + 2K) bytes of output, 2 * 2K bytes of history and 15 bytes of memory.
+// Two forms of the same computation.  k_features: one warp per game -- the
+// board is staged in shared memory once, then each player in turn gets a
+// visibility bitset (3x3 dilation of its team's cells) and a pass over the
+// cells, four consecutive cells per lane, that reads the memory, writes the
+// 24 + 2K channels with 16-byte streaming stores and writes the folded memory
+// back.  k_features_cta, for batches too small to fill the GPU one warp per
+// game: one CTA per game, warp q builds player q's bitset, then the warps
+// share the (player, 128-cell chunk) items; every warp reads the players'
+// memory headers before a CTA barrier, after which they are written.
+// HBM-bound: per player and cell it moves 4 (24 + 2K) bytes of output,
+// 2 * 2K bytes of history and 15 bytes of memory.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "gk_internal.h"
@@ -125,6 +131,245 @@ __device__ __forceinline__ void st4d(float* p, uint2 a, uint2 b) {
 __device__ __noinline__ float age_log(int dt) { return (float)(log(1.0 + (double)dt) / 5.0); }
 __device__ __forceinline__ float age_value(int dt) { return dt > 0 ? age_log(dt) : 0.0f; }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+// land and army of player q on the board, by one warp
+__device__ __forceinline__ void score_of(const int16_t* s_army, const int8_t* s_owner, int N, int q, int32_t* s_score,
+                                         int lane) {
+    int land = 0, army = 0;
+    for (int c = lane; c < N; c += 32)
+        if (s_owner[c] == q) {
+            land += 1;
+            army += s_army[c];
+        }
+    land = (int)__reduce_add_sync(kAll, (unsigned)land);
+    army = (int)__reduce_add_sync(kAll, (unsigned)army);
+    if (lane == 0) {
+        s_score[q] = land;
+        s_score[8 + q] = army;
+    }
+}
+
+// player p's visibility bitset (Sec. IV-B): the 3x3 dilation of its team's
+// cells, by one warp, through the scratch bitset s_team
+__device__ __forceinline__ void vis_of(const int8_t* s_owner, uint32_t* s_team, uint32_t* s_vis, int N, int W, int nw,
+                                       int mode, int tp, bool alive, int lane) {
+    for (int w = 0; w < nw; ++w) {
+        const int c = 32 * w + lane;
+        const int o = c < N ? s_owner[c] : -1;
+        const bool mine = alive && o >= 0 && (mode == 1 ? (o >> 1) : o) == tp;
+        const unsigned b = __ballot_sync(kAll, mine);
+        if (lane == 0) s_team[w] = b;
+    }
+    __syncwarp();
+    for (int w = lane; w < nw; w += 32) {
+        const uint32_t x = s_team[w];
+        const uint32_t left = shifted(s_team, nw, w, 1) & ~column_word(w, W, 0);       // from c - 1
+        const uint32_t right = shifted(s_team, nw, w, -1) & ~column_word(w, W, W - 1); // from c + 1
+        s_vis[w] = x | left | right;
+    }
+    __syncwarp();
+    uint32_t vis_w[4];
+    for (int i = 0; i < 4; ++i) {
+        const int w = lane + 32 * i;
+        vis_w[i] = 0u;
+        if (w < nw) vis_w[i] = (s_vis[w] | shifted(s_vis, nw, w, W) | shifted(s_vis, nw, w, -W)) & valid_word(N, w);
+    }
+    __syncwarp();
+    for (int i = 0; i < 4; ++i) {
+        const int w = lane + 32 * i;
+        if (w < nw) s_vis[w] = vis_w[i];
+    }
+    __syncwarp();
+}
+
+// one player's frame: its scalars and memory-header state
+struct PlayerFrame {
+    int p, tp, slot;
+    int opp_land, opp_army;
+    float f_own_land, f_own_army, f_opp_land, f_opp_army;
+    bool cleared, fold;
+    uint32_t n_fold;  // frames folded this episode, this one included
+    int head;         // ring slot of this frame
+    int nvalid;       // ring slots holding frames of this episode
+};
+
+__device__ __forceinline__ PlayerFrame player_frame(const FArgs& f, const GameInfo& gi, const GameScalars& sc,
+                                                    const int32_t* s_score, int p, int R) {
+    PlayerFrame x;
+    x.p = p;
+    x.tp = gi.mode == 1 ? (p >> 1) : p;
+    x.slot = gi.player_off + p;
+    // scalars of this player (Q30)
+    int opp_land = 0, opp_army = 0;
+    for (int q = 0; q < gi.P; ++q)
+        if ((gi.mode == 1 ? (q >> 1) : q) != x.tp) {
+            opp_land += s_score[q];
+            opp_army += s_score[8 + q];
+        }
+    x.opp_land = opp_land;
+    x.opp_army = opp_army;
+    x.f_own_land = (float)s_score[p];
+    x.f_own_army = (float)s_score[8 + p];
+    x.f_opp_land = (float)opp_land;
+    x.f_opp_army = (float)opp_army;
+    // memory header: clear on a new epoch, fold once per frame
+    const uint4 h = f.hdr[x.slot];
+    x.cleared = h.x != sc.epoch + 1u;
+    x.fold = x.cleared || h.y != sc.frame;
+    x.n_fold = (x.cleared ? 0u : h.z) + (x.fold ? 1u : 0u);
+    x.head = (int)((x.n_fold - 1u) % (uint32_t)R);
+    x.nvalid = (int)min(x.n_fold, (uint32_t)R);
+    return x;
+}
+
+// temporal tokens (App. A) of one player: the ring entry of this frame
+// (once), and entries k0, k0 + dk, ... of the newest-first copy
+__device__ __forceinline__ void player_tokens(const FArgs& f, const PlayerFrame& x, bool write_ring, uint32_t k0,
+                                              uint32_t dk) {
+    const uint32_t T = (uint32_t)f.window;
+    int2* ring = f.series_ring + (int64_t)x.slot * T;
+    if (write_ring && x.fold) ring[(x.n_fold - 1u) % T] = make_int2(x.opp_army, x.opp_land);
+    if (f.series_out) {
+        int2* so = f.series_out + (int64_t)x.slot * T;
+        const uint32_t valid = min(x.n_fold, T);
+        for (uint32_t k = k0; k < T; k += dk) {
+            int2 v = make_int2(0, 0);
+            if (k == 0)
+                v = make_int2(x.opp_army, x.opp_land);
+            else if (k < valid)
+                v = ring[(x.n_fold - 1u - k) % T];
+            so[k] = v;
+        }
+    }
+}
+
+// cells c .. c+3 of one player: read and fold the memory, write the 24 + 2K rows
+__device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, const PlayerFrame& x, int turn,
+                                          float f_turn, float f_phase, const int16_t* s_army, const int8_t* s_owner,
+                                          const int8_t* s_terrain, const uint32_t* s_vis, int c) {
+    const int H = gi.H, W = gi.W, N = gi.N, Npad = gi.Npad, mode = gi.mode, p = x.p, tp = x.tp;
+    const int C = 24 + 2 * f.hist, K = f.hist, R = f.hist + 1;
+    const int64_t q0 = gi.plane_off + (int64_t)p * Npad;  // this player's plane
+    float* out = f.out + q0 * C;
+    const int64_t pc = q0 + c;
+    // memory of cells c..c+3 (loads first)
+    uint32_t mb = 0u;
+    uint2 lea = make_uint2(0u, 0u);
+    int4 let = make_int4(0, 0, 0, 0);
+    if (!x.cleared) {
+        mb = __ldcs(reinterpret_cast<const unsigned int*>(f.mem_bits + pc));
+        lea = __ldcs(reinterpret_cast<const uint2*>(f.mem_army + pc));
+        let = __ldcs(reinterpret_cast<const int4*>(f.mem_turn + pc));
+    }
+    // board of cells c..c+3
+    const uint2 a2 = *reinterpret_cast<const uint2*>(s_army + c);
+    const uint32_t ow = *reinterpret_cast<const uint32_t*>(s_owner + c);
+    const uint32_t tw = *reinterpret_cast<const uint32_t*>(s_terrain + c);
+    const uint32_t vbits = (s_vis[c >> 5] >> (c & 31)) & 0xFu;
+    // one flag byte per cell (kF*) and the folded memory masks
+    uint32_t fl = 0u;
+    int lt[4] = {let.x, let.y, let.z, let.w};
+    float age[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool in = c + i < N;
+        const int o = (int)(int8_t)(ow >> (8 * i));
+        const uint32_t t = (tw >> (8 * i)) & 0x3u;
+        const bool v = in && ((vbits >> i) & 1u);
+        const bool opp = in && o >= 0 && (mode == 1 ? (o >> 1) : o) != tp;
+        uint32_t m = (mb >> (8 * i)) & 0x1Fu;
+        const bool seen_old = m & 1u;
+        if (v) {
+            m |= 1u;
+            if (opp) {
+                m |= 2u;
+                lt[i] = turn;
+            }
+            m |= t == 3u ? 4u : t == 2u ? 8u : t == 1u ? 16u : 0u;
+        }
+        mb = (mb & ~(0xFFu << (8 * i))) | (m << (8 * i));
+        age[i] = age_value((!v && (m & 2u)) ? turn - lt[i] : 0);
+        uint32_t b = in ? kFIn : 0u;
+        if (v) b |= kFVis;
+        if (in && o == p) b |= kFOwn;
+        if (v && opp) b |= kFOpp;
+        if (v && o == -1) b |= kFUnowned;
+        if (v && o == -1 && t != 1u) b |= kFNeutral;
+        if (in && !v && (t == 1u || t == 2u || (m & 4u))) b |= kFFogStruct;
+        if (!v && seen_old) b |= kFKeep;
+        fl |= b << (8 * i);
+    }
+    const uint2 own = select16(a2, fl, kFOwn);
+    const uint2 ene = select16(a2, fl, kFOpp);
+    const uint2 lea_n = or2(ene, select16(lea, fl, kFKeep));  // Q31
+    if (x.fold) {
+        *reinterpret_cast<uint32_t*>(f.mem_bits + pc) = mb;
+        *reinterpret_cast<uint2*>(f.mem_army + pc) = lea_n;
+        *reinterpret_cast<int4*>(f.mem_turn + pc) = make_int4(lt[0], lt[1], lt[2], lt[3]);
+        *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * x.head) * f.plane_cells + pc) = own;
+        *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * x.head + 1) * f.plane_cells + pc) = ene;
+    }
+    float* row = out + c;
+    st4i(row, select16(a2, fl, kFVis));
+    st4i(row += Npad, own);
+    st4i(row += Npad, ene);
+    st4i(row += Npad, select16(a2, fl, kFUnowned));
+    st4b(row += Npad, mb, 1u);
+    st4b(row += Npad, mb, 2u);
+    st4b(row += Npad, mb, 4u);
+    st4b(row += Npad, mb, 8u);
+    st4b(row += Npad, mb, 16u);
+    st4b(row += Npad, fl, kFNeutral);
+    st4b(row += Npad, fl, kFOwn);
+    st4b(row += Npad, fl, kFOpp);
+    st4b(row += Npad, fl & ~(fl >> 1), kFIn);  // on the board and not visible
+    st4b(row += Npad, fl, kFFogStruct);
+    st4s(row += Npad, fl, f_turn);
+    st4s(row += Npad, fl, f_phase);
+    st4s(row += Npad, fl, x.f_own_land);
+    st4s(row += Npad, fl, x.f_own_army);
+    st4s(row += Npad, fl, x.f_opp_land);
+    st4s(row += Npad, fl, x.f_opp_army);
+    st4i(row += Npad, lea_n);
+    st4(row += Npad, age[0], age[1], age[2], age[3]);
+    {  // coordinates (Q32)
+        float cx[4], cy[4];
+        int r = c / W, col = c - r * W;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool in = (fl >> (8 * i)) & kFIn;
+            cx[i] = in && W > 1 ? (float)col / (float)(W - 1) : 0.0f;
+            cy[i] = in && H > 1 ? (float)r / (float)(H - 1) : 0.0f;
+            if (++col == W) {
+                col = 0;
+                ++r;
+            }
+        }
+        st4(row += Npad, cx[0], cx[1], cx[2], cx[3]);
+        st4(row += Npad, cy[0], cy[1], cy[2], cy[3]);
+    }
+    // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back
+    uint2 po = own, pe = ene;
+    float* rd = row + (int64_t)Npad;
+    for (int k = 0; k < K; ++k, rd += Npad) {
+        uint2 no = make_uint2(0u, 0u), ne = make_uint2(0u, 0u);
+        if (k + 1 < x.nvalid) {
+            const int sl = (x.head - (k + 1) + R) % R;
+            no = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
+            ne = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
+        }
+        st4d(rd, po, no);
+        st4d(rd + (int64_t)K * Npad, pe, ne);
+        po = no;
+        pe = ne;
+    }
+}
+
 __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -141,10 +386,10 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     int32_t* s_score = reinterpret_cast<int32_t*>(s_vis + nw_max);  // land[8], army[8]
 
     const GameInfo gi = f.info[gidx];
-    const int H = gi.H, W = gi.W, N = gi.N, Npad = gi.Npad, P = gi.P, mode = gi.mode;
+    const int N = gi.N, Npad = gi.Npad, P = gi.P;
     const int nw = (Npad + 31) >> 5;
     const GameScalars sc = f.scal[gidx];
-    const int C = 24 + 2 * f.hist, K = f.hist, R = f.hist + 1;
+    const int R = f.hist + 1;
 
     // board to shared memory, 16 bytes per lane and copy
     {
@@ -161,20 +406,7 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     __syncwarp();
 
     // public scoreboard (Sec. IV-B): land and army per player
-    for (int q = 0; q < P; ++q) {
-        int land = 0, army = 0;
-        for (int c = lane; c < N; c += 32)
-            if (s_owner[c] == q) {
-                land += 1;
-                army += s_army[c];
-            }
-        land = (int)__reduce_add_sync(kAll, (unsigned)land);
-        army = (int)__reduce_add_sync(kAll, (unsigned)army);
-        if (lane == 0) {
-            s_score[q] = land;
-            s_score[8 + q] = army;
-        }
-    }
+    for (int q = 0; q < P; ++q) score_of(s_army, s_owner, N, q, s_score, lane);
     __syncwarp();
 
     const int turn = (int)sc.turn;
@@ -182,201 +414,110 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     const float f_phase = (float)(turn % 50) / 50.0f;
 
     for (int p = 0; p < P; ++p) {
-        const int tp = mode == 1 ? (p >> 1) : p;
-        const bool alive = (sc.alive >> p) & 1u;
-        // team cells, then their 3x3 dilation (Sec. IV-B)
-        for (int w = 0; w < nw; ++w) {
-            const int c = 32 * w + lane;
-            const int o = c < N ? s_owner[c] : -1;
-            const bool mine = alive && o >= 0 && (mode == 1 ? (o >> 1) : o) == tp;
-            const unsigned b = __ballot_sync(kAll, mine);
-            if (lane == 0) s_team[w] = b;
-        }
+        const int tp = gi.mode == 1 ? (p >> 1) : p;
+        vis_of(s_owner, s_team, s_vis, N, gi.W, nw, gi.mode, tp, (sc.alive >> p) & 1u, lane);
+        const PlayerFrame x = player_frame(f, gi, sc, s_score, p, R);
+        if (f.window > 0) player_tokens(f, x, lane == 0, (uint32_t)lane, 32u);
+        for (int c = 4 * lane; c < Npad; c += 128)
+            cell_quad(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis, c);
+        if (x.fold && lane == 0) f.hdr[x.slot] = make_uint4(sc.epoch + 1u, sc.frame, x.n_fold, 0u);
         __syncwarp();
-        for (int w = lane; w < nw; w += 32) {
-            const uint32_t x = s_team[w];
-            const uint32_t left = shifted(s_team, nw, w, 1) & ~column_word(w, W, 0);       // from c - 1
-            const uint32_t right = shifted(s_team, nw, w, -1) & ~column_word(w, W, W - 1); // from c + 1
-            s_vis[w] = x | left | right;
-        }
-        __syncwarp();
-        uint32_t vis_w[4];
-        for (int i = 0; i < 4; ++i) {
-            const int w = lane + 32 * i;
-            vis_w[i] = 0u;
-            if (w < nw)
-                vis_w[i] = (s_vis[w] | shifted(s_vis, nw, w, W) | shifted(s_vis, nw, w, -W)) & valid_word(N, w);
-        }
-        __syncwarp();
-        for (int i = 0; i < 4; ++i) {
-            const int w = lane + 32 * i;
-            if (w < nw) s_vis[w] = vis_w[i];
-        }
-        __syncwarp();
+    }
+}
 
-        // scalars of this player (Q30)
-        int opp_land = 0, opp_army = 0;
-        for (int q = 0; q < P; ++q)
-            if ((mode == 1 ? (q >> 1) : q) != tp) {
-                opp_land += s_score[q];
-                opp_army += s_score[8 + q];
-            }
-        const float f_own_land = (float)s_score[p], f_own_army = (float)s_score[8 + p];
-        const float f_opp_land = (float)opp_land, f_opp_army = (float)opp_army;
+// shared memory of the one-game CTA: board, a scratch and a visibility
+// bitset per player, scoreboard; a multiple of 16 bytes
+__host__ __device__ __forceinline__ int cta_bytes(int npad_max, int pmax) {
+    const int nw_max = (npad_max + 31) >> 5;
+    return (4 * npad_max + 8 * nw_max * pmax + 64 + 15) & ~15;
+}
 
-        // memory header: clear on a new epoch, fold once per frame
-        const int slot = gi.player_off + p;
-        const uint4 h = f.hdr[slot];
+__global__ void __launch_bounds__(1024) k_features_cta(const FArgs f, int pmax) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int gidx = blockIdx.x;  // the grid is one CTA per game
+
+    const int nw_max = (f.npad_max + 31) >> 5;
+    int16_t* s_army = reinterpret_cast<int16_t*>(smem);
+    int8_t* s_owner = reinterpret_cast<int8_t*>(smem + 2 * f.npad_max);
+    int8_t* s_terrain = reinterpret_cast<int8_t*>(smem + 3 * f.npad_max);
+    uint32_t* s_vis = reinterpret_cast<uint32_t*>(smem + 4 * f.npad_max);  // [pmax][nw_max]
+    uint32_t* s_team = s_vis + pmax * nw_max;                               // [pmax][nw_max] scratch
+    int32_t* s_score = reinterpret_cast<int32_t*>(s_team + pmax * nw_max);  // land[8], army[8]
+
+    const GameInfo gi = f.info[gidx];
+    const int N = gi.N, Npad = gi.Npad, P = gi.P;
+    const int nw = (Npad + 31) >> 5;
+    const GameScalars sc = f.scal[gidx];
+    const int R = f.hist + 1;
+    {  // board to shared memory, every 16-byte copy in flight at once
+        const uint4* ga = reinterpret_cast<const uint4*>(f.army + gi.cell_off);
+        const uint4* go = reinterpret_cast<const uint4*>(f.owner + gi.cell_off);
+        const uint4* gt = reinterpret_cast<const uint4*>(f.terrain + gi.cell_off);
+        const int n16 = Npad >> 4;
+        for (int v = threadIdx.x; v < 2 * n16; v += blockDim.x) cp_async16(reinterpret_cast<uint4*>(s_army) + v, ga + v);
+        for (int v = threadIdx.x; v < n16; v += blockDim.x) {
+            cp_async16(reinterpret_cast<uint4*>(s_owner) + v, go + v);
+            cp_async16(reinterpret_cast<uint4*>(s_terrain) + v, gt + v);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    // scoreboard and visibility (Sec. IV-B): warp q takes player q
+    for (int q = wid; q < P; q += nwarps) {
+        score_of(s_army, s_owner, N, q, s_score, lane);
+        const int tq = gi.mode == 1 ? (q >> 1) : q;
+        vis_of(s_owner, s_team + q * nw_max, s_vis + q * nw_max, N, gi.W, nw, gi.mode, tq, (sc.alive >> q) & 1u, lane);
+    }
+    __syncthreads();
+
+    const int turn = (int)sc.turn;
+    const float f_turn = (float)turn;
+    const float f_phase = (float)(turn % 50) / 50.0f;
+    const int chunks = (Npad + 127) >> 7;  // 128 cells: four per lane
+    uint4 my_hdr = make_uint4(0u, 0u, 0u, 0u);
+    if ((int)threadIdx.x < P) my_hdr = f.hdr[gi.player_off + threadIdx.x];  // read before the barrier below
+    for (int item = wid; item < P * chunks; item += nwarps) {
+        const int p = item / chunks, k = item - p * chunks;
+        const PlayerFrame x = player_frame(f, gi, sc, s_score, p, R);
+        // the player's tokens are shared by its chunk items
+        if (f.window > 0) {
+            const int per = min(chunks, nwarps);
+            if (k < per) player_tokens(f, x, k == 0 && lane == 0, (uint32_t)(32 * k + lane), (uint32_t)(32 * per));
+        }
+        const int c = 128 * k + 4 * lane;
+        if (c < Npad) cell_quad(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis + p * nw_max, c);
+    }
+    __syncthreads();  // every warp has read the headers
+    if ((int)threadIdx.x < P) {
+        const uint4 h = my_hdr;
         const bool cleared = h.x != sc.epoch + 1u;
         const bool fold = cleared || h.y != sc.frame;
-        const uint32_t n_fold = (cleared ? 0u : h.z) + (fold ? 1u : 0u);  // frames folded this episode
-        const int head = (int)((n_fold - 1u) % (uint32_t)R);             // ring slot of this frame
-        const int nvalid = (int)min(n_fold, (uint32_t)R);
-
-        // temporal tokens (App. A): opponents' army and land, newest first
-        if (f.window > 0) {
-            const uint32_t T = (uint32_t)f.window;
-            int2* ring = f.series_ring + (int64_t)slot * T;
-            if (fold && lane == 0) ring[(n_fold - 1u) % T] = make_int2(opp_army, opp_land);
-            if (f.series_out) {
-                int2* so = f.series_out + (int64_t)slot * T;
-                const uint32_t valid = min(n_fold, T);
-                for (uint32_t k = lane; k < T; k += 32) {
-                    int2 v = make_int2(0, 0);
-                    if (k == 0)
-                        v = make_int2(opp_army, opp_land);
-                    else if (k < valid)
-                        v = ring[(n_fold - 1u - k) % T];
-                    so[k] = v;
-                }
-            }
-        }
-
-        const int64_t q0 = gi.plane_off + (int64_t)p * Npad;  // this player's plane
-        float* out = f.out + q0 * C;
-        for (int c = 4 * lane; c < Npad; c += 128) {
-            const int64_t pc = q0 + c;
-            // memory of cells c..c+3 (loads first)
-            uint32_t mb = 0u;
-            uint2 lea = make_uint2(0u, 0u);
-            int4 let = make_int4(0, 0, 0, 0);
-            if (!cleared) {
-                mb = __ldcs(reinterpret_cast<const unsigned int*>(f.mem_bits + pc));
-                lea = __ldcs(reinterpret_cast<const uint2*>(f.mem_army + pc));
-                let = __ldcs(reinterpret_cast<const int4*>(f.mem_turn + pc));
-            }
-            // board of cells c..c+3
-            const uint2 a2 = *reinterpret_cast<const uint2*>(s_army + c);
-            const uint32_t ow = *reinterpret_cast<const uint32_t*>(s_owner + c);
-            const uint32_t tw = *reinterpret_cast<const uint32_t*>(s_terrain + c);
-            const uint32_t vbits = (s_vis[c >> 5] >> (c & 31)) & 0xFu;
-            // one flag byte per cell (kF*) and the folded memory masks
-            uint32_t fl = 0u;
-            int lt[4] = {let.x, let.y, let.z, let.w};
-            float age[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const bool in = c + i < N;
-                const int o = (int)(int8_t)(ow >> (8 * i));
-                const uint32_t t = (tw >> (8 * i)) & 0x3u;
-                const bool v = in && ((vbits >> i) & 1u);
-                const bool opp = in && o >= 0 && (mode == 1 ? (o >> 1) : o) != tp;
-                uint32_t m = (mb >> (8 * i)) & 0x1Fu;
-                const bool seen_old = m & 1u;
-                if (v) {
-                    m |= 1u;
-                    if (opp) {
-                        m |= 2u;
-                        lt[i] = turn;
-                    }
-                    m |= t == 3u ? 4u : t == 2u ? 8u : t == 1u ? 16u : 0u;
-                }
-                mb = (mb & ~(0xFFu << (8 * i))) | (m << (8 * i));
-                age[i] = age_value((!v && (m & 2u)) ? turn - lt[i] : 0);
-                uint32_t b = in ? kFIn : 0u;
-                if (v) b |= kFVis;
-                if (in && o == p) b |= kFOwn;
-                if (v && opp) b |= kFOpp;
-                if (v && o == -1) b |= kFUnowned;
-                if (v && o == -1 && t != 1u) b |= kFNeutral;
-                if (in && !v && (t == 1u || t == 2u || (m & 4u))) b |= kFFogStruct;
-                if (!v && seen_old) b |= kFKeep;
-                fl |= b << (8 * i);
-            }
-            const uint2 own = select16(a2, fl, kFOwn);
-            const uint2 ene = select16(a2, fl, kFOpp);
-            const uint2 lea_n = or2(ene, select16(lea, fl, kFKeep));  // Q31
-            if (fold) {
-                *reinterpret_cast<uint32_t*>(f.mem_bits + pc) = mb;
-                *reinterpret_cast<uint2*>(f.mem_army + pc) = lea_n;
-                *reinterpret_cast<int4*>(f.mem_turn + pc) = make_int4(lt[0], lt[1], lt[2], lt[3]);
-                *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * head) * f.plane_cells + pc) = own;
-                *reinterpret_cast<uint2*>(f.ring + (int64_t)(2 * head + 1) * f.plane_cells + pc) = ene;
-            }
-            float* row = out + c;
-            st4i(row, select16(a2, fl, kFVis));
-            st4i(row += Npad, own);
-            st4i(row += Npad, ene);
-            st4i(row += Npad, select16(a2, fl, kFUnowned));
-            st4b(row += Npad, mb, 1u);
-            st4b(row += Npad, mb, 2u);
-            st4b(row += Npad, mb, 4u);
-            st4b(row += Npad, mb, 8u);
-            st4b(row += Npad, mb, 16u);
-            st4b(row += Npad, fl, kFNeutral);
-            st4b(row += Npad, fl, kFOwn);
-            st4b(row += Npad, fl, kFOpp);
-            st4b(row += Npad, fl & ~(fl >> 1), kFIn);  // on the board and not visible
-            st4b(row += Npad, fl, kFFogStruct);
-            st4s(row += Npad, fl, f_turn);
-            st4s(row += Npad, fl, f_phase);
-            st4s(row += Npad, fl, f_own_land);
-            st4s(row += Npad, fl, f_own_army);
-            st4s(row += Npad, fl, f_opp_land);
-            st4s(row += Npad, fl, f_opp_army);
-            st4i(row += Npad, lea_n);
-            st4(row += Npad, age[0], age[1], age[2], age[3]);
-            {  // coordinates (Q32)
-                float cx[4], cy[4];
-                int r = c / W, col = c - r * W;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const bool in = (fl >> (8 * i)) & kFIn;
-                    cx[i] = in && W > 1 ? (float)col / (float)(W - 1) : 0.0f;
-                    cy[i] = in && H > 1 ? (float)r / (float)(H - 1) : 0.0f;
-                    if (++col == W) {
-                        col = 0;
-                        ++r;
-                    }
-                }
-                st4(row += Npad, cx[0], cx[1], cx[2], cx[3]);
-                st4(row += Npad, cy[0], cy[1], cy[2], cy[3]);
-            }
-            // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back
-            uint2 po = own, pe = ene;
-            float* rd = row + (int64_t)Npad;
-            for (int k = 0; k < K; ++k, rd += Npad) {
-                uint2 no = make_uint2(0u, 0u), ne = make_uint2(0u, 0u);
-                if (k + 1 < nvalid) {
-                    const int sl = (head - (k + 1) + R) % R;
-                    no = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
-                    ne = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
-                }
-                st4d(rd, po, no);
-                st4d(rd + (int64_t)K * Npad, pe, ne);
-                po = no;
-                pe = ne;
-            }
-        }
-        if (fold && lane == 0) f.hdr[slot] = make_uint4(sc.epoch + 1u, sc.frame, n_fold, 0u);
-        __syncwarp();
+        if (fold) f.hdr[gi.player_off + threadIdx.x] = make_uint4(sc.epoch + 1u, sc.frame, (cleared ? 0u : h.z) + 1u, 0u);
     }
 }
 
 }  // namespace
 
-int launch_features(const FArgs& f, void* stream) {
+int launch_features(const FArgs& f, int pmax, int form, void* stream) {
     if (f.n_games <= 0) return 0;
+    if (form == 0) {  // a CTA per game for small batches
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        form = f.n_games < 16 * sms ? 2 : 1;  // measured crossover: 2,048 games CTA, 4,096 warp
+    }
+    if (form == 2) {
+        const int chunks = (f.npad_max + 127) >> 7;
+        const int warps = std::max(1, std::min(32, pmax * chunks));
+        const int smem = cta_bytes(f.npad_max, pmax);
+        static SmemLimit limit;
+        const void* fn = (const void*)k_features_cta;
+        const int e = limit.raise(&fn, 1, smem);
+        if (e != 0) return e;
+        k_features_cta<<<f.n_games, 32 * warps, smem, (cudaStream_t)stream>>>(f, pmax);
+        return (int)cudaGetLastError();
+    }
     const int smem = kWarps * warp_bytes(f.npad_max);
     static SmemLimit limit;
     const void* fn = (const void*)k_features;

@@ -137,8 +137,10 @@ struct FArgs {
     int2* series_out;      // optional [slot][T]: newest first, 0 before the episode
 };
 
-// Launch the feature builder over every game on `stream`.  Returns a cudaError_t.
-int launch_features(const FArgs& f, void* stream);
+// Launch the feature builder over every game on `stream`: form 1 one warp
+// per game, 2 one CTA per game, 0 by batch size.  pmax = the most players of
+// any game.  Returns a cudaError_t.
+int launch_features(const FArgs& f, int pmax, int form, void* stream);
 
 // Policy sampling over the H x W x 9 action space: one warp per game.
 struct SArgs {
@@ -155,8 +157,10 @@ struct SArgs {
     int32_t npad_max;       // largest board (cells, multiple of 16)
 };
 
-// Launch the sampler over every game on `stream`.  Returns a cudaError_t.
-int launch_sample(const SArgs& a, void* stream);
+// Launch the sampler over every game on `stream`: form 1 one warp per game,
+// 2 (and 0, the default) one CTA per game with a warp per player.  pmax = the most
+// players of any game.  Returns a cudaError_t.
+int launch_sample(const SArgs& a, int pmax, int form, void* stream);
 
 // Bytes of shared memory one warp needs for games up to npad_max cells and
 // pmax players; also returns the bitset stride in words.

@@ -17,20 +17,20 @@
 // single-precision operation with round-to-nearest written out explicitly
 // (no contraction), so the weights are bit-reproducible.
 //
-// One warp per game, players in turn.  The board is staged in shared memory
-// (every 16-byte load in flight at once); legal entries lie only on the
-// player's own cells, so the warp first lists those cells in index order (a
-// ballot per 32 cells, no global load) and the passes run over the list, 32
-// own cells at a time: pass 1 derives each cell's nine legal bits and takes
-// the maximum; pass 2 (logits held in registers for the first 64 own cells,
-// read again from L1/L2 beyond) sums each cell's weights,
+// One CTA per game with a warp per player (k_sample_cta, the default), or one
+// warp per game with the players in turn (k_sample).  The board is staged in
+// shared memory (every 16-byte copy in flight at once); legal entries lie
+// only on the player's own cells, so the warp first lists those cells in
+// index order (a ballot per 32 cells, no global load) and the passes run over
+// the list, 32 own cells at a time: pass 1 derives each cell's nine legal
+// bits and takes the maximum; pass 2 (logits held in registers for the first
+// 64 own cells, read again from L1/L2 beyond) sums each cell's weights,
 // computing every exponential once, and keeps the sums per cell and per 32
 // cells; pass 3 finds the group, the cell and (nine lanes weighing the cell's
 // entries at once) the entry where the running sum first exceeds r.  Only the
-// own cells' logits are read (36 bytes each).  The
-// expanded mask, when asked for, is a dense pass over every cell (a cell's
-// entries belong to its owner) written through shared memory with 16-byte
-// stores.
+// own cells' logits are read (36 bytes each).  The expanded mask, when asked
+// for, is a dense pass over every cell (a cell's entries belong to its owner)
+// written through shared memory with 16-byte stores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,13 +87,16 @@ __device__ __forceinline__ uint32_t legal9(int own_p, int army, uint32_t terrain
     return b;
 }
 
-// shared memory of one warp, sized for boards up to npad_max cells: the
-// board (4 B per cell), the player's own cells in index order (2 B), their
-// legal bits (2 B) and weight sums (4 B), the weight sum of every 32 of
-// them (8 B), mask staging (288 B); a multiple of 16 bytes
-__host__ __device__ __forceinline__ int sample_warp_bytes(int npad_max) {
+// shared memory of one warp's player, sized for boards up to npad_max cells:
+// the player's own cells in index order (2 B), their legal bits (2 B) and
+// weight sums (4 B), the weight sum of every 32 of them (8 B), mask staging
+// (288 B); a multiple of 16 bytes.  The board (4 B per cell) comes first.
+__host__ __device__ __forceinline__ int sample_player_bytes(int npad_max) {
     const int rounds = (npad_max + 31) >> 5;
-    return 12 * npad_max + 8 * ((rounds + 1) & ~1) + 288;
+    return 8 * npad_max + 8 * ((rounds + 1) & ~1) + 288;
+}
+__host__ __device__ __forceinline__ int sample_warp_bytes(int npad_max) {
+    return 4 * npad_max + sample_player_bytes(npad_max);
 }
 
 // the nine logits of one cell, every load issued before any is used
@@ -116,169 +119,218 @@ __device__ __forceinline__ uint64_t warp_incl64(uint64_t x, int lane) {
     return x;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+// a game's board in shared memory, by `nthreads` threads from `tid` on
+__device__ __forceinline__ void stage_board(const SArgs& a, const GameInfo& gi, char* b, int np, int tid, int nthreads) {
+    const uint4* ga = reinterpret_cast<const uint4*>(a.army + gi.cell_off);
+    const uint4* go = reinterpret_cast<const uint4*>(a.owner + gi.cell_off);
+    const uint4* gt = reinterpret_cast<const uint4*>(a.terrain + gi.cell_off);
+    uint4* sa = reinterpret_cast<uint4*>(b);
+    uint4* so = reinterpret_cast<uint4*>(b + 2 * np);
+    uint4* st = reinterpret_cast<uint4*>(b + 3 * np);
+    const int n16 = gi.Npad >> 4;
+    for (int v = tid; v < 2 * n16; v += nthreads) cp_async16(sa + v, ga + v);
+    for (int v = tid; v < n16; v += nthreads) {
+        cp_async16(so + v, go + v);
+        cp_async16(st + v, gt + v);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// expanded mask rows r0 = row0, row0 + drow, ... (32 cells each) of every
+// player: a cell's legal entries belong to its owner only
+__device__ __forceinline__ void mask_rows(const SArgs& a, const GameInfo& gi, const GameScalars& sc,
+                                          const int16_t* s_army, const int8_t* s_owner, const uint8_t* s_terrain,
+                                          uint8_t* s_mask, int row0, int drow, int lane) {
+    const int N = gi.N, Npad = gi.Npad, P = gi.P;
+    for (int r0 = row0; r0 < Npad; r0 += drow) {
+        const int cells = min(32, Npad - r0), c = r0 + lane;
+        int o = -1;
+        uint32_t lb = 0u;
+        if (c < N) {
+            o = s_owner[c];
+            if (o >= 0) {
+                const bool moves = ((sc.alive >> o) & 1u) && !sc.finished;
+                lb = legal9(true, s_army[c], s_terrain[c], moves);
+            }
+        }
+        const int n16 = (9 * cells) >> 4;
+        for (int p = 0; p < P; ++p) {
+            const uint32_t bits = o == p ? lb : 0u;
+            if (lane < cells)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) s_mask[9 * lane + k] = (uint8_t)((bits >> k) & 1u);
+            __syncwarp();
+            const int64_t base = (gi.plane_off + (int64_t)p * Npad) * 9;
+            if (lane < n16)
+                reinterpret_cast<uint4*>(a.mask9 + base + 9 * r0)[lane] = reinterpret_cast<const uint4*>(s_mask)[lane];
+            __syncwarp();
+        }
+    }
+}
+
+// player p's action, by one warp over its region `w` of shared memory
+__device__ __forceinline__ int32_t sample_player(const SArgs& a, const GameInfo& gi, const GameScalars& sc, int p,
+                                                 const int16_t* s_army, const int8_t* s_owner,
+                                                 const uint8_t* s_terrain, char* w, int lane) {
+    const int np = a.npad_max, N = gi.N, Npad = gi.Npad;
+    uint32_t* s_w = reinterpret_cast<uint32_t*>(w);                // [np] per own cell
+    uint16_t* s_list = reinterpret_cast<uint16_t*>(w + 4 * np);    // [np] own cells
+    uint16_t* s_legal = reinterpret_cast<uint16_t*>(w + 6 * np);   // [np] per own cell
+    uint64_t* s_round = reinterpret_cast<uint64_t*>(w + 8 * np);   // [rounds]
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const bool moves = ((sc.alive >> p) & 1u) && !sc.finished;
+    const float* lg = a.logits + (gi.plane_off + (int64_t)p * Npad) * 9;
+    // the player's cells in index order (legal entries lie only there)
+    int n = 0;
+    for (int r0 = 0; r0 < N; r0 += 32) {
+        const int c = r0 + lane;
+        const bool mine = c < N && s_owner[c] == p;
+        const unsigned bal = __ballot_sync(kAll, mine);
+        if (mine) s_list[n + __popc(bal & lt_mask)] = (uint16_t)c;
+        n += __popc(bal);
+    }
+    __syncwarp();
+    if (n == 0) return 0;
+    // pass 1: legal bits and the maximum legal logit; the first two groups'
+    // logits stay in registers for pass 2
+    float m = -3.402823466e38f;
+    float v0[9], v1[9];
+    for (int i = lane; i < n; i += 32) {
+        const int c = s_list[i];
+        const uint32_t lb = legal9(true, s_army[c], s_terrain[c], moves);
+        s_legal[i] = (uint16_t)lb;
+        float v[9];
+        load9(v, lg + 9 * c);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if ((lb >> k) & 1u) m = fmaxf(m, v[k]);
+        if (i < 32) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v0[k] = v[k];
+        } else if (i < 64) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v1[k] = v[k];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
+    __syncwarp();
+    // pass 2: weight sums per own cell and per 32 of them (every exponential once)
+    uint64_t S = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        uint32_t wsum = 0u;
+        if (i < n) {
+            const int c = s_list[i];
+            const uint32_t lb = s_legal[i];
+            float v[9];
+            if (i0 == 0) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = v0[k];
+            } else if (i0 == 32) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = v1[k];
+            } else {
+                load9(v, lg + 9 * c);
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if ((lb >> k) & 1u) wsum += weight_shift(v[k], m);
+            s_w[i] = wsum;
+        }
+        const uint64_t rs = warp_sum64(wsum);
+        if (lane == 0) s_round[i0 >> 5] = rs;
+        S += rs;
+    }
+    __syncwarp();
+    const uint64_t d = stream_out(hkey(a.seed, gi.game_id, sc.frame, (uint64_t)p), 7);
+    const uint64_t r = __umul64hi(d, S);
+    // pass 3: the group of 32, then the cell, then the entry where the running sum first exceeds r
+    const int groups = (n + 31) >> 5;
+    uint64_t run = 0;
+    int jr = -1;
+    for (int j0 = 0; j0 < groups && jr < 0; j0 += 32) {
+        const uint64_t rs = j0 + lane < groups ? s_round[j0 + lane] : 0u;
+        const uint64_t incl = warp_incl64(rs, lane);
+        const unsigned hit = __ballot_sync(kAll, run + incl > r);
+        if (hit) {
+            const int L = __ffs(hit) - 1;
+            jr = j0 + L;
+            run += __shfl_sync(kAll, incl - rs, L);
+        } else {
+            run += __shfl_sync(kAll, incl, 31);
+        }
+    }
+    const int i = 32 * jr + lane;
+    const uint64_t wi = i < n ? s_w[i] : 0u;
+    const uint64_t incl = warp_incl64(wi, lane);
+    const unsigned hit = __ballot_sync(kAll, run + incl > r);
+    const int L = __ffs(hit) - 1;
+    // the entry inside the chosen cell: lanes 0..8 take one entry each
+    const uint64_t before = run + __shfl_sync(kAll, incl - wi, L);
+    const int cL = s_list[32 * jr + L];
+    const uint32_t lbL = s_legal[32 * jr + L];
+    uint64_t we = 0;
+    if (lane < 9 && ((lbL >> lane) & 1u)) we = weight_shift(__ldcg(lg + 9 * cL + lane), m);
+    const uint64_t ein = warp_incl64(we, lane);
+    const unsigned ehit = __ballot_sync(kAll, lane < 9 && before + ein > r);
+    return 9 * cL + (__ffs(ehit) - 1);
+}
+
+// one warp per game, players in turn
 __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gidx = blockIdx.x * warps_per_cta + wid;
     if (gidx >= a.n_games) return;
     const int np = a.npad_max;
-    const int rounds_max = (np + 31) >> 5;
     char* b = smem + (size_t)wid * sample_warp_bytes(np);
-    int16_t* s_army = reinterpret_cast<int16_t*>(b);
-    int8_t* s_owner = reinterpret_cast<int8_t*>(b + 2 * np);
-    uint8_t* s_terrain = reinterpret_cast<uint8_t*>(b + 3 * np);
-    uint32_t* s_w = reinterpret_cast<uint32_t*>(b + 4 * np);          // [np] per own cell
-    uint16_t* s_list = reinterpret_cast<uint16_t*>(b + 8 * np);       // [np] own cells
-    uint16_t* s_legal = reinterpret_cast<uint16_t*>(b + 10 * np);     // [np] per own cell
-    uint64_t* s_round = reinterpret_cast<uint64_t*>(b + 12 * np);     // [rounds]
-    uint8_t* s_mask = reinterpret_cast<uint8_t*>(s_round + ((rounds_max + 1) & ~1));  // [288]
-
+    char* w = b + 4 * np;
     const GameInfo gi = a.info[gidx];
     const GameScalars sc = a.scal[gidx];
-    const int N = gi.N, Npad = gi.Npad, P = gi.P;
-    {  // board to shared memory, every 16-byte load in flight at once
-        const uint4* ga = reinterpret_cast<const uint4*>(a.army + gi.cell_off);
-        const uint4* go = reinterpret_cast<const uint4*>(a.owner + gi.cell_off);
-        const uint4* gt = reinterpret_cast<const uint4*>(a.terrain + gi.cell_off);
-        const int n16 = Npad >> 4;
-        for (int v = lane; v < 2 * n16; v += 32) reinterpret_cast<uint4*>(s_army)[v] = __ldcg(ga + v);
-        for (int v = lane; v < n16; v += 32) {
-            reinterpret_cast<uint4*>(s_owner)[v] = __ldcg(go + v);
-            reinterpret_cast<uint4*>(s_terrain)[v] = __ldcg(gt + v);
-        }
-        __syncwarp();
-    }
-
-    // expanded mask: a cell's legal entries belong to its owner only
-    if (a.mask9) {
-        for (int r0 = 0; r0 < Npad; r0 += 32) {
-            const int cells = min(32, Npad - r0), c = r0 + lane;
-            int o = -1;
-            uint32_t lb = 0u;
-            if (c < N) {
-                o = s_owner[c];
-                if (o >= 0) {
-                    const bool moves = ((sc.alive >> o) & 1u) && !sc.finished;
-                    lb = legal9(true, s_army[c], s_terrain[c], moves);
-                }
-            }
-            const int n16 = (9 * cells) >> 4;
-            for (int p = 0; p < P; ++p) {
-                const uint32_t bits = o == p ? lb : 0u;
-                if (lane < cells)
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) s_mask[9 * lane + k] = (uint8_t)((bits >> k) & 1u);
-                __syncwarp();
-                const int64_t base = (gi.plane_off + (int64_t)p * Npad) * 9;
-                if (lane < n16)
-                    reinterpret_cast<uint4*>(a.mask9 + base + 9 * r0)[lane] = reinterpret_cast<const uint4*>(s_mask)[lane];
-                __syncwarp();
-            }
-        }
-    }
+    stage_board(a, gi, b, np, lane, 32);
+    __syncwarp();
+    const int16_t* s_army = reinterpret_cast<const int16_t*>(b);
+    const int8_t* s_owner = reinterpret_cast<const int8_t*>(b + 2 * np);
+    const uint8_t* s_terrain = reinterpret_cast<const uint8_t*>(b + 3 * np);
+    if (a.mask9)
+        mask_rows(a, gi, sc, s_army, s_owner, s_terrain, reinterpret_cast<uint8_t*>(w + sample_player_bytes(np) - 288),
+                  0, 32, lane);
     if (!a.logits) return;
-
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int p = 0; p < P; ++p) {
-        const bool moves = ((sc.alive >> p) & 1u) && !sc.finished;
-        const float* lg = a.logits + (gi.plane_off + (int64_t)p * Npad) * 9;
-        // the player's cells in index order (legal entries lie only there)
-        int n = 0;
-        for (int r0 = 0; r0 < N; r0 += 32) {
-            const int c = r0 + lane;
-            const bool mine = c < N && s_owner[c] == p;
-            const unsigned bal = __ballot_sync(kAll, mine);
-            if (mine) s_list[n + __popc(bal & lt_mask)] = (uint16_t)c;
-            n += __popc(bal);
-        }
+    for (int p = 0; p < gi.P; ++p) {
+        const int32_t action = sample_player(a, gi, sc, p, s_army, s_owner, s_terrain, w, lane);
+        if (lane == 0 && a.actions) a.actions[gi.player_off + p] = action;
         __syncwarp();
-        int32_t action = 0;
-        if (n > 0) {
-            // pass 1: legal bits and the maximum legal logit; the first two
-            // groups' logits stay in registers for pass 2
-            float m = -3.402823466e38f;
-            float v0[9], v1[9];
-            for (int i = lane; i < n; i += 32) {
-                const int c = s_list[i];
-                const uint32_t lb = legal9(true, s_army[c], s_terrain[c], moves);
-                s_legal[i] = (uint16_t)lb;
-                float v[9];
-                load9(v, lg + 9 * c);
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    if ((lb >> k) & 1u) m = fmaxf(m, v[k]);
-                if (i < 32) {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) v0[k] = v[k];
-                } else if (i < 64) {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) v1[k] = v[k];
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
-            __syncwarp();
-            // pass 2: weight sums per own cell and per 32 of them (every exponential once)
-            uint64_t S = 0;
-            for (int i0 = 0; i0 < n; i0 += 32) {
-                const int i = i0 + lane;
-                uint32_t w = 0u;
-                if (i < n) {
-                    const int c = s_list[i];
-                    const uint32_t lb = s_legal[i];
-                    float v[9];
-                    if (i0 == 0) {
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) v[k] = v0[k];
-                    } else if (i0 == 32) {
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) v[k] = v1[k];
-                    } else {
-                        load9(v, lg + 9 * c);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        if ((lb >> k) & 1u) w += weight_shift(v[k], m);
-                    s_w[i] = w;
-                }
-                const uint64_t rs = warp_sum64(w);
-                if (lane == 0) s_round[i0 >> 5] = rs;
-                S += rs;
-            }
-            __syncwarp();
-            const uint64_t d = stream_out(hkey(a.seed, gi.game_id, sc.frame, (uint64_t)p), 7);
-            const uint64_t r = __umul64hi(d, S);
-            // pass 3: the group of 32, then the cell, then the entry where the running sum first exceeds r
-            const int groups = (n + 31) >> 5;
-            uint64_t run = 0;
-            int jr = -1;
-            for (int j0 = 0; j0 < groups && jr < 0; j0 += 32) {
-                const uint64_t rs = j0 + lane < groups ? s_round[j0 + lane] : 0u;
-                const uint64_t incl = warp_incl64(rs, lane);
-                const unsigned hit = __ballot_sync(kAll, run + incl > r);
-                if (hit) {
-                    const int L = __ffs(hit) - 1;
-                    jr = j0 + L;
-                    run += __shfl_sync(kAll, incl - rs, L);
-                } else {
-                    run += __shfl_sync(kAll, incl, 31);
-                }
-            }
-            const int i = 32 * jr + lane;
-            const uint64_t w = i < n ? s_w[i] : 0u;
-            const uint64_t incl = warp_incl64(w, lane);
-            const unsigned hit = __ballot_sync(kAll, run + incl > r);
-            const int L = __ffs(hit) - 1;
-            // the entry inside the chosen cell: lanes 0..8 take one entry each
-            const uint64_t before = run + __shfl_sync(kAll, incl - w, L);
-            const int cL = s_list[32 * jr + L];
-            const uint32_t lbL = s_legal[32 * jr + L];
-            uint64_t we = 0;
-            if (lane < 9 && ((lbL >> lane) & 1u)) we = weight_shift(__ldcg(lg + 9 * cL + lane), m);
-            const uint64_t ein = warp_incl64(we, lane);
-            const unsigned ehit = __ballot_sync(kAll, lane < 9 && before + ein > r);
-            action = 9 * cL + (__ffs(ehit) - 1);
-        }
+    }
+}
+
+// one CTA per game (small batches): warp q takes players q, q + warps, ...
+// and mask rows q, q + warps, ... over its own region of shared memory
+__global__ void __launch_bounds__(256) k_sample_cta(const SArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int gidx = blockIdx.x;  // the grid is one CTA per game
+    const int np = a.npad_max;
+    char* w = smem + 4 * np + (size_t)wid * sample_player_bytes(np);
+    const GameInfo gi = a.info[gidx];
+    const GameScalars sc = a.scal[gidx];
+    stage_board(a, gi, smem, np, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int16_t* s_army = reinterpret_cast<const int16_t*>(smem);
+    const int8_t* s_owner = reinterpret_cast<const int8_t*>(smem + 2 * np);
+    const uint8_t* s_terrain = reinterpret_cast<const uint8_t*>(smem + 3 * np);
+    if (a.mask9)
+        mask_rows(a, gi, sc, s_army, s_owner, s_terrain, reinterpret_cast<uint8_t*>(w + sample_player_bytes(np) - 288),
+                  32 * wid, 32 * nwarps, lane);
+    if (!a.logits) return;
+    for (int p = wid; p < gi.P; p += nwarps) {
+        const int32_t action = sample_player(a, gi, sc, p, s_army, s_owner, s_terrain, w, lane);
         if (lane == 0 && a.actions) a.actions[gi.player_off + p] = action;
         __syncwarp();
     }
@@ -286,8 +338,23 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta
 
 }  // namespace
 
-int launch_sample(const SArgs& a, void* stream) {
+int launch_sample(const SArgs& a, int pmax, int form, void* stream) {
     if (a.n_games <= 0) return 0;
+    // a CTA per game by default: measured faster at every batch from 512 to
+    // 65,536 games of 24x24 but one (more warps per SM, players side by side)
+    if (form == 0) form = 2;
+    if (form == 2) {
+        // a warp per player, as many as fit next to the board (at least one)
+        const int fit = (227 * 1024 - 4 * a.npad_max) / sample_player_bytes(a.npad_max);
+        const int warps = std::max(1, std::min(std::min(pmax, kWarps), fit));
+        const int smem = 4 * a.npad_max + warps * sample_player_bytes(a.npad_max);
+        static SmemLimit limit;
+        const void* fn = (const void*)k_sample_cta;
+        const int e = limit.raise(&fn, 1, smem);
+        if (e != 0) return e;
+        k_sample_cta<<<a.n_games, 32 * warps, smem, (cudaStream_t)stream>>>(a);
+        return (int)cudaGetLastError();
+    }
     const int per_warp = sample_warp_bytes(a.npad_max);
     const int wpc = std::max(1, std::min(kWarps, (200 * 1024) / per_warp));
     const int smem = wpc * per_warp;

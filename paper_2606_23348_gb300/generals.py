@@ -60,7 +60,7 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
            "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
            "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
-           "gen_features_build_ex", "gen_sample_actions")
+           "gen_features_build_ex", "gen_features_set_form", "gen_sample_actions", "gen_set_sample_form")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -102,7 +102,9 @@ def load_library(path: str = LIB_PATH):
             "gen_features_create_ex": (C.c_int, [C.POINTER(vp), vp, C.c_int, C.c_int]),
             "gen_features_series_layout": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int64)]),
             "gen_features_build_ex": (C.c_int, [vp, vp, vp, vp]),
+            "gen_features_set_form": (C.c_int, [vp, C.c_int]),
             "gen_sample_actions": (C.c_int, [vp, vp, u64, vp, vp, vp]),
+            "gen_set_sample_form": (C.c_int, [vp, C.c_int]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
         }
@@ -282,6 +284,11 @@ class GeneralsEnv:
         import torch
         return torch.zeros(int(self.layout.plane_cells) * 9, dtype=torch.float32, device="cuda")
 
+    def set_sample_form(self, form: int):
+        """How sample_actions spreads a game over the GPU: 1 one warp per
+        game, 2 one CTA per game with a warp per player, 0 the default (2)."""
+        _check(self.lib.gen_set_sample_form(self.h, int(form)), "gen_set_sample_form")
+
     def sample_actions(self, logits, seed: int, actions=None, mask9=None):
         """Draw one action per player from `logits` (9 per plane cell) into
         `actions` (allocated when None); `mask9` (uint8, 9 per plane cell)
@@ -384,6 +391,13 @@ class Features:
         _check(self.lib.gen_features_build_ex(self.h, C.c_void_p(out.data_ptr()), sp, _cur_stream()),
                "gen_features_build_ex")
         return out
+
+    FORM_AUTO, FORM_WARP, FORM_CTA = 0, 1, 2
+
+    def set_form(self, form: int):
+        """Spread of a game over the GPU: FORM_WARP (one warp per game),
+        FORM_CTA (one CTA per game, for small batches) or FORM_AUTO."""
+        _check(self.lib.gen_features_set_form(self.h, int(form)), "gen_features_set_form")
 
     def player_series(self, series, g: int, p: int):
         """[T][2] (army, land) view of game g, player p inside a series output."""

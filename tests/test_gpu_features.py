@@ -96,18 +96,26 @@ def lockstep(env, orc, fb, ofb, frames, policy_seed, tag, every=1, subset_reset=
     return fout
 
 
-def pair(H, W, mode, P, hist=7, window=0, **kw):
+def pair(H, W, mode, P, hist=7, window=0, form=0, **kw):
     from paper_2606_23348_gb300.generals import GeneralsEnv
     env = GeneralsEnv(H, W, mode, P, **kw)
     orc = OracleEnv(H, W, mode, P, **kw)
-    return env, orc, env.features(hist, window), OracleFeatures(orc, hist, window)
+    fb = env.features(hist, window)
+    if form:
+        fb.set_form(form)
+    return env, orc, fb, OracleFeatures(orc, hist, window)
 
 
-def test_features_mixed_modes_with_resets():
+# both spreads of a game over the GPU: one warp per game, one CTA per game
+FORMS = pytest.mark.parametrize("form", [1, 2], ids=["warp", "cta"])
+
+
+@FORMS
+def test_features_mixed_modes_with_resets(form):
     """Ragged 1v1 / 2v2 / FFA boards, truncation resets every 25 turns, every frame compared."""
     G = 24
     H, W, mode, P = shapes(G, (4, 12), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=8)
-    env, orc, fb, ofb = pair(H, W, mode, P, window=32, seed=4, n_cities=2, max_turns=25)
+    env, orc, fb, ofb = pair(H, W, mode, P, window=32, form=form, seed=4, n_cities=2, max_turns=25)
     lockstep(env, orc, fb, ofb, 80, 6, "mixed")
 
 
@@ -119,11 +127,12 @@ def test_features_history_lengths(hist, window):
     lockstep(env, orc, fb, ofb, 30, 3, f"hist {hist}", every=3)
 
 
-def test_features_subset_reset_and_repeat_build():
+@FORMS
+def test_features_subset_reset_and_repeat_build(form):
     """A reset of some games clears their memory; a second build in one frame changes nothing."""
     G = 12
     H, W, mode, P = shapes(G, (6, 9), ((0, 0.5), (2, 0.5)), seed=2)
-    env, orc, fb, ofb = pair(H, W, mode, P, window=7, seed=3, n_cities=2)
+    env, orc, fb, ofb = pair(H, W, mode, P, window=7, form=form, seed=3, n_cities=2)
     fout = lockstep(env, orc, fb, ofb, 20, 5, "subset", subset_reset=[0, 5, 11])
     again = fb.build()
     import torch
@@ -131,9 +140,11 @@ def test_features_subset_reset_and_repeat_build():
     assert torch.equal(fout, again)
 
 
+@FORMS
 @pytest.mark.parametrize("H,W,mode,P", [(1, 2, 0, 2), (40, 1, 2, 3), (33, 5, 1, 4), (64, 64, 2, 8), (3, 3, 2, 8)])
-def test_features_edge_shapes(H, W, mode, P):
-    env, orc, fb, ofb = pair([H, H], [W, W], [mode, mode], [P, P], window=3, seed=5, n_cities=1, max_turns=15)
+def test_features_edge_shapes(H, W, mode, P, form):
+    env, orc, fb, ofb = pair([H, H], [W, W], [mode, mode], [P, P], window=3, form=form, seed=5, n_cities=1,
+                             max_turns=15)
     lockstep(env, orc, fb, ofb, 20, 9, f"edge {H}x{W}", every=4)
 
 
@@ -176,7 +187,8 @@ def test_feature_golden_on_gpu(path):
     assert n > 10
 
 
-def test_features_full_size_24x24_65536_sampled():
+@FORMS
+def test_features_full_size_24x24_65536_sampled(form):
     """65,536 games of 24x24: features built every frame on the GPU; three
     blocks of 32 games replayed by the oracle and compared at the end."""
     import torch
@@ -184,6 +196,7 @@ def test_features_full_size_24x24_65536_sampled():
     H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
     env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
     fb = env.features(7, 512)
+    fb.set_form(form)
     out = env.new_outputs()
     acts = env.new_actions()
     fout = fb.new_output()
@@ -225,5 +238,8 @@ def test_feature_builder_argument_errors():
         fb.build(out, torch.zeros(16, dtype=torch.int32, device="cuda"))  # no temporal window
     assert lib.gen_features_build(fb.h, C.c_void_p(out.data_ptr() + 4), None) != 0  # misaligned
     assert lib.gen_features_build(fb.h, None, None) != 0
+    for form in (-1, 3):
+        with pytest.raises(GeneralsError):
+            fb.set_form(form)
     fb.build(out)  # still usable
     torch.cuda.synchronize()

@@ -61,12 +61,18 @@ def pair(H, W, mode, P, **kw):
     return GeneralsEnv(H, W, mode, P, **kw), OracleEnv(H, W, mode, P, **kw)
 
 
+# both spreads of a game over the GPU: one warp per game, one CTA per game
+FORMS = pytest.mark.parametrize("form", [1, 2], ids=["warp", "cta"])
+
+
+@FORMS
 @pytest.mark.parametrize("scale", [0.0, 3.0, 40.0])
-def test_sampling_matches_oracle_mixed_modes(scale):
+def test_sampling_matches_oracle_mixed_modes(scale, form):
     import torch
     G = 30
     H, W, mode, P = shapes(G, (3, 14), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=5)
     env, orc = pair(H, W, mode, P, seed=8, n_cities=2)
+    env.set_sample_form(form)
     acts = env.new_actions()
     out = env.new_outputs()
     env.policy(3, acts)
@@ -98,10 +104,12 @@ def test_device_rollout_from_logits():
         compare_frame(env, out, orc, f"frame {f}")
 
 
+@FORMS
 @pytest.mark.parametrize("H,W,mode,P", [(1, 2, 0, 2), (40, 1, 2, 3), (64, 64, 2, 8), (3, 3, 2, 8)])
-def test_sampling_edge_shapes(H, W, mode, P):
+def test_sampling_edge_shapes(H, W, mode, P, form):
     import torch
     env, orc = pair([H, H], [W, W], [mode, mode], [P, P], seed=5, n_cities=1)
+    env.set_sample_form(form)
     acts = env.new_actions()
     out = env.new_outputs()
     env.policy(1, acts)
@@ -124,6 +132,15 @@ def test_expand_mask_only_and_errors():
     env.sample_actions(logits, 1, None, m9b)
     torch.cuda.synchronize()
     assert torch.equal(m9, m9b)
+    for form in (1, 2):  # the mask of either spread, and the actions with it
+        env.set_sample_form(form)
+        m9c, a1 = torch.empty_like(m9), env.sample_actions(logits, 1)
+        a2 = env.sample_actions(logits, 1, None, m9c)
+        torch.cuda.synchronize()
+        assert torch.equal(m9, m9c) and torch.equal(a1, a2)
+    for form in (-1, 3):
+        with pytest.raises(GeneralsError):
+            env.set_sample_form(form)
     assert env.lib.gen_sample_actions(env.h, None, 0, None, None, None) != 0  # nothing to compute
     with pytest.raises(GeneralsError):
         env.sample_actions(logits[1:], 1)  # misaligned logits
