@@ -45,9 +45,9 @@ MAP_SEED = 1
 NCU_TRAFFIC = {"kernel_sha1": "c8c074b3b410", "bytes_per_launch": 2 * 325580032.0,
                "warp_inst_per_launch": 2 * 58977272.0, "captured": "32,768 games (x2)", "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
-SAMPLE_NCU = {"kernel_sha1": "d7499ce12f09", "bytes_per_launch": 4 * 138351104.0,
-              "warp_inst_per_launch": 4 * 47394660.0, "captured": "16,384 games (x4)", "games": 65536}
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "6473b2b9435c", "bytes_per_launch": 8 * 1911564864.0,
+SAMPLE_NCU = {"kernel_sha1": "1229b630d960", "bytes_per_launch": 4 * 137880064.0,
+              "warp_inst_per_launch": 4 * 52898856.0, "captured": "16,384 games (x4)", "games": 65536}
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "c0e264f2bd12", "bytes_per_launch": 8 * 1910267904.0,
                        "captured": "8,192 games (x8)", "games": 65536}
 
 
@@ -685,7 +685,7 @@ def run_sampling(args, rank, world, local):
                                      and G == SAMPLE_NCU["games"] else None),
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": samp_ms,
-                         "kernel": "k_sample (H x W x 9 policy sampling)"},
+                         "kernel": "k_sample_cta (H x W x 9 policy sampling, a CTA per game)"},
             "issue_roofline": issue_roofline(samp_ms, G, clk, SAMPLE_NCU, "gk_sample.cu"),
             "step_launch_ms": step_ms,
             "gpu_launches": 2 * K,
