@@ -353,20 +353,32 @@ __device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, co
         st4(row += Npad, cx[0], cx[1], cx[2], cx[3]);
         st4(row += Npad, cy[0], cy[1], cy[2], cy[3]);
     }
-    // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back
-    uint2 po = own, pe = ene;
+    // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back;
+    // each pair is loaded two iterations ahead of the stores that use it
+    auto ring_pair = [&](int back, uint2& o, uint2& e) {  // own / enemy planes `back` frames ago
+        o = make_uint2(0u, 0u);
+        e = o;
+        if (back < x.nvalid) {
+            const int sl = (x.head - back + R) % R;
+            o = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
+            e = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
+        }
+    };
+    uint2 po = own, pe = ene, o1, e1, o2, e2;
+    ring_pair(1, o1, e1);
+    ring_pair(2, o2, e2);
     float* rd = row + (int64_t)Npad;
     for (int k = 0; k < K; ++k, rd += Npad) {
-        uint2 no = make_uint2(0u, 0u), ne = make_uint2(0u, 0u);
-        if (k + 1 < x.nvalid) {
-            const int sl = (x.head - (k + 1) + R) % R;
-            no = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
-            ne = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
-        }
-        st4d(rd, po, no);
-        st4d(rd + (int64_t)K * Npad, pe, ne);
-        po = no;
-        pe = ne;
+        uint2 o3, e3;
+        ring_pair(k + 3, o3, e3);
+        st4d(rd, po, o1);
+        st4d(rd + (int64_t)K * Npad, pe, e1);
+        po = o1;
+        pe = e1;
+        o1 = o2;
+        e1 = e2;
+        o2 = o3;
+        e2 = e3;
     }
 }
 
