@@ -42,12 +42,12 @@ MAP_SEED = 1
 # of the same kernel with inputs larger than L2 and scaled by the games it
 # processes (traffic grows in proportion); valid only for the kernel source
 # it was taken on.
-NCU_TRAFFIC = {"kernel_sha1": "c8c074b3b410", "bytes_per_launch": 2 * 325580032.0,
+NCU_TRAFFIC = {"kernel_sha1": "df64a6d61122", "bytes_per_launch": 2 * 325966336.0,
                "warp_inst_per_launch": 2 * 58977272.0, "captured": "32,768 games (x2)", "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
 SAMPLE_NCU = {"kernel_sha1": "1229b630d960", "bytes_per_launch": 4 * 137880064.0,
               "warp_inst_per_launch": 4 * 52898856.0, "captured": "16,384 games (x4)", "games": 65536}
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "c0e264f2bd12", "bytes_per_launch": 8 * 1910267904.0,
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "0becd141ea17", "bytes_per_launch": 8 * 1911037952.0,
                        "captured": "8,192 games (x8)", "games": 65536}
 
 

@@ -350,6 +350,14 @@ int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_serv
 int gen_sample_actions(gen_env *env, const float *d_logits, uint64_t seed, int32_t *d_actions, uint8_t *d_mask9,
                        void *stream);
 
+/* Games per warp in the step kernels (the results are the same): 1 = one
+ * warp per game; 2 = two games per warp (four in multi-frame launches)
+ * wherever the games allow it -- at most two players, boards of at most
+ * 1,024 padded cells (576 for four), no spawn options; 0 (default) = as 2 for
+ * launches of at least 12 x the SM count games (24 x in multi-frame
+ * launches), else 1.  GEN_ERR_BAD_ARG for NULL env or a mode outside 0..2. */
+int gen_set_lane_groups(gen_env *env, int mode);
+
 /* How gen_sample_actions spreads a game over the GPU (the results are the
  * same): 1 = one warp per game, players in turn; 2 = one CTA per game with a
  * warp per player (as many as fit in shared memory beside the board);

@@ -75,7 +75,8 @@ struct gen_env {
     int player_slots = 0;
     int pmax = 0;
     int npad_max = 0;
-    int sample_form = 0;  // gen_sample_actions: 0 by batch size, 1 warp per game, 2 CTA per game
+    int sample_form = 0;  // gen_sample_actions: 0 (default) and 2 a CTA per game, 1 a warp per game
+    int lane_groups = 0;  // step kernels: 0 by batch size, 1 a warp per game, 2 several per warp when allowed
     int nmax = 0;
     bool uniform = false;            // every game has the same board size and mode
     Bucket all;                      // every game, largest carve (used for game-id lists)
@@ -196,6 +197,7 @@ KArgs base_args(const gen_env* e, const Bucket& b, int op) {
     a.spawn_dmax = e->prm.max_general_dist;
     a.spawn_bfs = e->prm.bfs_distance ? 1 : 0;
     a.castle_radius = e->prm.castle_radius;
+    a.lane_groups = e->lane_groups;
     a.city_min = e->prm.city_army_min;
     a.city_span = e->prm.city_army_max - e->prm.city_army_min + 1;
     a.max_turns = e->prm.max_turns;
@@ -1012,6 +1014,13 @@ int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t
     a.npad_max = e->npad_max;
     const int rc = gk::launch_sample(a, e->pmax, e->sample_form, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, "sampler launch");
+    return GEN_OK;
+}
+
+int gen_set_lane_groups(gen_env* e, int mode) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (mode < 0 || mode > 2) return fail(GEN_ERR_BAD_ARG, "mode %d outside [0, 2]", mode);
+    e->lane_groups = mode;
     return GEN_OK;
 }
 

@@ -91,6 +91,9 @@ struct KArgs {
     int32_t spawn_dmax;     // cap on a general's distance to every earlier one (0: none)
     int32_t spawn_bfs;      // 1: spacing in BFS steps around mountains
     int32_t castle_radius;  // > 0: a neutral castle within this many steps of every general
+    // games per warp: 0 by batch size, 1 a warp per game, 2 two or four per
+    // warp whenever the games allow (two players, small boards, no spawn options)
+    int32_t lane_groups;
 };
 
 // Dynamic shared memory above 48 KiB needs a per-kernel opt-in on each

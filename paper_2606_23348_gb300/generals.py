@@ -60,7 +60,8 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_write_state", "gen_set_launch", "gen_autotune", "gen_copy_peak", "gen_last_error", "gen_destroy",
            "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
            "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
-           "gen_features_build_ex", "gen_features_set_form", "gen_sample_actions", "gen_set_sample_form")
+           "gen_features_build_ex", "gen_features_set_form", "gen_sample_actions", "gen_set_sample_form",
+           "gen_set_lane_groups")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
             "gen_features_set_form": (C.c_int, [vp, C.c_int]),
             "gen_sample_actions": (C.c_int, [vp, vp, u64, vp, vp, vp]),
             "gen_set_sample_form": (C.c_int, [vp, C.c_int]),
+            "gen_set_lane_groups": (C.c_int, [vp, C.c_int]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
         }
@@ -283,6 +285,14 @@ class GeneralsEnv:
         """Zero logits: 9 float32 per cell of every player plane."""
         import torch
         return torch.zeros(int(self.layout.plane_cells) * 9, dtype=torch.float32, device="cuda")
+
+    LANES_AUTO, LANES_WARP, LANES_NARROW = 0, 1, 2
+
+    def set_lane_groups(self, mode: int):
+        """Games per warp in the step kernels: LANES_WARP (one), LANES_NARROW
+        (two, four in rollouts, wherever the games allow) or LANES_AUTO (by
+        batch size)."""
+        _check(self.lib.gen_set_lane_groups(self.h, int(mode)), "gen_set_lane_groups")
 
     def set_sample_form(self, form: int):
         """How sample_actions spreads a game over the GPU: 1 one warp per

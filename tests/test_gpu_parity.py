@@ -22,11 +22,19 @@ def _built():
     build_library()
 
 
-def pair(H, W, mode, n_players, **kw):
+def pair(H, W, mode, n_players, lanes=0, **kw):
     from paper_2606_23348_gb300.generals import GeneralsEnv
     env = GeneralsEnv(H, W, mode, n_players, **kw)
+    if lanes:
+        env.set_lane_groups(lanes)
     orc = OracleEnv(H, W, mode, n_players, **kw)
     return env, orc
+
+
+# games per warp in the step kernels: one, by batch size, or two (four in
+# rollouts) wherever the games allow
+LANES = pytest.mark.parametrize("lanes", [1, 2], ids=["warp", "narrow"])
+LANES_AUTO = pytest.mark.parametrize("lanes", [0, 2], ids=["auto", "narrow"])
 
 
 def rollout_policy(env, orc, frames, policy_seed=2, check_every=1, tag=""):
@@ -49,20 +57,22 @@ def rollout_policy(env, orc, frames, policy_seed=2, check_every=1, tag=""):
     return out
 
 
-def test_c0_1v1_64x15x15_500_turns():
+@LANES
+def test_c0_1v1_64x15x15_500_turns(lanes):
     """The 64-game 15x15 1v1 workload, 500 turns of the benchmark policy, every frame compared."""
     H, W, mode, P, gen, frames = workload("1v1-64x15x15")
-    env, orc = pair(H, W, mode, P, seed=1, **gen)
+    env, orc = pair(H, W, mode, P, lanes=lanes, seed=1, **gen)
     rollout_policy(env, orc, frames, policy_seed=2, tag="c0")
 
 
-def test_mixed_modes_tiny_maps_captures_and_resets():
+@LANES_AUTO
+def test_mixed_modes_tiny_maps_captures_and_resets(lanes):
     """Ragged 1v1 / 2v2 / FFA games on small boards: captures, land transfer, eliminations,
     truncation and auto-reset all happen within a few hundred frames."""
     G = 96
     H, W, mode, P = shapes(G, (3, 9), ((0, 0.34), (1, 0.33), (2, 0.33)), seed=5)
     P = np.where(mode == 2, np.minimum(8, H * W), P).astype(np.int32)
-    env, orc = pair(H, W, mode, P, seed=11, min_general_dist=1, n_cities=1, max_turns=90)
+    env, orc = pair(H, W, mode, P, lanes=lanes, seed=11, min_general_dist=1, n_cities=1, max_turns=90)
     rollout_policy(env, orc, 300, policy_seed=7, tag="mixed")
     st = env.read_state()[3]
     assert st[:, 2].max() >= 2, "expected several resets"
@@ -95,18 +105,20 @@ def test_arbitrary_actions_validation():
 @pytest.mark.parametrize("H,W,mode,P", [(1, 2, 0, 2), (2, 1, 0, 2), (1, 40, 0, 2), (40, 1, 2, 3), (33, 5, 1, 4),
                                         (5, 33, 2, 8), (64, 64, 2, 8), (64, 64, 0, 2), (17, 31, 1, 4),
                                         (3, 3, 2, 8)])
-def test_edge_shapes(H, W, mode, P):
+@LANES_AUTO
+def test_edge_shapes(H, W, mode, P, lanes):
     G = 6
-    env, orc = pair(np.full(G, H), np.full(G, W), np.full(G, mode), np.full(G, P), seed=H * 100 + W,
-                    min_general_dist=0, n_cities=3, max_turns=25)
+    env, orc = pair(np.full(G, H), np.full(G, W), np.full(G, mode), np.full(G, P), lanes=lanes,
+                    seed=H * 100 + W, min_general_dist=0, n_cities=3, max_turns=25)
     rollout_policy(env, orc, 60, policy_seed=1, check_every=3, tag=f"{H}x{W}")
 
 
-def test_no_mountains_and_all_mountains():
+@LANES_AUTO
+def test_no_mountains_and_all_mountains(lanes):
     for thr in (0, 0xFFFFFFFF):
         G = 8
-        env, orc = pair(np.full(G, 9), np.full(G, 11), np.zeros(G), np.full(G, 2), seed=5, mountain_thresh=thr,
-                        n_cities=4, max_turns=30)
+        env, orc = pair(np.full(G, 9), np.full(G, 11), np.zeros(G), np.full(G, 2), lanes=lanes, seed=5,
+                        mountain_thresh=thr, n_cities=4, max_turns=30)
         rollout_policy(env, orc, 40, tag=f"mtn{thr}")
 
 
@@ -117,10 +129,11 @@ def test_two_player_ffa_and_1v1_in_narrow_groups():
     G = 40
     H, W, mode, _ = shapes(G, (4, 24), ((0, 0.5), (2, 0.5)), seed=13)
     P = np.full(G, 2, np.int32)
-    env, orc = pair(H, W, mode, P, seed=6, min_general_dist=1, n_cities=3, max_turns=50)
+    env, orc = pair(H, W, mode, P, lanes=2, seed=6, min_general_dist=1, n_cities=3, max_turns=50)
     rollout_policy(env, orc, 120, policy_seed=3, tag="ffa2 ragged")
     kw = dict(seed=9, min_general_dist=2, n_cities=4, max_turns=60)
     env = GeneralsEnv(12, 12, 2, 2, batch=G, **kw)
+    env.set_lane_groups(env.LANES_NARROW)
     orc = OracleEnv(np.full(G, 12), np.full(G, 12), np.full(G, 2), np.full(G, 2), **kw)
     rollout_policy(env, orc, 130, policy_seed=5, tag="ffa2 uniform")
 
@@ -325,7 +338,8 @@ EXHAUSTIVE_POSITIONS = [
 
 @pytest.mark.parametrize("side,rows", EXHAUSTIVE_POSITIONS, ids=[f"{s}x{s}-{i}" for i, (s, _) in enumerate(
     EXHAUSTIVE_POSITIONS)])
-def test_exhaustive_joint_actions_on_gpu(side, rows):
+@LANES
+def test_exhaustive_joint_actions_on_gpu(side, rows, lanes):
     """Every joint action of both players on a hand-built position, one game
     per joint action in a single launch (81^2 games on 3x3, 144^2 on 4x4),
     at an even and an odd turn, with auto-reset on: every state and output
@@ -341,6 +355,7 @@ def test_exhaustive_joint_actions_on_gpu(side, rows):
     for turn in (0, 1):
         kw = dict(seed=9, n_cities=1, min_general_dist=1)
         env = GeneralsEnv(np.full(G, side), np.full(G, side), np.zeros(G), np.full(G, 2), **kw)
+        env.set_lane_groups(lanes)
         orc = OracleEnv(np.full(G, side), np.full(G, side), np.zeros(G), np.full(G, 2), **kw)
         npad = int(env.npad[0])
         pad = lambda x, v: np.concatenate([x, np.full(npad - N, v, x.dtype)])

@@ -33,7 +33,7 @@ def frame_view(env, out, k):
     return v
 
 
-def make_pair(G=48, seed=3, two_player=False):
+def make_pair(G=48, seed=3, two_player=False, lanes=0):
     from paper_2606_23348_gb300.generals import GeneralsEnv
     modes = ((0, 0.5), (2, 0.5)) if two_player else ((0, 0.4), (1, 0.3), (2, 0.3))
     H, W, mode, P = shapes(G, (4, 20), modes, seed=seed)
@@ -41,12 +41,16 @@ def make_pair(G=48, seed=3, two_player=False):
     if two_player:
         P = np.full(G, 2, np.int32)
     kw = dict(seed=seed, min_general_dist=1, n_cities=2, max_turns=40)
-    return GeneralsEnv(H, W, mode, P, **kw), OracleEnv(H, W, mode, P, **kw)
+    env = GeneralsEnv(H, W, mode, P, **kw)
+    if lanes:
+        env.set_lane_groups(lanes)
+    return env, OracleEnv(H, W, mode, P, **kw)
 
 
+@pytest.mark.parametrize("lanes", [0, 2], ids=["auto", "narrow"])
 @pytest.mark.parametrize("form", [0, 1, 2], ids=["resident", "graph", "launches"])
-def test_rollout_matches_oracle(form):
-    env, orc = make_pair()
+def test_rollout_matches_oracle(form, lanes):
+    env, orc = make_pair(lanes=lanes)
     assert len(set(zip(env.npad // 256, env.P))) > 1  # several size buckets
     check_rollout(env, orc, form)
 
@@ -55,7 +59,7 @@ def test_rollout_matches_oracle(form):
 def test_rollout_two_player_ffa_with_1v1(form):
     """Two-player free-for-all games share the narrow lane groups (two or
     four games per warp) with 1v1 games: the same rules, bit-exact."""
-    env, orc = make_pair(G=64, seed=17, two_player=True)
+    env, orc = make_pair(G=64, seed=17, two_player=True, lanes=2)
     assert set(env.P.tolist()) == {2} and max(env.npad) <= 576
     check_rollout(env, orc, form)
 
