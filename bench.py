@@ -377,7 +377,7 @@ def run_ours(args, rank, world, local):
                        "cities": 12, "mountains": 0.2, "policy": "uniform legal, split p=0.2",
                        "parallelism": f"replicas x{world} (disjoint game ids)",
                        "l2": "inputs larger than L2 (state 151 MB + outputs 529 MB per step)",
-                       "launch": f"{args.warps or 8} games (warps) per CTA"},
+                       "launch": f"{args.warps or 8} warps per CTA, two games per warp"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",

@@ -223,9 +223,11 @@ int gen_write_state(gen_env *env, const int16_t *h_army, const int8_t *h_owner, 
  * effect at the next reset or auto-reset; synchronous. */
 int gen_set_spawn_range(gen_env *env, int min_dist, int max_dist);
 
-/* Launch shape of this environment's step kernel: games (warps) per CTA,
- * one of 1, 2, 4, 8 that fits the shared-memory limit.  Used by the
- * autotuner; results do not depend on it. */
+/* Launch shape of this environment's step kernel: warps per CTA, one of 1,
+ * 2, 4, 8 that fits the shared-memory limit (a warp runs one game, or two or
+ * four, see gen_set_lane_groups; launches of fewer games than fill every SM
+ * once take fewer warps per CTA).  Used by the autotuner; results do not
+ * depend on it. */
 int gen_set_launch(gen_env *env, int warps_per_cta);
 
 /* Pick each size bucket's launch shape (games per CTA among 2, 4, 8) by
