@@ -73,3 +73,12 @@ def test_null_env_calls_fail_cleanly(lib):
     assert lib.gen_policy(None, 0, None, None) == -1
     assert lib.gen_set_launch(None, 8) == -1
     assert lib.gen_copy_peak(0, 1, None) == -1
+
+
+def test_null_handles_of_the_form_switches_fail_cleanly(lib):
+    """The launch-form switches refuse a NULL handle with GEN_ERR_BAD_ARG and a
+    message, on the host, before any CUDA call."""
+    for call in (lambda: lib.gen_set_lane_groups(None, 0), lambda: lib.gen_set_sample_form(None, 0),
+                 lambda: lib.gen_features_set_form(None, 0), lambda: lib.gen_set_spawn_range(None, 0, 0)):
+        assert call() == -1
+        assert lib.gen_last_error().decode()
