@@ -381,3 +381,34 @@ def test_workload_shapes_are_seeded():
     H, W, mode, P = shapes(1000, (20, 40), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=1)
     assert H.min() >= 20 and H.max() <= 40
     assert abs(np.mean(mode == 1) - 0.3) < 0.01 and set(np.unique(P)) == {2, 4, 8}
+
+
+def test_two_player_free_for_all_is_1v1():
+    """With two players a free-for-all game follows exactly the 1v1 rules
+    (Sec. III: teams exist only in 2v2; elimination ends a game of two either
+    way), so the two modes give the same maps, moves, outputs and rewards
+    frame by frame.  The GPU runs both through the same two-player kernels."""
+    G = 24
+    rng = np.random.default_rng(3)
+    H = rng.integers(4, 16, G).astype(np.int32)
+    W = rng.integers(4, 16, G).astype(np.int32)
+    kw = dict(seed=5, min_general_dist=1, n_cities=3, max_turns=60)
+    a = OracleEnv(H, W, np.zeros(G, np.int32), np.full(G, 2, np.int32), **kw)
+    b = OracleEnv(H, W, np.full(G, 2, np.int32), np.full(G, 2, np.int32), **kw)
+    resets = 0
+    for f in range(200):
+        act = a.policy(4)
+        assert np.array_equal(act, b.policy(4)), f"policy differs at frame {f}"
+        a.step(act)
+        b.step(act)
+        for g in range(G):
+            for x, y in zip(a.board(g), b.board(g)):
+                assert np.array_equal(x, y), f"board of game {g} differs at frame {f}"
+            sa, sb = a.scalars(g), b.scalars(g)
+            assert sa["reward"].tolist() == sb["reward"].tolist() and sa["done"] == sb["done"]
+            resets += sa["done"] != 0
+            for p in range(2):
+                oa, ob = a.observe(g, p), b.observe(g, p)
+                for k in oa:
+                    assert np.array_equal(oa[k], ob[k]), f"{k} of game {g} player {p} differs at frame {f}"
+    assert resets > 0, "expected finished games"
