@@ -64,6 +64,22 @@ def test_rollout_two_player_ffa_with_1v1(form):
     check_rollout(env, orc, form)
 
 
+@pytest.mark.parametrize("lanes", [1, 2], ids=["warp", "narrow"])
+@pytest.mark.parametrize("mode,P", [(0, 2), (1, 4)], ids=["1v1", "2v2"])
+@pytest.mark.parametrize("form", [0, 1, 2], ids=["resident", "graph", "launches"])
+def test_uniform_batch_rollout_matches_oracle(form, mode, P, lanes):
+    """A batch of one board shape runs the uniform-shape kernels: every frame
+    of each form against the oracle, with a warp per game and (1v1) two or
+    four games per warp."""
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    G = 64
+    kw = dict(seed=21, min_general_dist=1, n_cities=4, max_turns=30)
+    env = GeneralsEnv(12, 13, mode, P, batch=G, **kw)
+    env.set_lane_groups(lanes)
+    orc = OracleEnv(np.full(G, 12), np.full(G, 13), np.full(G, mode), np.full(G, P), **kw)
+    check_rollout(env, orc, form)
+
+
 def check_rollout(env, orc, form):
     import torch
     K = 9
@@ -169,6 +185,25 @@ def test_full_size_ragged_131072_resident_64_frames_sampled():
     env.rollout(K, 2, acts, out, log, 0)
     torch.cuda.synchronize()
     _check_sampled(env, out, K, H, W, mode, P, gen, (0, 65536 - 12, 131072 - 24), 24, 2, log)
+
+
+def test_full_size_24x24_65536_resident_64_frames_sampled():
+    """The default workload in the form the benchmark's resident figure
+    times: one 64-frame rollout of 65,536 games of one shape (four games per
+    warp); three blocks of 24 games replayed by the oracle."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import workload
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24")
+    env = GeneralsEnv(H, W, mode, P, seed=1, **gen)
+    K = 64
+    out = env.new_outputs(frames=K)
+    acts = env.new_actions()
+    log = torch.zeros(K * int(env.layout.player_slots), dtype=torch.int32, device="cuda")
+    env.policy(2, acts)
+    env.rollout(K, 2, acts, out, log, 0)
+    torch.cuda.synchronize()
+    _check_sampled(env, out, K, H, W, mode, P, gen, (0, 32768 - 12, 65536 - 24), 24, 2, log)
 
 
 def test_full_size_mixed_32768_sampled():
