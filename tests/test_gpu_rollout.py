@@ -80,6 +80,19 @@ def test_uniform_batch_rollout_matches_oracle(form, mode, P, lanes):
     check_rollout(env, orc, form)
 
 
+@pytest.mark.parametrize("form", [0, 1], ids=["resident", "graph"])
+def test_uniform_batch_rollout_two_per_warp_large_boards(form):
+    """Uniform 28x30 1v1 boards (840 cells: too many for four games per warp,
+    two per warp in multi-frame launches too) against the oracle."""
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    G = 40
+    kw = dict(seed=23, min_general_dist=2, n_cities=6, max_turns=24)
+    env = GeneralsEnv(28, 30, 0, 2, batch=G, **kw)
+    env.set_lane_groups(env.LANES_NARROW)
+    orc = OracleEnv(np.full(G, 28), np.full(G, 30), np.zeros(G), np.full(G, 2), **kw)
+    check_rollout(env, orc, form)
+
+
 def check_rollout(env, orc, form):
     import torch
     K = 9
