@@ -84,7 +84,11 @@ typedef struct gen_params {
     int32_t castle_radius;     /* > 0: a neutral castle within this many steps of every general (6) */
 } gen_params;
 
-/* Caller-provided device output buffers (sizes from gen_layout). */
+/* Device output buffers of one frame (sizes from gen_layout): the
+ * observation planes, mask, reward, scoreboard and done flags of
+ * Sections III, IV-B and IV-G.  Fields are caller-provided device pointers;
+ * where a call says so, a NULL field (or a NULL gen_outputs) selects the
+ * environment's own buffer of that output (gen_outputs_get). */
 typedef struct gen_outputs {
     int16_t *obs_army;    /* [plane_cells] army if visible else 0 */
     int8_t *obs_owner;    /* [plane_cells] owner if visible else -2 */
@@ -96,6 +100,7 @@ typedef struct gen_outputs {
     uint8_t *done;        /* [n_games] 0 running, 1 terminal, 2 truncated */
 } gen_outputs;
 
+/* Sizes of an environment's per-game arrays (see "Layout" above). */
 typedef struct gen_layout_info {
     int32_t n_games;
     int32_t player_slots;  /* sum of P_g */
@@ -105,8 +110,9 @@ typedef struct gen_layout_info {
     int32_t max_cells;     /* max N_g */
 } gen_layout_info;
 
-/* Fill *p with the defaults: seed 1, 20% mountains, 8 castles of 40..50,
- * spacing floor((H+W)/3), no truncation, auto-reset on. */
+/* Fill *p with the defaults of the Section IV-A generator: seed 1, 20%
+ * mountains, 8 castles of 40..50, spacing floor((H+W)/3), no truncation,
+ * auto-reset on. */
 int gen_default_params(gen_params *p);
 
 /* Create a uniform batch of `batch` games of H x W in `mode` (0 1v1, 1 2v2,
@@ -121,26 +127,51 @@ int gen_create_ex(gen_env **out, const gen_params *p, int batch, const int32_t *
                   const int32_t *h_mode, const int32_t *h_n_players);
 
 /* Layout sizes and, when the arrays are non-NULL, the per-game host offsets
- * (h_plane_off[g], h_player_off[g], h_npad[g], each [n_games]). */
+ * (h_plane_off[g], h_player_off[g], h_npad[g], each [n_games]).  Interface
+ * addition: the paper's per-player H x W observations (Section IV-B) and
+ * H x W x 9 actions (Section IV-G) flattened into ragged arrays. */
 int gen_layout(const gen_env *env, gen_layout_info *info, int64_t *h_plane_off, int32_t *h_player_off,
                int32_t *h_npad);
 
 /* Regenerate games (next epoch, new map, turn 0; the frame counter runs on)
  * and write their observations, masks and scoreboard into `out` (reward 0,
  * done 0).  d_game_ids: device int32 [n] of distinct local game ids (ids
- * outside [0, n_games) are skipped), or NULL for all games.  Section IV-A. */
+ * outside [0, n_games) are skipped), or NULL for all games.  Section IV-A.
+ * `out` or any of its fields may be NULL: those outputs go to the
+ * environment's own buffers (see gen_outputs_get). */
 int gen_reset(gen_env *env, const int32_t *d_game_ids, int n, const gen_outputs *out, void *stream);
 
 /* Write the current observations, masks and scoreboard of every game into
- * `out` without advancing (reward 0, done 0). */
+ * `out` without advancing (reward 0, done 0): the fogged view of Section
+ * IV-B and the legal moves of Section IV-D.  NULL `out` or fields: the
+ * environment's own buffers, as for gen_reset. */
 int gen_observe(gen_env *env, const gen_outputs *out, void *stream);
 
 /* Advance every game by one turn.  d_actions: device int32 [player_slots].
- * Writes every field of `out`.  Section IV-B..IV-E. */
+ * Writes every field of `out`.  Section IV-B..IV-E.  `out` may be NULL, or
+ * have NULL fields: those outputs go to the environment's own buffers (see
+ * gen_outputs_get), valid until the next call that writes them. */
 int gen_step(gen_env *env, const int32_t *d_actions, const gen_outputs *out, void *stream);
 
-/* gen_step, then the benchmark policy for the next step computed from the
- * new masks in the same launch: d_next_actions [player_slots] receives, per
+/* The environment's own one-frame output buffers (device pointers, every
+ * field set), which gen_step / gen_step_policy / gen_reset / gen_observe
+ * write in place of NULL output fields and gen_step_host stages through.
+ * Interface addition (the paper's environment returns its observations,
+ * Sections III and IV-B).  Allocated on first use, by this call or by the
+ * first call given a NULL field -- a synchronous cudaMalloc, so make that
+ * first call outside any stream capture; held until gen_destroy.  Their
+ * contents are those of the last call that wrote into them.
+ * GEN_ERR_OOM when the allocation fails. */
+int gen_outputs_get(gen_env *env, gen_outputs *out);
+
+/* Device bytes the environment holds now: state arenas, game tables, size
+ * buckets, and its own output and staging buffers once allocated (feature
+ * builders hold their own).  Interface addition, no counterpart in the
+ * paper: memory accounting for admission budgets. */
+int gen_device_bytes(const gen_env *env, size_t *bytes);
+
+/* gen_step (NULL outputs as there), then the benchmark policy for the
+ * next step computed from the new masks in the same launch: d_next_actions [player_slots] receives, per
  * player, a uniformly drawn legal (cell, direction) pair (row-major cells,
  * then up, down, left, right; pass when none) sent whole, or halved with
  * probability 0.2, keyed by (policy_seed, global game id, frame, player).
@@ -166,10 +197,12 @@ int gen_step_policy(gen_env *env, const int32_t *d_actions, const gen_outputs *o
 int gen_rollout(gen_env *env, int K, uint64_t policy_seed, int32_t *d_actions, const gen_outputs *out,
                 int32_t *d_action_log, int form, void *stream);
 
-/* The benchmark policy alone, from the current state of every game. */
+/* The benchmark policy alone (the uniform random legal policy of gen_step_policy,
+ * over the Section IV-G action space), from the current state of every game. */
 int gen_policy(gen_env *env, uint64_t policy_seed, int32_t *d_actions, void *stream);
 
-/* gen_step with host buffers: copies h_actions [player_slots] to the device,
+/* gen_step with host buffers (Section IV-B..IV-E step; interface addition
+ * for host-side actors): copies h_actions [player_slots] to the device,
  * steps, copies every non-NULL output of `h_out` back into host memory (same
  * sizes as the device outputs) and synchronises the stream.  When
  * h_next_actions is non-NULL the benchmark policy of gen_step_policy runs in
@@ -204,7 +237,8 @@ int gen_step_host(gen_env *env, const int32_t *h_actions, const gen_outputs *h_o
 int gen_step_host_static(gen_env *env, const int32_t *h_actions, const gen_outputs *h_out, uint64_t policy_seed,
                          int32_t *h_next_actions, void *stream);
 
-/* Copy the whole game state to host memory: h_army [state_cells] int16,
+/* Copy the whole game state of Section IV (armies, owners, cell types,
+ * per-game counters) to host memory: h_army [state_cells] int16,
  * h_owner / h_terrain [state_cells] int8 (game g at its state offset,
  * sum of Npad of earlier games), h_scalars [n_games][8] uint32 = turn,
  * frame, epoch, alive bits, finished, invalid actions, saturations, error.
@@ -213,9 +247,33 @@ int gen_read_state(gen_env *env, int16_t *h_army, int8_t *h_owner, int8_t *h_ter
                    void *stream);
 
 /* Overwrite the whole game state from host memory (same layout as
- * gen_read_state; the error word is ignored).  Synchronous on `stream`. */
+ * gen_read_state; the error word is ignored).  Every cell and counter is
+ * checked against the rules' ranges (Section IV: cell types 0..3, owners
+ * -1..P-1, armies >= 0, padding cells empty, alive bits of the game's
+ * players); GEN_ERR_BAD_ARG names the first offender.  Synchronous on
+ * `stream`. */
 int gen_write_state(gen_env *env, const int16_t *h_army, const int8_t *h_owner, const int8_t *h_terrain,
                     const uint32_t *h_scalars, void *stream);
+
+/* Save everything that determines the environment's future frames into one
+ * opaque, versioned host blob: every board (Section IV), the per-game
+ * counters (turn, frame, epoch, alive players, finished, invalid actions,
+ * saturations, error word) and the generator and episode parameters,
+ * spawn range included (Sections IV-A and V).  Interface addition for
+ * checkpoint and resume.  With h_buf NULL only *used is set (the size);
+ * else h_buf must hold cap >= that many bytes, and *used receives the size
+ * written.  Synchronous on `stream`.  Feature builders keep their own
+ * memory, which the blob does not hold. */
+int gen_save_state(gen_env *env, void *h_buf, size_t cap, size_t *used, void *stream);
+
+/* Restore a blob written by gen_save_state into an environment of the same
+ * games (same count, and per game the same H, W, mode and players), which
+ * then continues frame for frame as the saved one would have: its
+ * generator parameters, seed and spawn range are replaced by the saved
+ * ones.  The blob is checked (magic, version, sizes, a checksum, every cell
+ * and counter within the rules' ranges) before anything changes;
+ * GEN_ERR_BAD_ARG says what failed.  Synchronous on `stream`. */
+int gen_load_state(gen_env *env, const void *h_buf, size_t size, void *stream);
 
 /* Change the spawn spacing of every later map of this environment (the
  * spawn-distance curriculum of Section V raises max_dist over training):
@@ -223,14 +281,17 @@ int gen_write_state(gen_env *env, const int16_t *h_army, const int8_t *h_owner, 
  * effect at the next reset or auto-reset; synchronous. */
 int gen_set_spawn_range(gen_env *env, int min_dist, int max_dist);
 
-/* Launch shape of this environment's step kernel: warps per CTA, one of 1,
+/* Tuning call, no counterpart in the paper.  Launch shape of this
+ * environment's step kernel: warps per CTA, one of 1,
  * 2, 4, 8 that fits the shared-memory limit (a warp runs one game, or two or
  * four, see gen_set_lane_groups; launches of fewer games than fill every SM
  * once take fewer warps per CTA).  Used by the autotuner; results do not
  * depend on it. */
 int gen_set_launch(gen_env *env, int warps_per_cta);
 
-/* Pick each size bucket's launch shape (games per CTA among 2, 4, 8) by
+/* Tuning call, no counterpart in the paper (Section IV-G runs every board
+ * size in one environment; this picks how).  Pick each size bucket's launch
+ * shape (games per CTA among 2, 4, 8) by
  * timing `steps` step launches of a scratch batch with the bucket's board
  * shapes (the environment's own games do not advance).  Results are cached
  * per (padded board size class, player class, SM count) for the process.
@@ -241,7 +302,8 @@ int gen_set_launch(gen_env *env, int warps_per_cta);
  * streams. */
 int gen_autotune(gen_env *env, int steps, char *report, size_t report_cap);
 
-/* Measure copy bandwidth of this GPU with the library's own 128-bit copy
+/* Measurement call, no counterpart in the paper: the HBM roofline
+ * denominator.  Measure copy bandwidth of this GPU with the library's own 128-bit copy
  * kernel over `bytes` (rounded down to 16 B), best of `reps`; returns GB/s
  * counting read + write bytes in *gbps.  Synchronous. */
 int gen_copy_peak(size_t bytes, int reps, double *gbps);
@@ -255,7 +317,10 @@ int gen_copy_peak(size_t bytes, int reps, double *gbps);
  * it ends.  Sessions are admitted while the device bytes they need fit the
  * budget; otherwise gen_server_open waits for others to close.  Each game is
  * keyed by the global game id its session was opened with, so its results
- * do not depend on the other sessions.  Section IV rules throughout. */
+ * do not depend on the other sessions.  Section IV rules throughout.  The
+ * server calls are interface additions with no counterpart in the paper
+ * (its simulator steps one fixed batch inside the training loop, Section
+ * IV-G); each gen_server_* declaration below belongs to this addition. */
 typedef struct gen_server gen_server;
 
 typedef struct gen_server_config {
@@ -330,7 +395,6 @@ typedef struct gen_sim_config {
 /* Run a server with closed-loop simulated clients and report its stats. */
 int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_server_stats *st);
 
-/* Reason for the last failure on this thread (never NULL). */
 /* ---- policy sampling over the H x W x 9 action space (Sec. IV-G, App. C) --
  * Logits: player plane q = plane_off[g] + p * Npad_g holds 9 * Npad_g float32
  * at q * 9, entry c * 9 + k for cell c and k = 0 pass, 1..4 all-but-one up,
@@ -352,7 +416,8 @@ int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_serv
 int gen_sample_actions(gen_env *env, const float *d_logits, uint64_t seed, int32_t *d_actions, uint8_t *d_mask9,
                        void *stream);
 
-/* Games per warp in the step kernels (the results are the same): 1 = one
+/* Tuning call, no counterpart in the paper.  Games per warp in the step
+ * kernels (the results are the same): 1 = one
  * warp per game; 2 = two games per warp (four in multi-frame launches)
  * wherever the games allow it -- at most two players, boards of at most
  * 1,024 padded cells (576 for four), no spawn options; 0 (default) = as 2 for
@@ -360,8 +425,8 @@ int gen_sample_actions(gen_env *env, const float *d_logits, uint64_t seed, int32
  * launches), else 1.  GEN_ERR_BAD_ARG for NULL env or a mode outside 0..2. */
 int gen_set_lane_groups(gen_env *env, int mode);
 
-/* How gen_sample_actions spreads a game over the GPU (the results are the
- * same): 1 = one warp per game, players in turn; 2 = one CTA per game with a
+/* Tuning call, no counterpart in the paper.  How gen_sample_actions
+ * spreads a game over the GPU (the results are the same): 1 = one warp per game, players in turn; 2 = one CTA per game with a
  * warp per player (as many as fit in shared memory beside the board);
  * 0 (default) = 2.  GEN_ERR_BAD_ARG for NULL env or a form outside 0..2. */
 int gen_set_sample_form(gen_env *env, int form);
@@ -402,11 +467,12 @@ int gen_features_create(gen_features **out, gen_env *env, int hist);
  * of window int32 pairs per player.  window in [0, 4096]; 0 = none. */
 int gen_features_create_ex(gen_features **out, gen_env *env, int hist, int window);
 
-/* Channels C and the number of floats the output buffer must hold. */
+/* Channels C (24 + 2 * hist, App. A) and the number of floats the output
+ * buffer must hold. */
 int gen_features_layout(const gen_features *f, int32_t *channels, int64_t *n_floats);
 
-/* Window T and the int32 count of the temporal-token output:
- * player_slots * T * 2. */
+/* Window T (App. A temporal tokens) and the int32 count of the
+ * temporal-token output: player_slots * T * 2. */
 int gen_features_series_layout(const gen_features *f, int32_t *window, int64_t *n_ints);
 
 /* Fold the current frame into the memory and write every player's features
@@ -421,17 +487,21 @@ int gen_features_build(gen_features *f, float *d_out, void *stream);
  * builder created without a window. */
 int gen_features_build_ex(gen_features *f, float *d_out, int32_t *d_series, void *stream);
 
-/* How the builder spreads a game over the GPU (the bytes written are the
- * same): 1 = one warp per game, players in turn; 2 = one CTA per game, its
+/* Tuning call, no counterpart in the paper.  How the builder spreads a
+ * game over the GPU (the bytes written are the same): 1 = one warp per game, players in turn; 2 = one CTA per game, its
  * warps sharing the (player, 128-cell chunk) items, for batches too small to
  * fill the GPU one warp per game; 0 (default) = 2 while the batch has fewer
  * games than 16 x the SM count, else 1.  GEN_ERR_BAD_ARG outside 0..2. */
 int gen_features_set_form(gen_features *f, int form);
 
+/* Free a builder's memory (App. A feature memory). */
 void gen_features_destroy(gen_features *f);
 
+/* Reason for the last failure on this thread (never NULL).  Interface
+ * addition: error reporting of the C-ABI. */
 const char *gen_last_error(void);
 
+/* Free the environment's device state and buffers (interface addition). */
 void gen_destroy(gen_env *env);
 
 #ifdef __cplusplus

@@ -57,6 +57,7 @@ struct Bucket {
     int nw_stride = 0;
     int warp_smem = 0;
     int warps = 8;    // games (warps) per CTA
+    bool tuned = false;  // warps set by gen_set_launch or the autotuner; else chosen per launch by occupancy
     int max_ctas = 0;
 };
 
@@ -102,6 +103,7 @@ struct gen_env {
     // cached rollout graph
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
+    size_t dev_bytes = 0;  // device memory this environment holds (gen_device_bytes)
 };
 
 namespace {
@@ -109,6 +111,7 @@ namespace {
 void free_env(gen_env* e) {
     if (!e) return;
     if (e->graph) cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;
     for (auto s : e->side) cudaStreamDestroy(s);
     for (auto v : e->join) cudaEventDestroy(v);
     if (e->fork) cudaEventDestroy(e->fork);
@@ -135,6 +138,22 @@ void free_env(gen_env* e) {
         cudaFree(e->d_out.done);
     }
     delete e;
+}
+
+// cudaMalloc that counts the bytes against the environment
+template <class T>
+cudaError_t dev_alloc(gen_env* e, T** p, size_t bytes) {
+    const cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (ce == cudaSuccess) e->dev_bytes += bytes;
+    return ce;
+}
+
+// A cached rollout graph holds kernel arguments captured by value (seed,
+// generator parameters, launch shapes): drop it whenever one of them changes.
+void drop_graph(gen_env* e) {
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;
+    e->graph_key.clear();
 }
 
 int check_params(const gen_params* p) {
@@ -230,7 +249,7 @@ void set_outputs(KArgs& a, const gen_outputs* o) {
 }
 
 int launch_one(const Bucket& b, const KArgs& a, void* stream, const char* what) {
-    const int rc = gk::launch_step(a, b.warps, b.max_ctas, stream);
+    const int rc = gk::launch_step(a, b.tuned ? b.warps : 0, b.max_ctas, stream);
     if (rc != 0) return cuda_fail((cudaError_t)rc, what);
     return GEN_OK;
 }
@@ -268,21 +287,60 @@ int players_for(int mode, int n_players) {
     return n_players;
 }
 
+// The environment's own output buffers (one frame) and action staging,
+// allocated on first use: all of them or none.
 int ensure_internal_outputs(gen_env* e) {
     if (e->have_out) return GEN_OK;
-    gen_outputs& o = e->d_out;
     const size_t pc = (size_t)e->plane_cells, ps = (size_t)e->player_slots;
-    CUDA_TRY(cudaMalloc(&o.obs_army, pc * 2), "cudaMalloc obs_army");
-    CUDA_TRY(cudaMalloc(&o.obs_owner, pc), "cudaMalloc obs_owner");
-    CUDA_TRY(cudaMalloc(&o.obs_terrain, pc), "cudaMalloc obs_terrain");
-    CUDA_TRY(cudaMalloc(&o.obs_vis, pc), "cudaMalloc obs_vis");
-    CUDA_TRY(cudaMalloc(&o.mask, pc), "cudaMalloc mask");
-    CUDA_TRY(cudaMalloc(&o.reward, ps * 4), "cudaMalloc reward");
-    CUDA_TRY(cudaMalloc(&o.scoreboard, ps * 8), "cudaMalloc scoreboard");
-    CUDA_TRY(cudaMalloc(&o.done, (size_t)e->G), "cudaMalloc done");
-    CUDA_TRY(cudaMalloc(&e->d_actions, ps * 4), "cudaMalloc actions");
+    const size_t bytes[9] = {pc * 2, pc, pc, pc, pc, ps * 4, ps * 8, (size_t)e->G, ps * 4};
+    void* p[9] = {};
+    cudaError_t ce = cudaSuccess;
+    size_t total = 0;
+    for (int i = 0; i < 9 && ce == cudaSuccess; ++i) {
+        ce = cudaMalloc(&p[i], bytes[i]);
+        total += bytes[i];
+    }
+    if (ce != cudaSuccess) {
+        for (void* x : p) cudaFree(x);
+        return ce == cudaErrorMemoryAllocation ? fail(GEN_ERR_OOM, "device allocation of the output buffers failed")
+                                               : cuda_fail(ce, "cudaMalloc outputs");
+    }
+    gen_outputs& o = e->d_out;
+    o.obs_army = static_cast<int16_t*>(p[0]);
+    o.obs_owner = static_cast<int8_t*>(p[1]);
+    o.obs_terrain = static_cast<int8_t*>(p[2]);
+    o.obs_vis = static_cast<uint8_t*>(p[3]);
+    o.mask = static_cast<uint8_t*>(p[4]);
+    o.reward = static_cast<float*>(p[5]);
+    o.scoreboard = static_cast<int32_t*>(p[6]);
+    o.done = static_cast<uint8_t*>(p[7]);
+    e->d_actions = static_cast<int32_t*>(p[8]);
+    e->dev_bytes += total;
     e->have_out = true;
     return GEN_OK;
+}
+
+// The outputs a call writes: the caller's buffers, with the environment's
+// own buffers in place of every NULL field (of every field when out is NULL).
+int resolve_outputs(gen_env* e, const gen_outputs* out, gen_outputs* res) {
+    const gen_outputs none{};
+    const gen_outputs& o = out ? *out : none;
+    const bool need = !o.obs_army || !o.obs_owner || !o.obs_terrain || !o.obs_vis || !o.mask || !o.reward ||
+                      !o.scoreboard || !o.done;
+    if (need) {
+        const int rc = ensure_internal_outputs(e);
+        if (rc) return rc;
+    }
+    const gen_outputs& d = e->d_out;
+    res->obs_army = o.obs_army ? o.obs_army : d.obs_army;
+    res->obs_owner = o.obs_owner ? o.obs_owner : d.obs_owner;
+    res->obs_terrain = o.obs_terrain ? o.obs_terrain : d.obs_terrain;
+    res->obs_vis = o.obs_vis ? o.obs_vis : d.obs_vis;
+    res->mask = o.mask ? o.mask : d.mask;
+    res->reward = o.reward ? o.reward : d.reward;
+    res->scoreboard = o.scoreboard ? o.scoreboard : d.scoreboard;
+    res->done = o.done ? o.done : d.done;
+    return check_outputs(res);
 }
 
 // Size class of a game: padded cells rounded up to a class edge, players
@@ -322,7 +380,7 @@ int build_buckets(gen_env* e) {
         i = j;
     }
     if (e->buckets.size() > 1) {
-        CUDA_TRY(cudaMalloc(&e->d_order, sizeof(int32_t) * (size_t)e->G), "cudaMalloc order");
+        CUDA_TRY(dev_alloc(e, &e->d_order, sizeof(int32_t) * (size_t)e->G), "cudaMalloc order");
         CUDA_TRY(cudaMemcpy(e->d_order, order.data(), sizeof(int32_t) * (size_t)e->G, cudaMemcpyHostToDevice),
                  "upload order");
         CUDA_TRY(cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming), "event");
@@ -437,11 +495,11 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
     }
 
     cudaError_t ce;
-    if ((ce = cudaMalloc(&e->d_info, sizeof(GameInfo) * (size_t)batch)) != cudaSuccess ||
-        (ce = cudaMalloc(&e->d_scal, sizeof(GameScalars) * (size_t)batch)) != cudaSuccess ||
-        (ce = cudaMalloc(&e->d_army, 2 * (size_t)cell)) != cudaSuccess ||
-        (ce = cudaMalloc(&e->d_owner, (size_t)cell)) != cudaSuccess ||
-        (ce = cudaMalloc(&e->d_terrain, (size_t)cell)) != cudaSuccess) {
+    if ((ce = dev_alloc(e, &e->d_info, sizeof(GameInfo) * (size_t)batch)) != cudaSuccess ||
+        (ce = dev_alloc(e, &e->d_scal, sizeof(GameScalars) * (size_t)batch)) != cudaSuccess ||
+        (ce = dev_alloc(e, &e->d_army, 2 * (size_t)cell)) != cudaSuccess ||
+        (ce = dev_alloc(e, &e->d_owner, (size_t)cell)) != cudaSuccess ||
+        (ce = dev_alloc(e, &e->d_terrain, (size_t)cell)) != cudaSuccess) {
         free_env(e);
         return ce == cudaErrorMemoryAllocation ? fail(GEN_ERR_OOM, "device allocation failed")
                                                : cuda_fail(ce, "cudaMalloc");
@@ -490,13 +548,15 @@ int gen_layout(const gen_env* e, gen_layout_info* info, int64_t* h_plane_off, in
     return GEN_OK;
 }
 
-int gen_reset(gen_env* e, const int32_t* d_game_ids, int n, const gen_outputs* out, void* stream) {
+int gen_reset(gen_env* e, const int32_t* d_game_ids, int n, const gen_outputs* out_arg, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    int rc = check_outputs(out);
+    if (d_game_ids && (n < 0 || n > e->G)) return fail(GEN_ERR_BAD_ARG, "reset count %d outside [0, %d]", n, e->G);
+    gen_outputs res;
+    int rc = resolve_outputs(e, out_arg, &res);
     if (rc) return rc;
+    const gen_outputs* out = &res;
     if (!d_game_ids)
         return launch_buckets(e, gk::OP_RESET, [&](KArgs& a) { set_outputs(a, out); }, stream, "reset launch");
-    if (n < 0 || n > e->G) return fail(GEN_ERR_BAD_ARG, "reset count %d outside [0, %d]", n, e->G);
     KArgs a = base_args(e, e->all, gk::OP_RESET);
     a.list = d_game_ids;
     a.n_items = n;
@@ -504,19 +564,37 @@ int gen_reset(gen_env* e, const int32_t* d_game_ids, int n, const gen_outputs* o
     return launch_one(e->all, a, stream, "reset launch");
 }
 
-int gen_observe(gen_env* e, const gen_outputs* out, void* stream) {
+int gen_observe(gen_env* e, const gen_outputs* out_arg, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    int rc = check_outputs(out);
+    gen_outputs res;
+    int rc = resolve_outputs(e, out_arg, &res);
     if (rc) return rc;
+    const gen_outputs* out = &res;
     return launch_buckets(e, gk::OP_OBSERVE, [&](KArgs& a) { set_outputs(a, out); }, stream, "observe launch");
 }
 
-int gen_step_policy(gen_env* e, const int32_t* d_actions, const gen_outputs* out, uint64_t policy_seed,
+int gen_outputs_get(gen_env* e, gen_outputs* out) {
+    if (!e || !out) return fail(GEN_ERR_BAD_ARG, "env or out is NULL");
+    const int rc = ensure_internal_outputs(e);
+    if (rc) return rc;
+    *out = e->d_out;
+    return GEN_OK;
+}
+
+int gen_device_bytes(const gen_env* e, size_t* bytes) {
+    if (!e || !bytes) return fail(GEN_ERR_BAD_ARG, "env or bytes is NULL");
+    *bytes = e->dev_bytes;
+    return GEN_OK;
+}
+
+int gen_step_policy(gen_env* e, const int32_t* d_actions, const gen_outputs* out_arg, uint64_t policy_seed,
                     int32_t* d_next_actions, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
-    int rc = check_outputs(out);
+    gen_outputs res;
+    int rc = resolve_outputs(e, out_arg, &res);
     if (rc) return rc;
+    const gen_outputs* out = &res;
     return launch_buckets(e, gk::OP_STEP,
                           [&](KArgs& a) {
                               a.actions = d_actions;
@@ -547,6 +625,7 @@ int gen_rollout(gen_env* e, int K, uint64_t policy_seed, int32_t* d_actions, con
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (K < 1) return fail(GEN_ERR_BAD_ARG, "K = %d < 1", K);
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
+    // K frames of outputs: the environment's own buffers hold one, so every field is the caller's
     int rc = check_outputs(out);
     if (rc) return rc;
     if (impl == GEN_ROLLOUT_RESIDENT) {
@@ -662,7 +741,7 @@ static int step_host_pipelined(gen_env* e, const gen_outputs& h, uint64_t policy
     if (!e->d_iota) {
         std::vector<int32_t> iota((size_t)e->G);
         for (int g = 0; g < e->G; ++g) iota[(size_t)g] = g;
-        CUDA_TRY(cudaMalloc(&e->d_iota, sizeof(int32_t) * (size_t)e->G), "cudaMalloc game ids");
+        CUDA_TRY(dev_alloc(e, &e->d_iota, sizeof(int32_t) * (size_t)e->G), "cudaMalloc game ids");
         CUDA_TRY(cudaMemcpy(e->d_iota, iota.data(), sizeof(int32_t) * (size_t)e->G, cudaMemcpyHostToDevice),
                  "upload game ids");
         CUDA_TRY(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking), "copy stream");
@@ -743,17 +822,42 @@ __device__ __align__(256) unsigned char g_static_stage[kStaticStageBytes];
 constexpr int kMaxStageDevices = 64;
 std::mutex g_stage_mu;
 unsigned char* g_stage_addr[kMaxStageDevices] = {};
+void* g_stage_ctx[kMaxStageDevices] = {};
 
+// The calling thread's current CUDA context (a driver handle), or NULL when
+// it cannot be read.  Read through the runtime's driver entry-point lookup,
+// so the library needs no link to the driver library.
+void* current_context() {
+    using CtxGetCurrent = int (*)(void**);
+    static const CtxGetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return static_cast<CtxGetCurrent>(nullptr);
+        return reinterpret_cast<CtxGetCurrent>(f);
+    }();
+    void* ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of the staging array on the current device.  Looked up
+// once per device with that device current, and again whenever the device's
+// context has changed since (cudaDeviceReset recreates it and the module,
+// and the array may then sit elsewhere).
 int static_stage(unsigned char** out) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kMaxStageDevices) return fail(GEN_ERR_BAD_ARG, "device %d beyond %d", dev, kMaxStageDevices);
     std::lock_guard<std::mutex> lk(g_stage_mu);
-    if (!g_stage_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_stage_addr[dev] || !ctx || ctx != g_stage_ctx[dev]) {
         void* p = nullptr;
         const cudaError_t ce = cudaGetSymbolAddress(&p, g_static_stage);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetSymbolAddress(static stage)");
         g_stage_addr[dev] = static_cast<unsigned char*>(p);
+        g_stage_ctx[dev] = current_context();
     }
     *out = g_stage_addr[dev];
     return GEN_OK;
@@ -817,10 +921,14 @@ int gen_step_host_static(gen_env* e, const int32_t* h_actions, const gen_outputs
     return GEN_OK;
 }
 
-int gen_read_state(gen_env* e, int16_t* h_army, int8_t* h_owner, int8_t* h_terrain, uint32_t* h_scalars,
-                   void* stream) {
-    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Host state of every game in the public layout (terrain bits 0-1 only);
+// synchronous on s.
+int read_state_into(gen_env* e, int16_t* h_army, int8_t* h_owner, int8_t* h_terrain, uint32_t* h_scalars,
+                    cudaStream_t s) {
     const size_t n = (size_t)e->state_cells;
     if (h_army) CUDA_TRY(cudaMemcpyAsync(h_army, e->d_army, 2 * n, cudaMemcpyDeviceToHost, s), "read army");
     if (h_owner) CUDA_TRY(cudaMemcpyAsync(h_owner, e->d_owner, n, cudaMemcpyDeviceToHost, s), "read owner");
@@ -835,10 +943,10 @@ int gen_read_state(gen_env* e, int16_t* h_army, int8_t* h_owner, int8_t* h_terra
     return GEN_OK;
 }
 
-int gen_write_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, const int8_t* h_terrain,
-                    const uint32_t* h_scalars, void* stream) {
-    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    if (!h_army || !h_owner || !h_terrain || !h_scalars) return fail(GEN_ERR_BAD_ARG, "host buffers are NULL");
+// Every game's state within the rules' ranges (Section IV: cell types,
+// owners, armies; alive bits of the game's players).
+int validate_state(const gen_env* e, const int16_t* h_army, const int8_t* h_owner, const int8_t* h_terrain,
+                   const uint32_t* h_scalars) {
     for (int g = 0; g < e->G; ++g) {
         const GameInfo& gi = e->h_info[(size_t)g];
         const uint32_t* sc = h_scalars + 8 * (size_t)g;
@@ -854,32 +962,188 @@ int gen_write_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, co
                             h_terrain[k], h_owner[k], h_army[k]);
         }
     }
-    cudaStream_t s = (cudaStream_t)stream;
+    return GEN_OK;
+}
+
+// Upload validated host state, then recompute the per-map cached bits;
+// synchronous on s.  keep_err: restore the error words as given (else 0).
+int upload_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, const int8_t* h_terrain,
+                 const uint32_t* h_scalars, bool keep_err, cudaStream_t s) {
     const size_t n = (size_t)e->state_cells;
     std::vector<GameScalars> sc((size_t)e->G);
     memcpy(sc.data(), h_scalars, sizeof(GameScalars) * (size_t)e->G);
-    for (auto& x : sc) x.err = 0;
+    if (!keep_err)
+        for (auto& x : sc) x.err = 0;
     CUDA_TRY(cudaMemcpyAsync(e->d_army, h_army, 2 * n, cudaMemcpyHostToDevice, s), "write army");
     CUDA_TRY(cudaMemcpyAsync(e->d_owner, h_owner, n, cudaMemcpyHostToDevice, s), "write owner");
     CUDA_TRY(cudaMemcpyAsync(e->d_terrain, h_terrain, n, cudaMemcpyHostToDevice, s), "write terrain");
     CUDA_TRY(cudaMemcpyAsync(e->d_scal, sc.data(), sizeof(GameScalars) * (size_t)e->G, cudaMemcpyHostToDevice, s),
              "write scalars");
-    int rc = launch_buckets(e, gk::OP_DERIVE, [](KArgs&) {}, stream, "derive launch");
+    int rc = launch_buckets(e, gk::OP_DERIVE, [](KArgs&) {}, s, "derive launch");
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(s), "write_state sync");
     return GEN_OK;
+}
+
+// ---- saved-state blob --------------------------------------------------
+// Header (kBlobHeader bytes), then per game int32 H, W, mode, players; army
+// int16 [state_cells]; owner int8 [state_cells]; terrain int8 [state_cells]
+// (cell type only); scalars uint32 [n_games][8].  Host byte order.
+constexpr char kBlobMagic[8] = {'G', 'E', 'N', 'S', 'T', 'A', 'T', 'E'};
+constexpr uint32_t kBlobVersion = 1;
+
+struct BlobHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    uint64_t total_bytes;
+    uint64_t checksum;  // FNV-1a 64 of every byte after the header
+    int32_t n_games;
+    int32_t player_slots;
+    int64_t state_cells;
+    gen_params params;  // generator and episode parameters, spawn range included
+};
+
+size_t blob_bytes(const gen_env* e) {
+    const size_t G = (size_t)e->G, n = (size_t)e->state_cells;
+    return sizeof(BlobHeader) + 16 * G + 4 * n + sizeof(GameScalars) * G;
+}
+
+// FNV-1a, 64-bit (Fowler, Noll, Vo)
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ULL;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+// Per-game derived fields of the game table from the parameters.
+void apply_params(gen_env* e, const gen_params& p) {
+    e->prm = p;
+    for (size_t g = 0; g < e->h_info.size(); ++g) {
+        GameInfo& gi = e->h_info[g];
+        gi.game_id = p.game_id_base + (uint64_t)g;
+        const int nc = p.n_cities >= 0 ? p.n_cities : (int)(((int64_t)gi.N * p.city_per_mille) / 1000);
+        gi.n_cities = (int16_t)nc;
+        const int d = p.min_general_dist >= 1 ? p.min_general_dist : (gi.H + gi.W) / 3;
+        gi.dmin = (int16_t)(d < 1 ? 1 : d);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int gen_read_state(gen_env* e, int16_t* h_army, int8_t* h_owner, int8_t* h_terrain, uint32_t* h_scalars,
+                   void* stream) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    return read_state_into(e, h_army, h_owner, h_terrain, h_scalars, (cudaStream_t)stream);
+}
+
+int gen_write_state(gen_env* e, const int16_t* h_army, const int8_t* h_owner, const int8_t* h_terrain,
+                    const uint32_t* h_scalars, void* stream) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (!h_army || !h_owner || !h_terrain || !h_scalars) return fail(GEN_ERR_BAD_ARG, "host buffers are NULL");
+    int rc = validate_state(e, h_army, h_owner, h_terrain, h_scalars);
+    if (rc) return rc;
+    return upload_state(e, h_army, h_owner, h_terrain, h_scalars, false, (cudaStream_t)stream);
+}
+
+int gen_save_state(gen_env* e, void* h_buf, size_t cap, size_t* used, void* stream) {
+    if (!e || !used) return fail(GEN_ERR_BAD_ARG, "env or used is NULL");
+    const size_t need = blob_bytes(e);
+    *used = need;
+    if (!h_buf) return GEN_OK;  // size query
+    if (cap < need) return fail(GEN_ERR_BAD_ARG, "buffer of %zu bytes; the saved state needs %zu", cap, need);
+    const size_t G = (size_t)e->G, n = (size_t)e->state_cells;
+    unsigned char* b = static_cast<unsigned char*>(h_buf);
+    unsigned char* shapes = b + sizeof(BlobHeader);
+    int16_t* army = reinterpret_cast<int16_t*>(shapes + 16 * G);
+    int8_t* owner = reinterpret_cast<int8_t*>(shapes + 16 * G + 2 * n);
+    int8_t* terrain = owner + n;
+    unsigned char* scal = reinterpret_cast<unsigned char*>(terrain + n);
+    // army sits at an even offset (header and shapes are multiples of 16 bytes)
+    static_assert(sizeof(BlobHeader) % 16 == 0, "blob sections stay aligned");
+    std::vector<uint32_t> sc(8 * G);
+    int rc = read_state_into(e, army, owner, terrain, sc.data(), (cudaStream_t)stream);
+    if (rc) return rc;
+    memcpy(scal, sc.data(), sizeof(uint32_t) * 8 * G);
+    for (size_t g = 0; g < G; ++g) {
+        const GameInfo& gi = e->h_info[g];
+        const int32_t v[4] = {gi.H, gi.W, gi.mode, gi.P};
+        memcpy(shapes + 16 * g, v, 16);
+    }
+    BlobHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kBlobMagic, 8);
+    h.version = kBlobVersion;
+    h.header_bytes = (uint32_t)sizeof(BlobHeader);
+    h.total_bytes = need;
+    h.n_games = e->G;
+    h.player_slots = e->player_slots;
+    h.state_cells = e->state_cells;
+    h.params = e->prm;
+    h.checksum = fnv1a64(b + sizeof(BlobHeader), need - sizeof(BlobHeader));
+    memcpy(b, &h, sizeof(h));
+    return GEN_OK;
+}
+
+int gen_load_state(gen_env* e, const void* h_buf, size_t size, void* stream) {
+    if (!e || !h_buf) return fail(GEN_ERR_BAD_ARG, "env or buffer is NULL");
+    if (size < sizeof(BlobHeader)) return fail(GEN_ERR_BAD_ARG, "saved state of %zu bytes is truncated", size);
+    const unsigned char* b = static_cast<const unsigned char*>(h_buf);
+    BlobHeader h;
+    memcpy(&h, b, sizeof(h));
+    if (memcmp(h.magic, kBlobMagic, 8) != 0) return fail(GEN_ERR_BAD_ARG, "not a saved environment state");
+    if (h.version != kBlobVersion || h.header_bytes != sizeof(BlobHeader))
+        return fail(GEN_ERR_BAD_ARG, "saved-state version %u (header %u bytes); this library reads version %u",
+                    h.version, h.header_bytes, kBlobVersion);
+    const size_t need = blob_bytes(e);
+    if (h.n_games != e->G || h.state_cells != e->state_cells || h.player_slots != e->player_slots ||
+        h.total_bytes != need || size < need)
+        return fail(GEN_ERR_BAD_ARG, "saved state of %d games / %lld cells (%zu bytes) does not fit this environment "
+                    "(%d games / %lld cells, %zu bytes)", h.n_games, (long long)h.state_cells, size, e->G,
+                    (long long)e->state_cells, need);
+    if (fnv1a64(b + sizeof(BlobHeader), need - sizeof(BlobHeader)) != h.checksum)
+        return fail(GEN_ERR_BAD_ARG, "saved state is corrupt (checksum mismatch)");
+    const size_t G = (size_t)e->G, n = (size_t)e->state_cells;
+    const unsigned char* shapes = b + sizeof(BlobHeader);
+    for (size_t g = 0; g < G; ++g) {
+        int32_t v[4];
+        memcpy(v, shapes + 16 * g, 16);
+        const GameInfo& gi = e->h_info[g];
+        if (v[0] != gi.H || v[1] != gi.W || v[2] != gi.mode || v[3] != gi.P)
+            return fail(GEN_ERR_BAD_ARG, "game %zu: saved %dx%d mode %d with %d players, environment %dx%d mode %d "
+                        "with %d players", g, v[0], v[1], v[2], v[3], gi.H, gi.W, gi.mode, gi.P);
+    }
+    int rc = check_params(&h.params);
+    if (rc) return rc;
+    // copies: the blob need not be aligned for int16 / uint32 access
+    std::vector<int16_t> army(n);
+    std::vector<uint32_t> sc(8 * G);
+    memcpy(army.data(), shapes + 16 * G, 2 * n);
+    const int8_t* owner = reinterpret_cast<const int8_t*>(shapes + 16 * G + 2 * n);
+    const int8_t* terrain = owner + n;
+    memcpy(sc.data(), terrain + n, sizeof(uint32_t) * 8 * G);
+    if ((rc = validate_state(e, army.data(), owner, terrain, sc.data())) != GEN_OK) return rc;
+    drop_graph(e);
+    apply_params(e, h.params);
+    CUDA_TRY(cudaMemcpy(e->d_info, e->h_info.data(), sizeof(GameInfo) * G, cudaMemcpyHostToDevice),
+             "upload game table");
+    return upload_state(e, army.data(), owner, terrain, sc.data(), true, (cudaStream_t)stream);
 }
 
 int gen_set_spawn_range(gen_env* e, int min_dist, int max_dist) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (max_dist < 0 || max_dist > 32767 || min_dist > 32767)
         return fail(GEN_ERR_BAD_ARG, "spawn range [%d, %d] invalid", min_dist, max_dist);
-    e->prm.min_general_dist = min_dist;
-    e->prm.max_general_dist = max_dist;
-    for (auto& gi : e->h_info) {
-        const int d = min_dist >= 1 ? min_dist : (gi.H + gi.W) / 3;
-        gi.dmin = (int16_t)(d < 1 ? 1 : d);
-    }
+    drop_graph(e);
+    gen_params p = e->prm;
+    p.min_general_dist = min_dist;
+    p.max_general_dist = max_dist;
+    apply_params(e, p);
     CUDA_TRY(cudaMemcpy(e->d_info, e->h_info.data(), sizeof(GameInfo) * (size_t)e->G, cudaMemcpyHostToDevice),
              "upload game table");
     return GEN_OK;
@@ -1020,6 +1284,7 @@ int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t
 int gen_set_lane_groups(gen_env* e, int mode) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (mode < 0 || mode > 2) return fail(GEN_ERR_BAD_ARG, "mode %d outside [0, 2]", mode);
+    drop_graph(e);
     e->lane_groups = mode;
     return GEN_OK;
 }
@@ -1039,8 +1304,10 @@ int gen_set_launch(gen_env* e, int warps_per_cta) {
         if (warps_per_cta * b.warp_smem > kMaxSmemPerCta)
             return fail(GEN_ERR_BAD_ARG, "%d warps need %d bytes of shared memory", warps_per_cta,
                         warps_per_cta * b.warp_smem);
+    drop_graph(e);
     for (auto& b : e->buckets) {
         b.warps = warps_per_cta;
+        b.tuned = true;
         int rc = shape_bucket(b);
         if (rc) return rc;
     }
@@ -1053,6 +1320,7 @@ int gen_autotune(gen_env* e, int steps, char* report, size_t report_cap) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    drop_graph(e);
     std::string rep;
     char line[256];
     for (size_t bi = 0; bi < e->buckets.size(); ++bi) {
@@ -1064,6 +1332,7 @@ int gen_autotune(gen_env* e, int steps, char* report, size_t report_cap) {
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) {
                 b.warps = it->second;
+                b.tuned = true;
                 int rc = shape_bucket(b);
                 if (rc) return rc;
                 snprintf(line, sizeof(line), "bucket %zu (%d games, <=%d cells, <=%d players): %d warps/CTA (cached)\n",
@@ -1123,6 +1392,7 @@ int gen_autotune(gen_env* e, int steps, char* report, size_t report_cap) {
         cudaError_t ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
         b.warps = best_w;
+        b.tuned = true;
         if ((rc = shape_bucket(b)) != GEN_OK) return rc;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -32,7 +32,9 @@
 
 #include <atomic>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "gk_internal.h"
 
@@ -116,7 +118,7 @@ struct Smem {
     uint32_t* colL;    // last column
     uint32_t* vis;     // [pmax][stride]
     uint32_t* tmp;
-    uint64_t* legal;   // [pmax][chunks]: bit 4j+d = move of chunk cell j towards d is legal
+    uint8_t* cnt;      // [pmax][chunks]: legal (cell, direction) pairs of the player in the chunk
     int32_t* misc;     // [0..7] general cells, [8..15] land, [16..23] army
     int stride;
 };
@@ -140,8 +142,8 @@ __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
     w += pm * st;
     s.tmp = w;
     w += st;
-    s.legal = reinterpret_cast<uint64_t*>(w);  // 8-byte aligned: every region above is
-    w += (2 * pm * (np >> 4) + 3) & ~3;
+    s.cnt = reinterpret_cast<uint8_t*>(w);
+    w += ((pm * (np >> 4) + 15) & ~15) >> 2;  // whole 16-byte units
     s.misc = reinterpret_cast<int32_t*>(w);
     s.stride = st;
     return s;
@@ -963,6 +965,24 @@ __device__ __forceinline__ uint32_t nibbles16(uint32_t x) {
     return (y | (y >> 8)) & 0xFFFFu;
 }
 
+// Legal moves of player p in chunk ch as 64 bits, 4 per cell in (cell,
+// direction) order: the player owns the cell, it holds at least 2, and the
+// neighbour towards the direction is passable.  The caller knows the player
+// is alive and the game running.
+__device__ __forceinline__ uint64_t chunk_legal64(const Smem& s, int p, int ch) {
+    const int c0 = ch << 4;
+    const int wi = c0 >> 5, sh = c0 & 16;
+    const uint32_t mv = ((s.own[p * s.stride + wi] & s.big[wi]) >> sh) & 0xFFFFu;
+    const uint4 T = *reinterpret_cast<const uint4*>(s.terrain + c0);
+    const uint32_t tw[4] = {T.x, T.y, T.z, T.w};
+    uint32_t nib[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nib[k] = ((tw[k] >> 2) & 0x0F0F0F0Fu) & (spread4((mv >> (4 * k)) & 15u) * 0x0Fu);
+    const uint32_t lo = nibbles16(nib[0]) | (nibbles16(nib[1]) << 16);
+    const uint32_t hi = nibbles16(nib[2]) | (nibbles16(nib[3]) << 16);
+    return ((uint64_t)hi << 32) | lo;
+}
+
 // ---- observation + mask chunks of 16 cells (Sec. IV-B, App. A, Sec. IV-G) --
 // WRITE: store the planes; COUNT: legal (cell, direction) pairs per chunk.
 template <bool WRITE, bool COUNT, int LW>
@@ -988,10 +1008,9 @@ __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32
             om[k] = dpb & (spread4((mv >> (4 * k)) & 15u) * 0xFFu);
         }
         if (COUNT) {
-            // the chunk's legal moves as 64 bits: 4 per cell in (cell, direction) order
-            const uint32_t lo = nibbles16(om[0]) | (nibbles16(om[1]) << 16);
-            const uint32_t hi = nibbles16(om[2]) | (nibbles16(om[3]) << 16);
-            s.legal[p * nch + ch] = ((uint64_t)hi << 32) | lo;
+            // legal (cell, direction) pairs of the chunk: the low nibble of each mask byte
+            s.cnt[p * nch + ch] = (uint8_t)(__popc(om[0] & 0x0F0F0F0Fu) + __popc(om[1] & 0x0F0F0F0Fu) +
+                                            __popc(om[2] & 0x0F0F0F0Fu) + __popc(om[3] & 0x0F0F0F0Fu));
         }
         if (WRITE) {
             const uint32_t vis16 = (s.vis[p * st + wi] >> sh) & 0xFFFFu;
@@ -1042,7 +1061,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, const Grp<LW>& t)
 }
 
 // ---- benchmark policy: uniform legal (cell, direction), split p = 0.2 -------
-// Needs the chunk masks of output_pass<*, true>.  Players are scanned two at
+// Needs the chunk counts of output_pass<*, true>.  Players are scanned two at
 // a time (16-bit counts packed in one 32-bit warp scan: a board has at most
 // 4 x 4096 legal pairs); the lane holding pair j walks its chunks and selects
 // the bit by popcount bisection.
@@ -1065,9 +1084,8 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
     for (int p0 = 0; p0 < g.P; p0 += 2) {
         uint32_t mine = 0;
         for (int c = c_lo; c < c_hi; ++c) {
-            const uint64_t m0 = s.legal[p0 * nch + c];
-            mine += __popcll(m0);
-            if (p0 + 1 < g.P) mine += (uint32_t)__popcll(s.legal[(p0 + 1) * nch + c]) << 16;
+            mine += s.cnt[p0 * nch + c];
+            if (p0 + 1 < g.P) mine += (uint32_t)s.cnt[(p0 + 1) * nch + c] << 16;
         }
         const uint32_t incl2 = warp_incl_scan(mine, t);
         const uint32_t total2 = t.shfl(incl2, LW - 1);
@@ -1085,12 +1103,12 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
                 if (t.lane == L) {
                     uint32_t jj = j - (incl - ((mine >> (16 * q)) & 0xFFFFu));
                     for (int c = c_lo; c < c_hi; ++c) {
-                        const uint64_t m = s.legal[p * nch + c];
-                        const uint32_t n = (uint32_t)__popcll(m);
+                        const uint32_t n = s.cnt[p * nch + c];
                         if (jj >= n) {
                             jj -= n;
                             continue;
                         }
+                        const uint64_t m = chunk_legal64(s, p, c);
                         uint32_t x = (uint32_t)m;
                         int bit = 0;
                         const uint32_t nlo = __popc(x);
@@ -1425,20 +1443,32 @@ __global__ void k_copy(const uint4* __restrict__ src, uint4* __restrict__ dst, s
     for (; i < n; i += stride) __stcs(dst + i, __ldcs(src + i));
 }
 
+// Every step-kernel instantiation may take up to the per-CTA maximum of
+// dynamic shared memory on the current device: set once per device, so no
+// launch shape needs its own opt-in (the limit gates launches only).
+int allow_max_smem() {
+    static SmemLimit limit;
+    const void* fns[14] = {
+        (const void*)k_generals<false, false, 32, false>, (const void*)k_generals<true, false, 32, false>,
+        (const void*)k_generals<false, false, 32, true>,  (const void*)k_generals<true, false, 32, true>,
+        (const void*)k_generals<false, false, 16, false>, (const void*)k_generals<true, false, 16, false>,
+        (const void*)k_generals<false, false, 16, true>,  (const void*)k_generals<true, false, 16, true>,
+        (const void*)k_generals<false, false, 8, false>,  (const void*)k_generals<true, false, 8, false>,
+        (const void*)k_generals<false, false, 8, true>,   (const void*)k_generals<true, false, 8, true>,
+        (const void*)k_generals<false, true, 32, false>,  (const void*)k_generals<true, true, 32, false>};
+    return limit.raise(fns, 14, 227 * 1024);
+}
+
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
     int nw = (npad_max + 31) / 32;
     nw = (nw + 1) & ~1;  // even: the carve stays a multiple of 16 bytes
     if (nw_stride) *nw_stride = nw;
-    const int legal_words = (2 * pmax * (npad_max >> 4) + 3) & ~3;
-    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + 4 * legal_words + 4 * 24;
+    const int cnt_bytes = (pmax * (npad_max >> 4) + 15) & ~15;
+    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + cnt_bytes + 4 * 24;
 }
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
-    static SmemLimit limit;  // per device, only ever raised
-    const void* fns[6] = {(const void*)k_generals<false, false, 32, false>, (const void*)k_generals<true, false, 32, false>,
-                          (const void*)k_generals<false, false, 32, true>,  (const void*)k_generals<true, false, 32, true>,
-                          (const void*)k_generals<false, true, 32, false>,  (const void*)k_generals<true, true, 32, false>};
-    cudaError_t e = (cudaError_t)limit.raise(fns, 6, smem_bytes);
+    cudaError_t e = (cudaError_t)allow_max_smem();
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0, dev = 0, sms = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_generals<false, false, 32, false>, 32 * warps_per_cta,
@@ -1465,19 +1495,74 @@ int init_tables() {
     return 0;
 }
 
+// Resident CTAs of kernel f per SM for a launch shape, from the occupancy
+// calculator; cached per (kernel, threads, bytes) for the process.
+int ctas_per_sm(const void* f, int threads, int smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(f, threads, smem, dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, (size_t)smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = n;
+    return n;
+}
+
+// Launch shape of one step launch: warps per CTA.  `fixed` > 0 is the
+// caller's choice (gen_set_launch, the autotuner); otherwise the count among
+// 8, 4, 2, 1 whose CTAs keep the most warps resident per SM (ties: more warps
+// per CTA).  Either way, launches too small to give every SM a CTA take
+// fewer warps per CTA.
+int pick_warps(const void* f, int fixed, int games_per_warp, int warp_smem, int n_items, int sms) {
+    int w = fixed;
+    if (w <= 0) {
+        int best = 0;
+        w = 1;
+        for (int cand : {8, 4, 2, 1}) {
+            const int smem = cand * games_per_warp * warp_smem;
+            if (smem > 227 * 1024) continue;
+            const int warps = ctas_per_sm(f, 32 * cand, smem) * cand;
+            if (warps > best) {
+                best = warps;
+                w = cand;
+            }
+        }
+    }
+    while (w > 1 && (n_items + games_per_warp * w - 1) / (games_per_warp * w) < sms) w >>= 1;
+    return w;
+}
+
 // The plain-generator kernels of one lane-group width: per frame or
 // multi-frame, for uniform or per-game shapes.
 template <int LW>
-int launch_plain(const KArgs& a, bool multi, dim3 grid, dim3 block, int smem, cudaStream_t st) {
-    if (LW < 32) {  // more than 48 KB of shared memory per CTA for small games
-        static SmemLimit limit;
-        const void* fns[4] = {(const void*)k_generals<false, false, LW, false>,
-                              (const void*)k_generals<true, false, LW, false>,
-                              (const void*)k_generals<false, false, LW, true>,
-                              (const void*)k_generals<true, false, LW, true>};
-        const int e = limit.raise(fns, 4, smem);
-        if (e != 0) return e;
-    }
+const void* plain_kernel(bool multi, bool uniform) {
+    if (multi && uniform) return (const void*)k_generals<true, false, LW, true>;
+    if (multi) return (const void*)k_generals<true, false, LW, false>;
+    if (uniform) return (const void*)k_generals<false, false, LW, true>;
+    return (const void*)k_generals<false, false, LW, false>;
+}
+
+template <int LW>
+int launch_plain(const KArgs& a, bool multi, int fixed_warps, int max_ctas, int sms, cudaStream_t st) {
+    constexpr int kPerWarp = 32 / LW;
+    const void* f = plain_kernel<LW>(multi, a.uniform != 0);
+    const int warps = pick_warps(f, fixed_warps, kPerWarp, a.warp_smem, a.n_items, sms);
+    const int games_per_cta = kPerWarp * warps;
+    const int smem = a.warp_smem * games_per_cta;
+    int blocks = (a.n_items + games_per_cta - 1) / games_per_cta;
+    // multi-frame launches: a grid of many waves, groups stride over any items beyond it
+    if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
+    const dim3 grid(blocks), block(32 * warps);
     if (multi && a.uniform)
         k_generals<true, false, LW, true><<<grid, block, smem, st>>>(a);
     else if (multi)
@@ -1495,6 +1580,10 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     const bool spawn = a.spawn_dmax > 0 || a.spawn_bfs || a.castle_radius > 0;
     const bool multi = a.frames > 1 || a.action_log;
     const cudaStream_t st = (cudaStream_t)stream;
+    {
+        const int e = allow_max_smem();
+        if (e != 0) return e;
+    }
     static std::atomic<int> sm_count{0};  // of the first device used: only the launch shape depends on it
     int sms = sm_count.load(std::memory_order_relaxed);
     if (sms == 0) {
@@ -1511,31 +1600,27 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     // frame and 4,096 resident)
     const bool large = a.n_items >= (multi ? 24 : 12) * sms;
     const bool small = !spawn && a.pmax <= kPairMaxPlayers && (a.lane_groups == 2 || (a.lane_groups == 0 && large));
+    const int wcap = warps_per_cta > 0 ? warps_per_cta : 1;  // the fixed shape must fit too
     int per_warp = 1;
-    if (small && multi && a.npad_max <= kQuadMaxCells && 4 * warps_per_cta * a.warp_smem <= 227 * 1024)
+    if (small && multi && a.npad_max <= kQuadMaxCells && 4 * wcap * a.warp_smem <= 227 * 1024)
         per_warp = 4;
-    else if (small && a.npad_max <= kPairMaxCells && 2 * warps_per_cta * a.warp_smem <= 227 * 1024)
+    else if (small && a.npad_max <= kPairMaxCells && 2 * wcap * a.warp_smem <= 227 * 1024)
         per_warp = 2;
-    // small batches: fewer warps per CTA until the grid covers every SM once
-    while (warps_per_cta > 1 &&
-           (a.n_items + per_warp * warps_per_cta - 1) / (per_warp * warps_per_cta) < sms)
-        warps_per_cta >>= 1;
-    const int games_per_cta = per_warp * warps_per_cta;
-    const int smem = a.warp_smem * games_per_cta;
-    int blocks = (a.n_items + games_per_cta - 1) / games_per_cta;
-    // multi-frame launches: a grid of many waves, groups stride over any items beyond it
-    if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
-    const dim3 grid(blocks), block(32 * warps_per_cta);
     if (spawn) {  // one game per warp, shapes read per game
+        const void* f = multi ? (const void*)k_generals<true, true, 32, false> : (const void*)k_generals<false, true, 32, false>;
+        const int warps = pick_warps(f, warps_per_cta, 1, a.warp_smem, a.n_items, sms);
+        const int smem = a.warp_smem * warps;
+        int blocks = (a.n_items + warps - 1) / warps;
+        if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
         if (multi)
-            k_generals<true, true, 32, false><<<grid, block, smem, st>>>(a);
+            k_generals<true, true, 32, false><<<blocks, 32 * warps, smem, st>>>(a);
         else
-            k_generals<false, true, 32, false><<<grid, block, smem, st>>>(a);
+            k_generals<false, true, 32, false><<<blocks, 32 * warps, smem, st>>>(a);
         return (int)cudaGetLastError();
     }
-    if (per_warp == 4) return launch_plain<8>(a, multi, grid, block, smem, st);
-    if (per_warp == 2) return launch_plain<16>(a, multi, grid, block, smem, st);
-    return launch_plain<32>(a, multi, grid, block, smem, st);
+    if (per_warp == 4) return launch_plain<8>(a, multi, warps_per_cta, max_ctas, sms, st);
+    if (per_warp == 2) return launch_plain<16>(a, multi, warps_per_cta, max_ctas, sms, st);
+    return launch_plain<32>(a, multi, warps_per_cta, max_ctas, sms, st);
 }
 
 int launch_copy(const void* src, void* dst, size_t n16, int blocks, void* stream) {

@@ -61,7 +61,7 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
            "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
            "gen_features_build_ex", "gen_features_set_form", "gen_sample_actions", "gen_set_sample_form",
-           "gen_set_lane_groups")
+           "gen_set_lane_groups", "gen_outputs_get", "gen_device_bytes", "gen_save_state", "gen_load_state")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -107,6 +107,10 @@ def load_library(path: str = LIB_PATH):
             "gen_sample_actions": (C.c_int, [vp, vp, u64, vp, vp, vp]),
             "gen_set_sample_form": (C.c_int, [vp, C.c_int]),
             "gen_set_lane_groups": (C.c_int, [vp, C.c_int]),
+            "gen_outputs_get": (C.c_int, [vp, C.POINTER(GenOutputs)]),
+            "gen_device_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+            "gen_save_state": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t), vp]),
+            "gen_load_state": (C.c_int, [vp, vp, C.c_size_t, vp]),
             "gen_last_error": (C.c_char_p, []),
             "gen_destroy": (None, [vp]),
         }
@@ -174,6 +178,38 @@ class Outputs:
         return sum(t.numel() * t.element_size() for t in self.tensors())
 
 
+class _DevicePtr:
+    """A device buffer the library owns, seen by torch through the CUDA array
+    interface (zero copy)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, shape=None):
+        self.__cuda_array_interface__ = {"shape": shape or (n,), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class LibraryOutputs(Outputs):
+    """Torch views of an environment's own output buffers (gen_outputs_get):
+    what gen_step writes for NULL output fields, valid until the environment
+    is destroyed."""
+
+    def __init__(self, env: "GeneralsEnv"):  # noqa: super() not called: the library owns the memory
+        import torch
+        st = GenOutputs()
+        _check(env.lib.gen_outputs_get(env.h, C.byref(st)), "gen_outputs_get")
+        pc, ps, G = int(env.layout.plane_cells), int(env.layout.player_slots), int(env.layout.n_games)
+        view = lambda ptr, n, t, shape=None: torch.as_tensor(_DevicePtr(ptr, n, t, shape), device="cuda")
+        self.obs_army = view(st.obs_army, pc, "<i2")
+        self.obs_owner = view(st.obs_owner, pc, "|i1")
+        self.obs_terrain = view(st.obs_terrain, pc, "|i1")
+        self.obs_vis = view(st.obs_vis, pc, "|u1")
+        self.mask = view(st.mask, pc, "|u1")
+        self.reward = view(st.reward, ps, "<f4")
+        self.scoreboard = view(st.scoreboard, ps, "<i4", (ps, 2))
+        self.done = view(st.done, G, "|u1")
+        self.struct = st
+        self.env = env  # keeps the environment (and its buffers) alive
+
+
 class GeneralsEnv:
     """A batch of games held on the GPU by libgenerals.
 
@@ -230,8 +266,9 @@ class GeneralsEnv:
         return torch.zeros(int(self.layout.player_slots), dtype=torch.int32, device="cuda")
 
     # ---- calls ----------------------------------------------------------
-    def observe(self, out: Outputs, stream=None):
-        _check(self.lib.gen_observe(self.h, C.byref(out.struct), stream or _cur_stream()), "gen_observe")
+    def observe(self, out: Outputs | None = None, stream=None):
+        ref = C.byref(out.struct) if out is not None else None
+        _check(self.lib.gen_observe(self.h, ref, stream or _cur_stream()), "gen_observe")
 
     def reset(self, out: Outputs, game_ids=None, stream=None):
         if game_ids is None:
@@ -240,12 +277,38 @@ class GeneralsEnv:
             _check(self.lib.gen_reset(self.h, C.c_void_p(game_ids.data_ptr()), int(game_ids.numel()),
                                       C.byref(out.struct), stream or _cur_stream()), "gen_reset")
 
-    def step(self, actions, out: Outputs, stream=None):
-        _check(self.lib.gen_step(self.h, C.c_void_p(actions.data_ptr()), C.byref(out.struct),
-                                 stream or _cur_stream()), "gen_step")
+    def step(self, actions, out: Outputs | None = None, stream=None):
+        """One turn of every game; out=None writes the environment's own
+        buffers (library_outputs())."""
+        ref = C.byref(out.struct) if out is not None else None
+        _check(self.lib.gen_step(self.h, C.c_void_p(actions.data_ptr()), ref, stream or _cur_stream()), "gen_step")
 
-    def step_policy(self, actions, out: Outputs, policy_seed: int, next_actions, stream=None):
-        _check(self.lib.gen_step_policy(self.h, C.c_void_p(actions.data_ptr()), C.byref(out.struct),
+    def library_outputs(self) -> LibraryOutputs:
+        """Torch views of the environment's own output buffers."""
+        return LibraryOutputs(self)
+
+    def device_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(self.lib.gen_device_bytes(self.h, C.byref(n)), "gen_device_bytes")
+        return int(n.value)
+
+    def save_state(self) -> np.ndarray:
+        """Everything that determines later frames, as one opaque host blob (uint8)."""
+        need = C.c_size_t()
+        _check(self.lib.gen_save_state(self.h, None, 0, C.byref(need), _cur_stream()), "gen_save_state")
+        buf = np.empty(int(need.value), np.uint8)
+        used = C.c_size_t()
+        _check(self.lib.gen_save_state(self.h, buf.ctypes.data, buf.nbytes, C.byref(used), _cur_stream()),
+               "gen_save_state")
+        return buf[:int(used.value)]
+
+    def load_state(self, blob):
+        blob = np.ascontiguousarray(blob, np.uint8)
+        _check(self.lib.gen_load_state(self.h, blob.ctypes.data, blob.nbytes, _cur_stream()), "gen_load_state")
+
+    def step_policy(self, actions, out: Outputs | None, policy_seed: int, next_actions, stream=None):
+        ref = C.byref(out.struct) if out is not None else None
+        _check(self.lib.gen_step_policy(self.h, C.c_void_p(actions.data_ptr()), ref,
                                         int(policy_seed), C.c_void_p(next_actions.data_ptr()),
                                         stream or _cur_stream()), "gen_step_policy")
 

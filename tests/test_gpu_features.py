@@ -243,3 +243,51 @@ def test_feature_builder_argument_errors():
             fb.set_form(form)
     fb.build(out)  # still usable
     torch.cuda.synchronize()
+
+
+def test_age_row_every_dt_up_to_65535_bit_exact():
+    """The age row log(1 + dt) / 5 (App. A row 21, Q31) for every dt in
+    [0, 65535], bit for bit against the oracle: the library evaluates the
+    logarithm with CUDA's double log and the oracle with the host C library's,
+    each rounding once to float.  One game per dt on a 1 x 6 board: at turn
+    100 player 1 holds the cell next to player 0's general (seen), then the
+    generals swap ends and the turn moves on by dt, so player 0 remembers an
+    enemy in fog there for dt turns."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    G, N = 65536, 6
+    kw = dict(seed=1, n_cities=0, min_general_dist=1)
+    env = GeneralsEnv(1, N, 0, 2, batch=G, **kw)
+    orc = OracleEnv(np.ones(G, np.int32), np.full(G, N, np.int32), np.zeros(G, np.int32), np.full(G, 2, np.int32), **kw)
+    fb, ofb = env.features(7), OracleFeatures(orc, 7)
+    npad = int(env.npad[0])
+
+    def place(terrain, owner, army, turns, frame):
+        a = np.zeros((G, npad), np.int16)
+        o = np.full((G, npad), -1, np.int8)
+        t = np.zeros((G, npad), np.int8)
+        a[:, :N], o[:, :N], t[:, :N] = army, owner, terrain
+        sc = np.zeros((G, 8), np.uint32)
+        sc[:, 0], sc[:, 1], sc[:, 3] = turns, frame, 3
+        env.write_state(a.reshape(-1), o.reshape(-1), t.reshape(-1), sc)
+        for g in range(G):
+            orc.set_game(g, army, owner, terrain, turn=int(turns[g]), frame=frame)
+
+    # seen: player 1's plain next to player 0's general
+    place([3, 0, 0, 0, 0, 3], [0, 1, -1, -1, -1, 1], [5, 3, 0, 0, 0, 5], np.full(G, 100), 1)
+    out = fb.build()
+    compare_features(env, fb, out, ofb.build(), "seen", games=range(0, G, 4099), orc_index=lambda k: 4099 * k)
+    # fogged for dt = g turns: the generals swap ends, the cell is neutral again
+    dts = np.arange(G, dtype=np.int64)
+    place([3, 0, 0, 0, 0, 3], [1, -1, -1, -1, -1, 0], [5, 0, 0, 0, 0, 5], 100 + dts, 2)
+    out = fb.build()
+    want = ofb.build()
+    torch.cuda.synchronize()
+    C = fb.channels
+    got = out.view(G, 2, C, npad)[:, 0, AGE, 1].cpu().numpy()
+    exp = np.array([w[0][AGE][1] for w in want], np.float32)
+    assert exp[0] == 0.0 and exp[1] > 0.0  # dt = 0 gives log(1) = 0; the row is live
+    bad = np.flatnonzero(got.view(np.uint32) != exp.view(np.uint32))
+    assert bad.size == 0, f"age row differs at dt {bad[:10].tolist()} ({bad.size} values)"
+    # and every channel of a spread of games, against the oracle
+    compare_features(env, fb, out, [want[g] for g in range(0, G, 997)], "fogged", games=range(0, G, 997))

@@ -82,3 +82,17 @@ def test_null_handles_of_the_form_switches_fail_cleanly(lib):
                  lambda: lib.gen_features_set_form(None, 0), lambda: lib.gen_set_spawn_range(None, 0, 0)):
         assert call() == -1
         assert lib.gen_last_error().decode()
+
+
+def test_boundary_additions_refuse_null_handles(lib):
+    """The saved-state blob, the environment's own outputs and the byte count
+    refuse NULL arguments on the host, before any CUDA call."""
+    used = C.c_size_t()
+    out = gen.GenOutputs()
+    buf = (C.c_ubyte * 256)()
+    for call in (lambda: lib.gen_save_state(None, None, 0, C.byref(used), None),
+                 lambda: lib.gen_load_state(None, buf, 256, None),
+                 lambda: lib.gen_outputs_get(None, C.byref(out)),
+                 lambda: lib.gen_device_bytes(None, C.byref(used))):
+        assert call() == -1
+        assert lib.gen_last_error().decode()

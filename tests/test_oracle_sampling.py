@@ -94,3 +94,62 @@ def test_single_legal_entry_and_no_legal_entry():
     env.set_game(0, army, owner, terrain, turn=0, alive=0b01)
     a, m = env.sample_actions([lg], 3)
     assert m[0][1].sum() == 0 and a[0, 1] == 0  # no legal entry: pass
+
+
+def _one_by_three(frame=5):
+    """A 1x3 board: player 0's general (5 units) | a neutral plain | player 1's
+    general (5 units).  Player 0's legal entries (Q35) are, in index order,
+    pass on its cell (index 0), all-but-one right (index 4) and half right
+    (index 8): up, down and left leave the board."""
+    env = OracleEnv(np.array([1]), np.array([3]), np.array([0]), np.array([2]), seed=1, n_cities=0,
+                    min_general_dist=1)
+    env.set_game(0, np.array([5, 0, 5]), np.array([0, -1, 1]), np.array([3, 0, 3]), turn=5, frame=frame)
+    return env
+
+
+def _logits(l0, l4, l8):
+    x = np.full((2, 27), -30.0, np.float32)
+    x[0, 0], x[0, 4], x[0, 8] = l0, l4, l8
+    return [x]
+
+
+# Worked by hand in exact integer arithmetic (Q36).  The draw of player 0 of
+# game 0 at frame 5 under seed 1 is d = sm(key(1, 0, 5, 0), 7)
+# = 13191151713292224422 (the hash is pinned to SplitMix64's published
+# outputs in test_oracle_hash.py).
+D_DRAW = 13191151713292224422
+
+
+def test_sampling_worked_example_equal_weights():
+    """Three legal entries of logit 0: each weighs floor(E(0) * 2^24) = 2^24,
+    S = 3 * 2^24 = 50331648.  d * S = 663932404748021160745107456, whose high
+    64 bits give r = 35991847.  Running sums 16777216, 33554432, 50331648:
+    the first above r is the third, index 8 (half move right).  (Taking the
+    low 64 bits, 14398910256543432704, exceeds S and draws nothing.)"""
+    from oracle import key, sm
+    assert sm(key(1, 0, 5, 0), 7) == D_DRAW
+    env = _one_by_three()
+    acts, masks = env.sample_actions(_logits(0.0, 0.0, 0.0), 1)
+    assert masks[0][0].nonzero()[0].tolist() == [0, 4, 8]
+    assert acts[0, 0] == 8
+
+
+def test_sampling_worked_example_draw_on_a_boundary():
+    """Weights 2^24 (pass, logit 0), 6684345 (right, logit -0.9202535152435303,
+    float32 0xbf6b95bc: floor(E(x) * 2^24) = 6684345) and 0 (half right, logit
+    -30 < -25 / log2 e, E = 0).  S = 23461561, d * S =
+    309485010581660034102442742, r = 16777216: exactly the first running sum.
+    The first entry whose running sum EXCEEDS r is the second, index 4; a
+    rule of "at least r" would draw index 0, and the low 64 bits
+    (760314965377661686) would draw nothing."""
+    x = float(np.array([0xBF6B95BC], np.uint32).view(np.float32)[0])
+    assert x == -0.9202535152435303
+    assert int(np.floor(np.float32(exp37(x)) * np.float32(16777216.0))) == 6684345
+    assert exp37(-30.0) == 0.0
+    env = _one_by_three()
+    acts, _ = env.sample_actions(_logits(0.0, x, -30.0), 1)
+    assert acts[0, 0] == 4
+    # one frame later the draw differs and the same weights need not pick index 4:
+    # the frame is part of the key
+    from oracle import key, sm
+    assert sm(key(1, 0, 6, 0), 7) != D_DRAW

@@ -39,6 +39,7 @@ def test_static_stage_matches_host_step_on_consecutive_calls():
     act_b = act_a.clone().pin_memory()
     nxt_a = torch.empty_like(act_a).pin_memory()
     nxt_b = torch.empty_like(act_b).pin_memory()
+    held = env_b.device_bytes()  # env_b only ever takes the static path
     for call in range(2):
         env_a.step_host(act_a, out_a, 17, nxt_a)
         env_b.step_host_static(act_b, out_b, 17, nxt_b)
@@ -47,6 +48,7 @@ def test_static_stage_matches_host_step_on_consecutive_calls():
         np.testing.assert_array_equal(nxt_a.numpy(), nxt_b.numpy(), err_msg=f"call {call}")
         act_a.copy_(nxt_a)
         act_b.copy_(nxt_b)
+        assert env_b.device_bytes() == held, "the static entry point allocated device memory"
 
 
 def test_static_stage_rejects_batches_beyond_its_size():
