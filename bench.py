@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "1v1-65536x24x24"
+STEP_PREROLL = 256  # frames of the benchmark policy before the default workload's warm-up and timed steps
 METRIC = "frames/s per GB300 (bit-exact vs oracle)"
 UNIT = "frames/s"
 POLICY_SEED = 2
@@ -160,6 +161,25 @@ class ClockSampler:
         busy = [x for x in sm if mx and x > 0.3 * mx] or sm
         return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def free_port() -> int:
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def launch_ranks(n: int, argv=None) -> int:
+    """Started with --gpus N > 1 outside a launcher: run this same command as
+    N ranks on this node (one process per GPU, rendezvous on 127.0.0.1) and
+    return their exit status.  Each rank steps its own games (global ids
+    offset by rank); rank 0 prints the line, with n_gpus the ranks that
+    reported."""
+    argv = sys.argv[1:] if argv is None else argv
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
 
 
 def dist_setup(n_gpus):
@@ -295,7 +315,9 @@ def run_ours(args, rank, world, local):
     acts = env.new_actions()
     stream = torch.cuda.current_stream()
     env.policy(POLICY_SEED, acts)
-    for _ in range(args.warmup):
+    # pre-roll to mid-game (players own territory, auto-resets under way),
+    # then the untimed warm-up steps
+    for _ in range(STEP_PREROLL + args.warmup):
         env.step_policy(acts, out, POLICY_SEED, acts)
     torch.cuda.synchronize()
 
@@ -337,8 +359,7 @@ def run_ours(args, rank, world, local):
         ms = r0.elapsed_time(r1) / (rounds * Kr)
         rb = algorithmic_bytes_resident(env, Kr)
         resident = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "rollout_frames": Kr,
-                    "bytes_per_frame": rb, "hbm_frac_own_bytes": rb / (ms * 1e-3) / 1e9 / peaks()[0],
-                    "hbm_frac_plain_bytes": algorithmic_bytes(env) / (ms * 1e-3) / 1e9 / peaks()[0]}
+                    "own_bytes_per_frame": rb, "hbm_frac_own_bytes": rb / (ms * 1e-3) / 1e9 / peaks()[0]}
         del outK
 
     # e2e: the same step through the host-buffer entry point, copies timed
@@ -352,6 +373,27 @@ def run_ours(args, rank, world, local):
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if NCU_TRAFFIC["kernel_sha1"] == kernel_sha1() and G == NCU_TRAFFIC["games"] else None)
     own_peak = copy_peak_gbps(1 << 30, 5) if (rank == 0 and not args.no_copy_peak) else None
+
+    # every other workload, each with its own timing and roofline (one GPU)
+    configs = None
+    if world == 1 and not args.no_configs:
+        del out
+        torch.cuda.empty_cache()
+        configs = {}
+        jobs = (("ragged_131072", lambda: rollout_record(args, "1v1-131072-ragged15to30", 64, 1, rank)),
+                ("mixed_32768", lambda: rollout_record(args, "mixed-32768-sides20to40", 64, 1, rank)),
+                ("served_256", lambda: served_record(args, args.served_seconds_default)),
+                ("features", lambda: features_record(args, 65536, 10, rank)),
+                ("sampler", lambda: sampler_record(args, 65536, 10, rank)),
+                ("selfplay_512x512", lambda: selfplay_record(args, rank)))
+        for name, job in jobs:
+            t0 = time.perf_counter()
+            try:
+                configs[name] = job()
+            except Exception as exc:  # one workload failing must not hide the others
+                configs[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            configs[name]["bench_seconds"] = round(time.perf_counter() - t0, 1)
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -387,6 +429,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "resident_rollout_form": resident,
+            "configs": configs,
             "gpu_launches": K,
             "clocks": clk.summary(),
             "kernel_sha1": kernel_sha1(),
@@ -394,59 +437,84 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def run_rollout_workload(args, rank, world, local):
-    """Ragged / mixed workloads: per-frame launches vs K-frame rollouts (CUDA
-    graph of K launches, and one resident launch), bucketed by board size."""
+def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0) -> dict:
+    """A ragged or mixed workload in every launch form, each with both batch
+    forms (one launch per size bucket on forked streams, and one persistent
+    work-list launch over every bucket): per-frame launches, the same K frames
+    as a CUDA graph, and one resident K-frame launch; frames/s and the HBM
+    fraction of each (plain-form bytes per frame; the resident form also
+    against its own bytes, the state moving once per K frames)."""
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
     from paper_2606_23348_gb300.workloads import shard, workload
 
-    torch.cuda.set_device(local)
-    H, W, mode, P, gen, _ = workload(args.workload)
+    H, W, mode, P, gen, _ = workload(name)
     G = int(H.shape[0])
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
-    tune = env.autotune(steps=3) if args.autotune else "off"
-    K = args.rollout
+    tune = env.autotune(steps=3) if getattr(args, "autotune", False) else "off"
     stream = torch.cuda.current_stream()
     acts = env.new_actions()
     env.policy(POLICY_SEED, acts)
     peak, peak_kind = peaks()
     nbytes = algorithmic_bytes(env)
-    forms = {}
-    rounds = max(1, args.steps // K)
-    # plain: one launch per frame into a single-frame buffer
-    out1 = env.new_outputs()
-    for _ in range(args.warmup):
-        env.step_policy(acts, out1, POLICY_SEED, acts)
+    rb = algorithmic_bytes_resident(env, K)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(rounds * K):
-        env.step_policy(acts, out1, POLICY_SEED, acts)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / (rounds * K)
-    forms["plain"] = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms,
-                      "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak, "launches_per_frame": len_buckets(env)}
-    del out1
+    forms = {}
+    out1 = env.new_outputs()
     outK = env.new_outputs(frames=K)
-    for name, form in (("graph", 1), ("resident", 0)):
-        for _ in range(2):
-            env.rollout(K, POLICY_SEED, acts, outK, None, form)
+    for bname, batch in (("buckets", env.BATCH_BUCKETS), ("worklist", env.BATCH_WORKLIST)):
+        env.set_batch_form(batch)
+        for _ in range(max(3, args.warmup)):
+            env.step_policy(acts, out1, POLICY_SEED, acts)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(rounds):
-            env.rollout(K, POLICY_SEED, acts, outK, None, form)
+        for _ in range(rounds * K):
+            env.step_policy(acts, out1, POLICY_SEED, acts)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / (rounds * K)
-        rec = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak}
-        if form == 0:
-            rb = algorithmic_bytes_resident(env, K)
-            rec["resident_bytes_per_frame"] = rb
-            rec["resident_hbm_frac"] = rb / (ms * 1e-3) / 1e9 / peak
-        forms[name] = rec
+        forms[f"plain_{bname}"] = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms,
+                                   "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak,
+                                   "launches_per_frame": len_buckets(env) if batch == 1 else 1}
+        for fname, form in (("graph", 1), ("resident", 0)):
+            for _ in range(2):
+                env.rollout(K, POLICY_SEED, acts, outK, None, form)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(rounds):
+                env.rollout(K, POLICY_SEED, acts, outK, None, form)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (rounds * K)
+            rec = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak}
+            if form == 0:
+                rec["own_bytes_per_frame"] = rb
+                rec["hbm_frac_own_bytes"] = rb / (ms * 1e-3) / 1e9 / peak
+            forms[f"{fname}_{bname}"] = rec
+    buckets = len_buckets(env)
+    del out1, outK, env
+    torch.cuda.empty_cache()
+    best_plain = max(("plain_buckets", "plain_worklist"), key=lambda k: forms[k]["frames_per_s"])
+    p = forms[best_plain]
+    return {"workload": name, "games": G, "rollout_frames": K, "size_buckets": buckets, "autotune": tune,
+            "forms": forms,
+            "roofline": {"bound": "hbm", "achieved": nbytes / (p["ms_per_frame"] * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": p["hbm_frac"], "traffic": None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_frame": nbytes, "form": best_plain,
+                         "kernel": "k_worklist" if best_plain == "plain_worklist" else "k_generals per bucket"}}
+
+
+def run_rollout_workload(args, rank, world, local):
+    """Ragged / mixed workloads: per-frame launches vs K-frame rollouts (CUDA
+    graph of K launches, and one resident launch), bucketed by board size."""
+    import torch
+    torch.cuda.set_device(local)
+    K = args.rollout
+    rounds = max(1, args.steps // K)
+    rec = rollout_record(args, args.workload, K, rounds, rank)
+    forms = rec["forms"]
     best = max(forms, key=lambda k: forms[k]["frames_per_s"])
     if rank == 0:
         line = {
@@ -454,70 +522,98 @@ def run_rollout_workload(args, rank, world, local):
             "steps": rounds * K, "warmup": args.warmup, "ms_per_step": forms[best]["ms_per_frame"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
             "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
-            "config": {"workload": args.workload, "games_per_gpu": G, "rollout_frames": K, "best_form": best,
-                       "size_buckets": len_buckets(env), "autotune": tune,
+            "config": {"workload": args.workload, "games_per_gpu": rec["games"], "rollout_frames": K,
+                       "best_form": best, "size_buckets": rec["size_buckets"], "autotune": rec["autotune"],
                        "l2": "inputs larger than L2"},
-            "roofline": {"bound": "hbm", "achieved": nbytes / (forms["plain"]["ms_per_frame"] * 1e-3) / 1e9,
-                         "peak": peak, "unit": "GB/s", "frac": forms["plain"]["hbm_frac"], "traffic": None,
-                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                         "algorithmic_bytes_per_frame": nbytes, "kernel": "k_generals per-frame launches"},
-            "forms": forms,
-            "gpu_launches": rounds * K * len_buckets(env),
+            "roofline": rec["roofline"], "forms": forms,
+            "gpu_launches": rounds * K * (rec["size_buckets"] if best.endswith("buckets") else 1),
         }
         print(json.dumps(line), flush=True)
 
 
-def run_served(args, rank, world, local):
-    """256 closed-loop actor clients (exponential think time, mean 2 ms), each
-    holding 64..1024 mixed games with sides 15..40, opening and closing
-    sessions continuously, against an 80 GB admission budget; then the plain
-    bucketed step kernel on a batch of the same shapes."""
+SERVED_PARAMS = dict(seed=MAP_SEED, n_cities=-1, city_per_mille=30, city_army_min=40, city_army_max=50,
+                     min_general_dist=0)
+SERVED_SIM = dict(clients=256, mean_interarrival_ms=2.0, min_games=64, max_games=1024, min_side=15, max_side=40,
+                  frac_1v1=0.4, frac_2v2=0.3, min_steps=20, max_steps=200, seed=11, policy_seed=POLICY_SEED,
+                  budget_bytes=80 << 30, host_outputs=0, copy_outputs=0, open_loop=1)
+
+
+def _served_row(st: dict) -> dict:
+    keep = ("frames_per_s", "requests", "lat_p50_ms", "lat_p99_ms", "lat_mean_ms", "service_p50_ms", "service_p99_ms",
+            "offered_requests_per_s", "tick_games_mean", "sessions_admitted", "sessions_waited",
+            "sessions_waited_budget", "peak_bytes_in_use", "budget", "seconds")
+    return {k: st[k] for k in keep}
+
+
+def served_record(args, seconds: float, sweep: bool = False, admission: bool = False) -> dict:
+    """The served workload: 256 actor clients with open-loop Poisson arrivals
+    (mean 2 ms per client), each holding 64..1024 mixed games (40% 1v1, 30%
+    2v2, 30% FFA-8) with sides 15..40, opening and closing sessions
+    continuously, against an 80 GB admission budget; outputs stay on the
+    device (GPU actors).  Beside it the plain bucketed step kernel on a batch
+    of the same shape mix.  sweep: the same clients at 2, 4 and 8 times the
+    offered load.  admission: an 80 GB run whose sessions (FFA-8, 16,384 to
+    32,768 games each) outgrow the budget, so that admission defers."""
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
     from paper_2606_23348_gb300.server import simulate
     from paper_2606_23348_gb300.workloads import MOUNTAIN_THRESH_20PCT, shapes
 
-    torch.cuda.set_device(local)
-    params = dict(seed=MAP_SEED, mountain_thresh=MOUNTAIN_THRESH_20PCT, n_cities=-1, city_per_mille=30,
-                  city_army_min=40, city_army_max=50, min_general_dist=0)
-    sim = dict(clients=256, mean_interarrival_ms=2.0, min_games=64, max_games=1024, min_side=15, max_side=40,
-               frac_1v1=0.4, frac_2v2=0.3, min_steps=20, max_steps=200, seconds=args.served_seconds,
-               seed=11, policy_seed=POLICY_SEED, budget_bytes=80 << 30)
-    res = {}
-    for mode_name, host, copy in (("device_outputs", 0, 0), ("host_outputs", 1, 1)):
-        res[mode_name] = simulate(params, host_outputs=host, copy_outputs=copy, **sim)
+    params = dict(SERVED_PARAMS, mountain_thresh=MOUNTAIN_THRESH_20PCT)
+    rec = {"workload": "served-256-clients", "arrivals": "open loop, Poisson, mean 2 ms per client",
+           "latency": "scheduled arrival to result in the client's buffers (queueing included); "
+                      "service_* from submission",
+           "nominal": _served_row(simulate(params, seconds=seconds, **SERVED_SIM))}
+    if sweep:
+        rec["load_sweep"] = []
+        for mean in (8.0, 4.0, 1.0):  # a quarter, half and twice the nominal offered load
+            st = simulate(params, seconds=seconds, **{**SERVED_SIM, "mean_interarrival_ms": mean})
+            rec["load_sweep"].append({"mean_interarrival_ms": mean, **_served_row(st)})
+    if admission:
+        st = simulate(params, seconds=seconds, **{**SERVED_SIM, "clients": 64, "min_games": 16384,
+                                                  "max_games": 32768, "frac_1v1": 0.0, "frac_2v2": 0.0,
+                                                  "min_steps": 10, "max_steps": 40, "open_loop": 0})
+        rec["admission_80gb"] = {"sessions": "64 clients x 16,384..32,768 FFA-8 games, sides 15..40, closed loop",
+                                 **_served_row(st)}
     # the plain fixed-size kernel on a batch with the same shape distribution
     G = 256 * 544
     H, W, mode, P = shapes(G, (15, 40), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=11)
     env = GeneralsEnv(H, W, mode, P, **params)
-    out = env.new_outputs()
-    acts = env.new_actions()
+    out, acts = env.new_outputs(), env.new_actions()
     env.policy(POLICY_SEED, acts)
-    for _ in range(args.warmup):
+    for _ in range(max(3, args.warmup)):
         env.step_policy(acts, out, POLICY_SEED, acts)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    n = 20
     e0.record(stream)
-    n = max(10, min(args.steps, 100))
     for _ in range(n):
         env.step_policy(acts, out, POLICY_SEED, acts)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / n
-    plain = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "games": G}
-    dev = res["device_outputs"]
+    rec["plain_bucketed_kernel_same_mix"] = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "games": G}
+    del env, out, acts
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_served(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    rec = served_record(args, args.served_seconds, sweep=True, admission=True)
+    nom = rec["nominal"]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": dev["frames_per_s"], "unit": UNIT, "n_gpus": world,
-            "steps": int(dev["requests"]), "warmup": args.warmup, "ms_per_step": dev["lat_mean_ms"],
+            "metric": METRIC, "value": nom["frames_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": int(nom["requests"]), "warmup": args.warmup, "ms_per_step": nom["lat_mean_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
             "data": "synthetic (simulated actor clients, seeded maps, random legal policy)",
-            "config": {"workload": "served-256-clients", **{k: v for k, v in sim.items() if k != "budget_bytes"},
-                       "budget_gb": 80},
-            "served": res, "plain_fixed_size_kernel": plain,
-            "latency_ms": {"p50": dev["lat_p50_ms"], "p99": dev["lat_p99_ms"]},
+            "config": {"workload": "served-256-clients", **{k: v for k, v in SERVED_SIM.items() if k != "budget_bytes"},
+                       "budget_gb": 80, "seconds": args.served_seconds},
+            "served": rec, "latency_ms": {"p50": nom["lat_p50_ms"], "p99": nom["lat_p99_ms"]},
         }
         print(json.dumps(line), flush=True)
 
@@ -532,65 +628,52 @@ def feature_bytes_per_player_cell(hist: int, players: int) -> float:
     return 4 * C + 7 + 4 * hist + 11 + 4.0 / players
 
 
-def run_features(args, rank, world, local):
+def features_record(args, G: int, K: int, rank: int = 0, clk=None) -> dict:
     """Per frame: the fused step + policy, then the 38-channel feature tensor
-    of every player (App. A) with its persistent memory."""
+    of every player (App. A) with its persistent memory and the 512-frame
+    temporal tokens; the feature launch timed on its own."""
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
     from paper_2606_23348_gb300.workloads import shard, workload
 
-    torch.cuda.set_device(local)
-    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=args.games or None)
-    G = int(H.shape[0])
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=G)
     hist, window = 7, 512
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
     fb = env.features(hist, window)
-    out = env.new_outputs()
-    acts = env.new_actions()
-    fout = fb.new_output()
-    ser = fb.new_series()
+    out, acts = env.new_outputs(), env.new_actions()
+    fout, ser = fb.new_output(), fb.new_series()
     stream = torch.cuda.current_stream()
     env.policy(POLICY_SEED, acts)
     for _ in range(max(3, args.warmup)):
         env.step_policy(acts, out, POLICY_SEED, acts)
         fb.build(fout, ser)
     torch.cuda.synchronize()
-    K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    with ClockSampler(local) as clk:
-        barrier(world)
-        torch.cuda.synchronize()
-        t_all[0].record(stream)
-        for k in range(K):
-            ev[k][0].record(stream)
-            env.step_policy(acts, out, POLICY_SEED, acts)
-            ev[k][1].record(stream)
-            fb.build(fout, ser)
-            ev[k][2].record(stream)
-        t_all[1].record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-    elapsed_ms = max_over_ranks(t_all[0].elapsed_time(t_all[1]), world)
+    t_all[0].record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        env.step_policy(acts, out, POLICY_SEED, acts)
+        ev[k][1].record(stream)
+        fb.build(fout, ser)
+        ev[k][2].record(stream)
+    t_all[1].record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = t_all[0].elapsed_time(t_all[1])
     step_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     feat_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    value = sum_over_ranks(float(G * K), world) / (elapsed_ms * 1e-3)
     cells = 2 * 576 * G
     # + temporal tokens per player: T - 1 ring entries read, one written, T written out (8 B each)
     nbytes = feature_bytes_per_player_cell(hist, 2) * cells + 2 * G * 8 * (2 * window)
     peak, peak_kind = peaks()
     achieved = nbytes / (feat_ms * 1e-3) / 1e9
-    if rank == 0:
-        line = {
-            "metric": "game frames/s with the 38-channel feature tensor and temporal tokens", "value": value,
-            "unit": "frames/s",
-            "n_gpus": world, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
-            "config": {"workload": "features-65536x24x24", "games_per_gpu": G, "hist": hist, "channels": 24 + 2 * hist,
-                       "temporal_window": window,
-                       "l2": "inputs larger than L2 (features 11.5 GB + memory 2.9 GB per frame)"},
+    del fb, env, out, fout, ser
+    torch.cuda.empty_cache()
+    return {"workload": "features-65536x24x24" if G == 65536 else f"features-{G}x24x24", "games": G,
+            "hist": hist, "channels": 24 + 2 * hist, "temporal_window": window,
+            "frames_per_s": G * K / (elapsed_ms * 1e-3), "ms_per_frame": elapsed_ms / K,
+            "step_launch_ms": step_ms, "feature_launch_ms": feat_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (FEATURE_NCU_TRAFFIC["bytes_per_launch"]
                                      if FEATURE_NCU_TRAFFIC["kernel_sha1"] == kernel_sha1("gk_features.cu")
@@ -598,9 +681,25 @@ def run_features(args, rank, world, local):
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": feat_ms,
                          "kernel_sha1": kernel_sha1("gk_features.cu"),
-                         "kernel": "k_features (38-channel feature tensor)"},
-            "step_launch_ms": step_ms,
-            "gpu_launches": 2 * K,
+                         "kernel": "k_features (38-channel feature tensor)"}}
+
+
+def run_features(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        rec = features_record(args, args.games or 65536, args.steps, rank)
+    if rank == 0:
+        line = {
+            "metric": "game frames/s with the 38-channel feature tensor and temporal tokens",
+            "value": rec["frames_per_s"] * world, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_frame"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
+            "config": {"workload": rec["workload"], "games_per_gpu": rec["games"], "hist": rec["hist"],
+                       "channels": rec["channels"], "temporal_window": rec["temporal_window"],
+                       "l2": "inputs larger than L2 (features 11.5 GB + memory 2.9 GB per frame)"},
+            "roofline": rec["roofline"], "step_launch_ms": rec["step_launch_ms"], "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -616,52 +715,43 @@ def owned_player_cells(env) -> float:
     return float(np.count_nonzero(owner >= 0))
 
 
-def run_sampling(args, rank, world, local):
-    """Device self-play shape: per frame, actions sampled from H x W x 9
-    logits (k_sample), then the step (k_generals without the fused policy)."""
+def sampler_record(args, G: int, K: int, rank: int = 0, clk=None) -> dict:
+    """Device self-play shape at mid-game: per frame, actions sampled from
+    H x W x 9 logits (the sampler kernel), then the step (without the fused
+    policy); the sampler launch timed on its own."""
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
     from paper_2606_23348_gb300.workloads import shard, workload
 
-    torch.cuda.set_device(local)
-    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=args.games or None)
-    G = int(H.shape[0])
+    H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=G)
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
-    out = env.new_outputs()
-    acts = env.new_actions()
+    out, acts = env.new_outputs(), env.new_actions()
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     logits = torch.randn(int(env.layout.plane_cells) * 9, generator=g, device="cuda") * 2.0
     stream = torch.cuda.current_stream()
-    # pre-roll to mid-game (the benchmark policy), so players own territory
     env.policy(POLICY_SEED, acts)
-    for _ in range(SAMPLE_PREROLL):
+    for _ in range(SAMPLE_PREROLL):  # to mid-game, so that players own territory
         env.step_policy(acts, out, POLICY_SEED, acts)
     for _ in range(max(3, args.warmup)):
         env.sample_actions(logits, POLICY_SEED, acts)
         env.step(acts, out)
     torch.cuda.synchronize()
     owned0 = owned_player_cells(env)
-    K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    with ClockSampler(local) as clk:
-        barrier(world)
-        torch.cuda.synchronize()
-        t_all[0].record(stream)
-        for k in range(K):
-            ev[k][0].record(stream)
-            env.sample_actions(logits, POLICY_SEED, acts)
-            ev[k][1].record(stream)
-            env.step(acts, out)
-            ev[k][2].record(stream)
-        t_all[1].record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-    elapsed_ms = max_over_ranks(t_all[0].elapsed_time(t_all[1]), world)
+    t_all[0].record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        env.sample_actions(logits, POLICY_SEED, acts)
+        ev[k][1].record(stream)
+        env.step(acts, out)
+        ev[k][2].record(stream)
+    t_all[1].record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = t_all[0].elapsed_time(t_all[1])
     samp_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     step_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    value = sum_over_ranks(float(G * K), world) / (elapsed_ms * 1e-3)
     # the logits a sampler must read (36 B per cell each player owns: legal entries lie only
     # there), board 4 B per cell once per game, actions 4 B per player; owned cells averaged
     # over the start and the end of the timed region
@@ -669,16 +759,12 @@ def run_sampling(args, rank, world, local):
     nbytes = 36.0 * owned + 4.0 * 576 * G + 4.0 * 2 * G
     peak, peak_kind = peaks()
     achieved = nbytes / (samp_ms * 1e-3) / 1e9
-    if rank == 0:
-        line = {
-            "metric": "game frames/s, actions sampled on the device from H x W x 9 logits", "value": value,
-            "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
-            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 logits, int16 state",
-            "data": "synthetic (seeded counter-hash maps, N(0, 2) logits, auto-reset)",
-            "config": {"workload": "sample-65536x24x24", "games_per_gpu": G, "preroll_frames": SAMPLE_PREROLL,
-                       "owned_cells_per_player": owned / (2 * G),
-                       "l2": "inputs larger than L2 (logits 2.7 GB)"},
+    del env, out, logits
+    torch.cuda.empty_cache()
+    return {"workload": "sample-65536x24x24" if G == 65536 else f"sample-{G}x24x24", "games": G,
+            "preroll_frames": SAMPLE_PREROLL, "owned_cells_per_player": owned / (2 * G),
+            "frames_per_s": G * K / (elapsed_ms * 1e-3), "ms_per_frame": elapsed_ms / K,
+            "sampler_launch_ms": samp_ms, "step_launch_ms": step_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (SAMPLE_NCU["bytes_per_launch"]
                                      if SAMPLE_NCU["kernel_sha1"] == kernel_sha1("gk_sample.cu")
@@ -686,26 +772,41 @@ def run_sampling(args, rank, world, local):
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": samp_ms,
                          "kernel": "k_sample_cta (H x W x 9 policy sampling, a CTA per game)"},
-            "issue_roofline": issue_roofline(samp_ms, G, clk, SAMPLE_NCU, "gk_sample.cu"),
-            "step_launch_ms": step_ms,
-            "gpu_launches": 2 * K,
-            "clocks": clk.summary(),
+            "issue_roofline": issue_roofline(samp_ms, G, clk, SAMPLE_NCU, "gk_sample.cu") if clk else None}
+
+
+def run_sampling(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        rec = sampler_record(args, args.games or 65536, args.steps, rank, clk)
+    rec["issue_roofline"] = issue_roofline(rec["sampler_launch_ms"], rec["games"], clk, SAMPLE_NCU, "gk_sample.cu")
+    if rank == 0:
+        line = {
+            "metric": "game frames/s, actions sampled on the device from H x W x 9 logits",
+            "value": rec["frames_per_s"] * world, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_frame"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 logits, int16 state",
+            "data": "synthetic (seeded counter-hash maps, N(0, 2) logits, auto-reset)",
+            "config": {"workload": rec["workload"], "games_per_gpu": rec["games"], "preroll_frames": SAMPLE_PREROLL,
+                       "owned_cells_per_player": rec["owned_cells_per_player"],
+                       "l2": "inputs larger than L2 (logits 2.7 GB)"},
+            "roofline": rec["roofline"], "issue_roofline": rec["issue_roofline"],
+            "step_launch_ms": rec["step_launch_ms"], "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
 
 
-def run_selfplay(args, rank, world, local):
+def selfplay_record(args, rank: int = 0, T: int = 512, G: int = 512) -> dict:
     """The paper's rollout shape (512 environments x 512 steps) as a device
     self-play loop: per frame, actions sampled from H x W x 9 logits, the
     step, and the feature tensor with temporal tokens, with no host round
-    trip; plain launches and the same 512 frames replayed as one CUDA graph."""
+    trip; plain launches and the same T frames replayed as one CUDA graph."""
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
     from paper_2606_23348_gb300.workloads import shard, workload
 
-    torch.cuda.set_device(local)
-    G, T = 512, 512
     H, W, mode, P, gen, _ = workload("1v1-65536x24x24", G=G)
     env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
     fb = env.features(7, 512)
@@ -738,12 +839,11 @@ def run_selfplay(args, rank, world, local):
         for _ in range(T):
             frame()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
-        torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
     res["graph"] = e0.elapsed_time(e1)
 
     def per_frame_ms(fn):
@@ -763,19 +863,30 @@ def run_selfplay(args, rank, world, local):
              "step": per_frame_ms(lambda: env.step(acts, out))}
     parts["features (rest of a plain frame)"] = res["plain"] / T - parts["sample"] - parts["step"]
     best = min(res, key=res.get)
-    value = sum_over_ranks(float(G * T), world) / (max_over_ranks(res[best], world) * 1e-3)
+    del graph, fb, env
+    torch.cuda.empty_cache()
+    return {"workload": "selfplay-512x512", "games": G, "frames": T, "hist": 7, "temporal_window": 512,
+            "frames_per_s": G * T / (res[best] * 1e-3), "ms_per_frame": res[best] / T, "best_form": best,
+            "forms": {k: {"ms_per_frame": v / T, "frames_per_s": G * T / (v * 1e-3)} for k, v in res.items()},
+            "ms_per_frame_by_kernel": parts}
+
+
+def run_selfplay(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        rec = selfplay_record(args, rank)
     if rank == 0:
         print(json.dumps({
-            "metric": "game frames/s of a device self-play rollout (sample, step, features)", "value": value,
-            "unit": "frames/s", "n_gpus": world, "steps": T, "warmup": max(3, args.warmup),
-            "ms_per_step": res[best] / T, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 logits and features, int16 state",
+            "metric": "game frames/s of a device self-play rollout (sample, step, features)",
+            "value": rec["frames_per_s"] * world, "unit": "frames/s", "n_gpus": world, "steps": rec["frames"],
+            "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_frame"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 logits and features, int16 state",
             "data": "synthetic (seeded counter-hash maps, N(0, 1) logits, auto-reset)",
-            "config": {"workload": "selfplay-512x512", "games_per_gpu": G, "frames": T, "hist": 7,
-                       "temporal_window": 512, "l2": "fits in L2 (small batch; latency-bound)"},
-            "forms": {k: {"ms_per_frame": v / T, "frames_per_s": G * T / (v * 1e-3)} for k, v in res.items()},
-            "ms_per_frame_by_kernel": parts,
-            "gpu_launches": 3 * T, "clocks": clk.summary()}), flush=True)
+            "config": {"workload": "selfplay-512x512", "games_per_gpu": rec["games"], "frames": rec["frames"],
+                       "hist": 7, "temporal_window": 512, "l2": "fits in L2 (small batch; latency-bound)"},
+            "forms": rec["forms"], "ms_per_frame_by_kernel": rec["ms_per_frame_by_kernel"],
+            "gpu_launches": 3 * rec["frames"], "clocks": clk.summary()}), flush=True)
 
 
 def run_batch_sweep(args, rank, world, local):
@@ -899,9 +1010,17 @@ def main():
     ap.add_argument("--rollout", type=int, default=64, help="frames per rollout (ragged / mixed workloads)")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--served-seconds", type=float, default=10.0, help="measured window of the served workload")
+    ap.add_argument("--served-seconds-default", type=float, default=3.0,
+                    help="measured window of the served record inside the default line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only (no ragged / mixed / served / features / sampler / self-play records)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus))
     rank, world, local = dist_setup(args.gpus)
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but {world} ranks were started")
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -340,6 +340,10 @@ typedef struct gen_server_stats {
     double lat_p50_ms, lat_p99_ms, lat_mean_ms; /* submit to result in the caller's buffers */
     double tick_games_mean;  /* games per tick */
     double bytes_in_use, budget;
+    uint64_t sessions_waited_budget; /* admissions that waited while the byte budget was full */
+    double peak_bytes_in_use;        /* most bytes sessions held at once in the window */
+    double service_p50_ms, service_p99_ms; /* submit to result, as seen by the server */
+    double offered_requests_per_s;   /* simulations: the clients' request rate (open loop: arrivals) */
 } gen_server_stats;
 
 /* Allocates the arenas for the configured capacities (device memory, and
@@ -390,9 +394,19 @@ typedef struct gen_sim_config {
     size_t budget_bytes;        /* admission budget */
     int32_t host_outputs;       /* see gen_server_config */
     int32_t copy_outputs;       /* clients copy every output into their own host buffers */
+    int32_t open_loop;          /* 1: Poisson arrivals at mean_interarrival_ms, independent of completions;
+                                   latencies run from each request's scheduled arrival */
+    int32_t reserved;           /* 0 */
 } gen_sim_config;
 
-/* Run a server with closed-loop simulated clients and report its stats. */
+/* Run a server with simulated clients and report its stats.  Closed loop
+ * (open_loop 0): each client thinks for an exponential time after its
+ * previous result, then steps.  Open loop (open_loop 1): each client's
+ * requests arrive as a Poisson process at the mean interval whatever the
+ * server does; a request that arrives while the session's previous step is
+ * still out waits for it, and lat_* count from the scheduled arrival
+ * (queueing included), service_* from the submission.  Interface addition,
+ * no counterpart in the paper. */
 int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_server_stats *st);
 
 /* ---- policy sampling over the H x W x 9 action space (Sec. IV-G, App. C) --
@@ -424,6 +438,18 @@ int gen_sample_actions(gen_env *env, const float *d_logits, uint64_t seed, int32
  * launches of at least 12 x the SM count games (24 x in multi-frame
  * launches), else 1.  GEN_ERR_BAD_ARG for NULL env or a mode outside 0..2. */
 int gen_set_lane_groups(gen_env *env, int mode);
+
+/* Tuning call, no counterpart in the paper (Section IV-G runs every board
+ * size and mode in one environment; this picks how a batch of several size
+ * buckets is launched; the results are the same): 1 = one launch per size
+ * bucket, buckets after the first on side streams; 2 = one persistent
+ * work-list launch per frame (per rollout in the resident form): CTAs take
+ * items -- up to a CTA's worth of one bucket's games, largest boards first --
+ * from an atomic counter and carve their shared memory per item; 0 (default)
+ * = 2.  Batches with spawn options always take form 1.  The work list's
+ * counter belongs to the environment: order its calls on one stream.
+ * GEN_ERR_BAD_ARG for NULL env or a form outside 0..2. */
+int gen_set_batch_form(gen_env *env, int form);
 
 /* Tuning call, no counterpart in the paper.  How gen_sample_actions
  * spreads a game over the GPU (the results are the same): 1 = one warp per game, players in turn; 2 = one CTA per game with a

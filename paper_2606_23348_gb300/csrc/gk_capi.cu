@@ -104,6 +104,12 @@ struct gen_env {
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
     size_t dev_bytes = 0;  // device memory this environment holds (gen_device_bytes)
+    // work-list form: every bucket in one launch ([0] per frame, [1] multi-frame)
+    int batch_form = 0;  // 0 auto, 1 one launch per bucket, 2 one work-list launch
+    gk::BucketGeom* d_geoms = nullptr;
+    gk::WorkItem* d_items[2] = {};
+    int32_t* d_counter = nullptr;
+    int wl_items[2] = {}, wl_smem[2] = {}, wl_ctas[2] = {};
 };
 
 namespace {
@@ -123,6 +129,10 @@ void free_env(gen_env* e) {
     cudaFree(e->d_terrain);
     cudaFree(e->d_actions);
     cudaFree(e->d_iota);
+    cudaFree(e->d_geoms);
+    cudaFree(e->d_items[0]);
+    cudaFree(e->d_items[1]);
+    cudaFree(e->d_counter);
     if (e->copy) cudaStreamDestroy(e->copy);
     for (auto v : e->chunk_ev)
         if (v) cudaEventDestroy(v);
@@ -256,9 +266,30 @@ int launch_one(const Bucket& b, const KArgs& a, void* stream, const char* what) 
 
 // Every game, one launch per size bucket; buckets after the first run on
 // side streams forked from and joined back into `stream`.
+// The work-list form serves batches of several buckets without spawn
+// options (their generator runs in its own kernel).
+bool use_worklist(const gen_env* e) {
+    const bool spawn = e->prm.max_general_dist > 0 || e->prm.bfs_distance || e->prm.castle_radius > 0;
+    return e->buckets.size() > 1 && e->d_items[0] && !spawn && e->batch_form != 1;
+}
+
 template <class Fill>
 int launch_buckets(gen_env* e, int op, Fill fill, void* stream, const char* what) {
     const size_t nb = e->buckets.size();
+    if (use_worklist(e)) {
+        KArgs a = base_args(e, e->all, op);
+        fill(a);
+        const int m = (a.frames > 1 || a.action_log) ? 1 : 0;
+        gk::WArgs w;
+        w.items = e->d_items[m];
+        w.n_items = e->wl_items[m];
+        w.geoms = e->d_geoms;
+        w.order = e->d_order;
+        w.counter = e->d_counter;
+        const int rc = gk::launch_worklist(a, w, e->wl_smem[m], e->wl_ctas[m], stream);
+        if (rc != 0) return cuda_fail((cudaError_t)rc, what);
+        return GEN_OK;
+    }
     if (nb == 1) {
         KArgs a = base_args(e, e->buckets[0], op);
         fill(a);
@@ -396,6 +427,59 @@ int build_buckets(gen_env* e) {
     return GEN_OK;
 }
 
+// The work lists of a batch of several buckets: per bucket its shared-memory
+// geometry and lane-group width, and items of as many consecutive games (in
+// the bucket order, largest boards first) as one CTA of the work-list kernel
+// holds.  Rebuilt when the lane-group setting changes; synchronous.
+int build_worklist(gen_env* e) {
+    if (e->buckets.size() < 2) return GEN_OK;
+    const size_t nb = e->buckets.size();
+    std::vector<gk::BucketGeom> geoms(nb);
+    for (size_t i = 0; i < nb; ++i) {
+        const Bucket& b = e->buckets[i];
+        geoms[i].geom = gk::bucket_geom(b.npad_max, b.nw_stride, b.pmax);
+        geoms[i].group_smem = b.warp_smem;
+        geoms[i].lw = (b.pmax <= 2 && b.npad_max <= 1024 && e->lane_groups != 1) ? 16 : 32;
+        geoms[i].pad = 0;
+    }
+    if (!e->d_geoms) {
+        CUDA_TRY(dev_alloc(e, &e->d_geoms, sizeof(gk::BucketGeom) * nb), "cudaMalloc bucket geometry");
+        CUDA_TRY(dev_alloc(e, &e->d_counter, sizeof(int32_t)), "cudaMalloc work counter");
+    }
+    CUDA_TRY(cudaMemcpy(e->d_geoms, geoms.data(), sizeof(gk::BucketGeom) * nb, cudaMemcpyHostToDevice),
+             "upload bucket geometry");
+    for (int m = 0; m < 2; ++m) {
+        int smem = 0, ctas = 0;
+        const int rc = gk::worklist_shape(m == 1, &smem, &ctas);
+        if (rc != 0) return cuda_fail((cudaError_t)rc, "work-list launch shape");
+        std::vector<gk::WorkItem> items;
+        for (size_t i = 0; i < nb; ++i) {
+            const Bucket& b = e->buckets[i];
+            const int groups = 8 * (32 / geoms[i].lw);
+            const int per = std::max(1, std::min(groups, smem / b.warp_smem));
+            if (per * b.warp_smem > smem)
+                return fail(GEN_ERR_BAD_ARG, "a %d-cell board needs %d bytes of shared memory per game", b.npad_max,
+                            b.warp_smem);
+            for (int k = 0; k < b.n; k += per) {
+                gk::WorkItem it;
+                it.first = b.offset + k;
+                it.count = std::min(per, b.n - k);
+                it.bucket = (int)i;
+                it.pad = 0;
+                items.push_back(it);
+            }
+        }
+        if (!e->d_items[m])
+            CUDA_TRY(dev_alloc(e, &e->d_items[m], sizeof(gk::WorkItem) * items.size()), "cudaMalloc work list");
+        CUDA_TRY(cudaMemcpy(e->d_items[m], items.data(), sizeof(gk::WorkItem) * items.size(), cudaMemcpyHostToDevice),
+                 "upload work list");
+        e->wl_items[m] = (int)items.size();
+        e->wl_smem[m] = smem;
+        e->wl_ctas[m] = ctas;
+    }
+    return GEN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -489,7 +573,8 @@ int gen_create_ex(gen_env** out, const gen_params* p, int batch, const int32_t* 
     e->all.n = batch;
     e->all.npad_max = e->npad_max;
     e->all.pmax = e->pmax;
-    if ((rc = shape_bucket(e->all)) != GEN_OK || (rc = build_buckets(e)) != GEN_OK) {
+    if ((rc = shape_bucket(e->all)) != GEN_OK || (rc = build_buckets(e)) != GEN_OK ||
+        (rc = build_worklist(e)) != GEN_OK) {
         free_env(e);
         return rc;
     }
@@ -1286,6 +1371,14 @@ int gen_set_lane_groups(gen_env* e, int mode) {
     if (mode < 0 || mode > 2) return fail(GEN_ERR_BAD_ARG, "mode %d outside [0, 2]", mode);
     drop_graph(e);
     e->lane_groups = mode;
+    return build_worklist(e);  // the work lists' lane-group widths follow the setting
+}
+
+int gen_set_batch_form(gen_env* e, int form) {
+    if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
+    if (form < 0 || form > 2) return fail(GEN_ERR_BAD_ARG, "form %d outside [0, 2]", form);
+    drop_graph(e);
+    e->batch_form = form;
     return GEN_OK;
 }
 

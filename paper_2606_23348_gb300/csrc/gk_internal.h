@@ -173,6 +173,36 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride);
 // kernel's shared-memory limit as a side effect).  Returns a cudaError_t.
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out);
 
+// ---- work-list launch: every size bucket of a ragged batch in one launch --
+// One item: `count` games of one bucket, entries first .. first+count-1 of
+// the environment's game order (largest boards first).
+struct WorkItem {
+    int32_t first, count, bucket, pad;
+};
+// A bucket's shared-memory geometry (packed as the kernels' carve expects),
+// bytes per lane group and lane-group width (16: two games per warp, 32).
+struct BucketGeom {
+    uint32_t geom;
+    int32_t group_smem;
+    int32_t lw;
+    int32_t pad;
+};
+struct WArgs {
+    const WorkItem* items;
+    int32_t n_items;
+    const BucketGeom* geoms;
+    const int32_t* order;
+    int32_t* counter;  // next item; zeroed by launch_worklist before the kernel
+};
+// Packed geometry word of a bucket (as the kernels unpack it).
+uint32_t bucket_geom(int npad_max, int nw_stride, int pmax);
+// Dynamic shared memory per CTA and CTAs of the whole GPU for the work-list
+// kernel (`multi`: multi-frame form).  Returns a cudaError_t.
+int worklist_shape(bool multi, int* cta_smem, int* ctas);
+// Zero the item counter, then one persistent launch of `ctas` CTAs that
+// take items until the list is done.  Returns a cudaError_t.
+int launch_worklist(const KArgs& a, const WArgs& w, int cta_smem, int ctas, void* stream);
+
 // Launch the step kernel with `warps_per_cta` games per CTA on `stream`.
 // Returns a cudaError_t value.
 int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream);

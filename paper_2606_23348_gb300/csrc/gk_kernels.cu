@@ -123,9 +123,16 @@ struct Smem {
     int stride;
 };
 
-__device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
+// A warp's shared-memory geometry packed in one word: padded cells of the
+// largest board (13 bits), bitset stride in words (8 bits), players (4 bits).
+__host__ __device__ __forceinline__ uint32_t pack_geom(int npad_max, int nw_stride, int pmax) {
+    return (uint32_t)npad_max | ((uint32_t)nw_stride << 13) | ((uint32_t)pmax << 21);
+}
+__device__ __forceinline__ uint32_t geom_of(const KArgs& a) { return pack_geom(a.npad_max, a.nw_stride, a.pmax); }
+
+__device__ __forceinline__ Smem carve_geom(char* base, uint32_t geom) {
     Smem s;
-    const int np = a.npad_max, st = a.nw_stride, pm = a.pmax;
+    const int np = (int)(geom & 0x1FFFu), st = (int)((geom >> 13) & 0xFFu), pm = (int)(geom >> 21);
     s.army = reinterpret_cast<int16_t*>(base);
     s.owner = reinterpret_cast<int8_t*>(base + 2 * np);
     s.terrain = reinterpret_cast<uint8_t*>(base + 3 * np);
@@ -148,6 +155,7 @@ __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
     s.stride = st;
     return s;
 }
+__device__ __forceinline__ Smem carve(char* base, const KArgs& a) { return carve_geom(base, geom_of(a)); }
 
 struct Game {
     int H, W, N, Npad, nch, P, mode, nw;
@@ -735,17 +743,18 @@ __device__ __forceinline__ void generate_body(const KArgs& a, const Game& g, con
 // the game and shared-memory views themselves, so that the step kernel never
 // materialises those structures in local memory for a call it rarely makes.
 template <int LW, bool UNI>
-__device__ __noinline__ void generate(const KArgs& a, int gidx, char* warp_base, uint64_t gid, uint32_t epoch,
-                                     int warp_lane) {
-    generate_body(a, game_of<UNI>(a, gidx), carve(warp_base, a), gid, epoch, Grp<LW>(warp_lane));
+__device__ __noinline__ void generate(const KArgs& a, int gidx, char* warp_base, uint32_t geom, uint64_t gid,
+                                     uint32_t epoch, int warp_lane) {
+    generate_body(a, game_of<UNI>(a, gidx), carve_geom(warp_base, geom), gid, epoch, Grp<LW>(warp_lane));
 }
-__device__ __noinline__ void generate_spawn(const KArgs& a, int gidx, char* warp_base, uint64_t gid,
+__device__ __noinline__ void generate_spawn(const KArgs& a, int gidx, char* warp_base, uint32_t geom, uint64_t gid,
                                            uint32_t epoch, int lane) {
-    generate_spawn_body(a, game_of(a, gidx), carve(warp_base, a), gid, epoch, lane);
+    generate_spawn_body(a, game_of(a, gidx), carve_geom(warp_base, geom), gid, epoch, lane);
 }
 template <int LW, bool UNI>
-__device__ __noinline__ void derive_passable_at(const KArgs& a, int gidx, char* warp_base, int warp_lane) {
-    derive_passable(game_of<UNI>(a, gidx), carve(warp_base, a), Grp<LW>(warp_lane));
+__device__ __noinline__ void derive_passable_at(const KArgs& a, int gidx, char* warp_base, uint32_t geom,
+                                               int warp_lane) {
+    derive_passable(game_of<UNI>(a, gidx), carve_geom(warp_base, geom), Grp<LW>(warp_lane));
 }
 
 // ---- one move on lane 0 (Sec. IV-D, IV-E) ----------------------------------
@@ -1210,8 +1219,8 @@ namespace {
 
 
 template <bool MULTI, bool SPAWN, int LW, bool UNI>
-__device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const int gidx,
-                                         const Grp<LW>& t) {
+__device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const uint32_t geom,
+                                         const int gidx, const Grp<LW>& t) {
     Game g = game_of<UNI>(a, gidx);
     if constexpr (LW < 32) {
         // narrow groups run only two-player games without teams: 1v1, or a
@@ -1250,15 +1259,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
         if constexpr (SPAWN)
-            generate_spawn(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+            generate_spawn(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         else
-            generate<LW, UNI>(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+            generate<LW, UNI>(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
     } else if (a.op == OP_DERIVE) {
-        derive_passable_at<LW, UNI>(a, gidx, warp_base, t.lane + t.shift);
+        derive_passable_at<LW, UNI>(a, gidx, warp_base, geom, t.lane + t.shift);
         wrote_state = true;
     }
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
@@ -1317,9 +1326,9 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
                 if (a.auto_reset) {
                     epoch += 1;
                     if constexpr (SPAWN)
-                        generate_spawn(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+                        generate_spawn(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     else
-                        generate<LW, UNI>(a, gidx, warp_base, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+                        generate<LW, UNI>(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, t);
@@ -1412,14 +1421,52 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) 
         if (item >= a.n_items) return;
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) return;
-        run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, gidx, t);
+        run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, geom_of(a), gidx, t);
     } else {
         for (int item = blockIdx.x * gpc + grp; item < a.n_items; item += gridDim.x * gpc) {
             const int gidx = a.list ? a.list[item] : item;
             if (gidx < 0 || gidx >= a.n_games) continue;
             t.sync();
-            run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, gidx, t);
+            run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, geom_of(a), gidx, t);
         }
+    }
+}
+
+// Every size bucket of a ragged or mixed batch in one persistent launch.  A
+// CTA takes one work item at a time (an atomic counter over a list ordered
+// largest boards first), carves its shared memory for that item's bucket and
+// runs one game per lane group: two per warp for two-player buckets of small
+// boards, one per warp otherwise.  The CTA waits at a barrier between items,
+// so that the next item may carve the same bytes differently.
+template <bool MULTI>
+__global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_worklist(const KArgs a, const WArgs w) {
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(w.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= w.n_items) return;  // the same for every thread of the CTA
+        const WorkItem item = w.items[it];
+        const BucketGeom bg = w.geoms[item.bucket];
+        if (bg.lw == 16) {
+            const Grp<16> t(wl);
+            const int grp = 2 * warp + (wl >> 4);
+            if (grp < item.count) {
+                char* base = smem_raw + grp * bg.group_smem;
+                run_game<MULTI, false, 16, false>(a, carve_geom(base, bg.geom), base, bg.geom,
+                                                  w.order[item.first + grp], t);
+            }
+        } else {
+            const Grp<32> t(wl);
+            if (warp < item.count) {
+                char* base = smem_raw + warp * bg.group_smem;
+                run_game<MULTI, false, 32, false>(a, carve_geom(base, bg.geom), base, bg.geom,
+                                                  w.order[item.first + warp], t);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1457,6 +1504,48 @@ int allow_max_smem() {
         (const void*)k_generals<false, false, 8, true>,   (const void*)k_generals<true, false, 8, true>,
         (const void*)k_generals<false, true, 32, false>,  (const void*)k_generals<true, true, 32, false>};
     return limit.raise(fns, 14, 227 * 1024);
+}
+
+uint32_t bucket_geom(int npad_max, int nw_stride, int pmax) { return pack_geom(npad_max, nw_stride, pmax); }
+
+int worklist_shape(bool multi, int* cta_smem, int* ctas) {
+    // four CTAs of 8 warps per SM per frame (the register budget's limit),
+    // three in multi-frame launches; each takes an equal share of the SM's
+    // shared memory less the per-CTA reservation
+    const void* f = multi ? (const void*)k_worklist<true> : (const void*)k_worklist<false>;
+    int dev = 0, sms = 0, smem_sm = 0, reserved = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int want = multi ? 3 : 4;
+    int bytes = ((smem_sm / want - reserved - 64) / 16) * 16;  // 64: the kernel's static item slot
+    if (bytes > 227 * 1024) bytes = 227 * 1024;
+    // the kernel's own static slot counts against the per-CTA limit too
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return (int)e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 256, (size_t)bytes)) != cudaSuccess)
+        return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    *cta_smem = bytes;
+    *ctas = per_sm * sms;
+    return 0;
+}
+
+int launch_worklist(const KArgs& a, const WArgs& w, int cta_smem, int ctas, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return (int)e;
+    const bool multi = a.frames > 1 || a.action_log;
+    const int grid = ctas < w.n_items ? ctas : w.n_items;
+    if (grid <= 0) return 0;
+    if (multi)
+        k_worklist<true><<<grid, 256, cta_smem, st>>>(a, w);
+    else
+        k_worklist<false><<<grid, 256, cta_smem, st>>>(a, w);
+    return (int)cudaGetLastError();
 }
 
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {

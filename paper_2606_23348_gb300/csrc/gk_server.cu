@@ -131,6 +131,9 @@ struct Tick {
     cudaEvent_t fork = nullptr, done = nullptr;
     int32_t* d_list = nullptr;
     int32_t* h_list = nullptr;  // pinned
+    gk::WorkItem* d_items = nullptr;  // the tick's work list (one launch over every class)
+    gk::WorkItem* h_items = nullptr;  // pinned
+    int32_t* d_counter = nullptr;
     std::vector<Request*> reqs;
     bool busy = false;
     double t_launch = 0;
@@ -185,6 +188,10 @@ struct gen_server {
     cudaStream_t admin = nullptr;
     Tick ticks[2];
     std::map<std::pair<int, int>, ClassShape> shapes;
+    // work-list launches: per size class its geometry, items of a CTA's worth of games
+    gk::BucketGeom* d_geoms = nullptr;
+    int class_per_item[kClasses] = {};
+    int wl_smem = 0, wl_ctas = 0;
     std::mutex mu;
     std::condition_variable cv_req, cv_admit;
     std::deque<Request*> queue;
@@ -195,7 +202,8 @@ struct gen_server {
     // statistics
     std::mutex stat_mu;
     std::vector<double> lat;
-    uint64_t frames = 0, requests = 0, tick_count = 0, admitted = 0, waited = 0;
+    uint64_t frames = 0, requests = 0, tick_count = 0, admitted = 0, waited = 0, waited_budget = 0;
+    size_t peak_in_use = 0;  // under mu
     double t0 = 0, tick_games_sum = 0;
     std::string fatal;
 };
@@ -301,6 +309,41 @@ int launch_tick(gen_server* sv, Tick& t) {
         }
     SCUDA(cudaMemcpyAsync(t.d_list, t.h_list, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, t.stream),
           "tick list upload");
+    const bool spawn = sv->prm.max_general_dist > 0 || sv->prm.bfs_distance || sv->prm.castle_radius > 0;
+    bool fits = true;
+    for (int c = 0; c < kClasses; ++c) fits = fits && (count[c] == 0 || sv->class_per_item[c] >= 1);
+    if (!spawn && fits) {
+        // one persistent work-list launch over every class of the tick
+        int n_items = 0;
+        for (int c = 0; c < kClasses; ++c)
+            for (int64_t j = 0; j < count[c]; j += sv->class_per_item[c]) {
+                gk::WorkItem& it = t.h_items[n_items++];
+                it.first = (int32_t)(start[c] + j);
+                it.count = (int32_t)std::min<int64_t>(sv->class_per_item[c], count[c] - j);
+                it.bucket = c;
+                it.pad = 0;
+            }
+        SCUDA(cudaMemcpyAsync(t.d_items, t.h_items, sizeof(gk::WorkItem) * (size_t)n_items, cudaMemcpyHostToDevice,
+                              t.stream),
+              "tick work-list upload");
+        ClassShape cs;
+        int rc = class_shape(sv, 256, 2, &cs);
+        if (rc) return rc;
+        KArgs a = server_args(sv, gk::OP_STEP, cs);  // geometry comes with each item
+        gk::WArgs w;
+        w.items = t.d_items;
+        w.n_items = n_items;
+        w.geoms = sv->d_geoms;
+        w.order = t.d_list;
+        w.counter = t.d_counter;
+        rc = gk::launch_worklist(a, w, sv->wl_smem, sv->wl_ctas, t.stream);
+        if (rc) return sfail(GEN_ERR_CUDA, "tick launch: %s", cudaGetErrorString((cudaError_t)rc));
+        SCUDA(cudaEventRecord(t.done, t.stream), "tick event");
+        t.busy = true;
+        t.games = games;
+        t.t_launch = now_ms();
+        return GEN_OK;
+    }
     int used = 0;
     for (int c = 0; c < kClasses; ++c) used += count[c] > 0;
     if (used > 1) SCUDA(cudaEventRecord(t.fork, t.stream), "fork");
@@ -404,7 +447,11 @@ void free_server(gen_server* sv) {
         if (t.stream) cudaStreamDestroy(t.stream);
         cudaFree(t.d_list);
         cudaFreeHost(t.h_list);
+        cudaFree(t.d_items);
+        cudaFreeHost(t.h_items);
+        cudaFree(t.d_counter);
     }
+    cudaFree(sv->d_geoms);
     if (sv->admin) cudaStreamDestroy(sv->admin);
     cudaFree(sv->d_info);
     cudaFree(sv->d_scal);
@@ -522,6 +569,9 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
         if (ce == cudaSuccess) ce = cudaMalloc(&t.d_list, sizeof(int32_t) * G);
         if (ce == cudaSuccess) ce = cudaHostAlloc(&t.h_list, sizeof(int32_t) * G, cudaHostAllocPortable);
+        if (ce == cudaSuccess) ce = cudaMalloc(&t.d_items, sizeof(gk::WorkItem) * G);
+        if (ce == cudaSuccess) ce = cudaHostAlloc(&t.h_items, sizeof(gk::WorkItem) * G, cudaHostAllocPortable);
+        if (ce == cudaSuccess) ce = cudaMalloc(&t.d_counter, sizeof(int32_t));
         for (int i = 0; i < 24 && ce == cudaSuccess; ++i) {  // one per size class
             cudaStream_t s;
             cudaEvent_t v;
@@ -530,6 +580,24 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
             if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
             if (ce == cudaSuccess) t.join.push_back(v);
         }
+    }
+    if (ce == cudaSuccess) {
+        // the work-list kernel's launch shape and every size class's geometry
+        int rc = gk::worklist_shape(false, &sv->wl_smem, &sv->wl_ctas);
+        ce = (cudaError_t)rc;
+        gk::BucketGeom geoms[kClasses];
+        for (int c = 0; c < kClasses && ce == cudaSuccess; ++c) {
+            int st = 0;
+            const int npad = class_edge(c), P = class_players(c);
+            const int bytes = gk::warp_smem_bytes(npad, P, &st);
+            geoms[c].geom = gk::bucket_geom(npad, st, P);
+            geoms[c].group_smem = bytes;
+            geoms[c].lw = (P <= 2 && npad <= 1024) ? 16 : 32;
+            geoms[c].pad = 0;
+            sv->class_per_item[c] = std::min(8 * (32 / geoms[c].lw), sv->wl_smem / bytes);
+        }
+        if (ce == cudaSuccess) ce = cudaMalloc(&sv->d_geoms, sizeof(geoms));
+        if (ce == cudaSuccess) ce = cudaMemcpy(sv->d_geoms, geoms, sizeof(geoms), cudaMemcpyHostToDevice);
     }
     if (ce != cudaSuccess) {
         free_server(sv);
@@ -582,9 +650,10 @@ int gen_server_open(gen_server* sv, int n, const int32_t* h_H, const int32_t* h_
     {
         std::unique_lock<std::mutex> lk(sv->mu);
         const auto deadline = Clock::now() + std::chrono::milliseconds(wait_ms > 0 ? wait_ms : 0);
-        bool waited = false;
+        bool waited = false, over_budget = false;
         while (true) {
             if (!sv->fatal.empty()) return sfail(GEN_ERR_STATE, "server failed: %s", sv->fatal.c_str());
+            if (sv->in_use + s.bytes > sv->budget) over_budget = true;
             if (sv->in_use + s.bytes <= sv->budget) {
                 s.g0 = sv->a_games.alloc(n, 1);
                 s.c0 = s.g0 >= 0 ? sv->a_cells.alloc(s.cells, 16) : -1;
@@ -600,6 +669,7 @@ int gen_server_open(gen_server* sv, int n, const int32_t* h_H, const int32_t* h_
                 return sfail(GEN_ERR_OOM, "no room for %d games (%zu bytes) within %d ms", n, s.bytes, wait_ms);
         }
         sv->in_use += s.bytes;
+        sv->peak_in_use = std::max(sv->peak_in_use, sv->in_use);
         s.id = sv->next_id++;
         int64_t c = s.c0, pl = s.p0, sl = s.s0;
         for (auto& gi : s.info) {
@@ -622,6 +692,7 @@ int gen_server_open(gen_server* sv, int n, const int32_t* h_H, const int32_t* h_
         std::lock_guard<std::mutex> sl2(sv->stat_mu);
         sv->admitted += 1;
         sv->waited += waited ? 1 : 0;
+        sv->waited_budget += over_budget ? 1 : 0;
     }
     // generate the session's games (epoch 0), write their first observations and policy actions
     ClassShape c;
@@ -711,7 +782,14 @@ int gen_server_step(gen_server* sv, int session, const int32_t* h_actions, const
         std::unique_lock<std::mutex> lk(r.m);
         r.cv.wait(lk, [&] { return r.done; });
     }
-    if (r.rc != GEN_OK) return sfail(r.rc, "step failed: %s", sv->fatal.c_str());
+    if (r.rc != GEN_OK) {
+        std::string why;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);  // the scheduler writes fatal under mu
+            why = sv->fatal;
+        }
+        return sfail(r.rc, "step failed: %s", why.c_str());
+    }
     // results out of the session's ranges
     if (sv->host_outputs) {
         const gen_outputs& o = sv->out_host;
@@ -782,11 +860,12 @@ int gen_server_stats_get(gen_server* sv, gen_server_stats* st, int reset) {
         st->ticks = sv->tick_count;
         st->sessions_admitted = sv->admitted;
         st->sessions_waited = sv->waited;
+        st->sessions_waited_budget = sv->waited_budget;
         st->seconds = (now_ms() - sv->t0) * 1e-3;
         st->tick_games_mean = sv->tick_count ? sv->tick_games_sum / (double)sv->tick_count : 0.0;
         if (reset) {
             sv->lat.clear();
-            sv->requests = sv->frames = sv->tick_count = sv->admitted = sv->waited = 0;
+            sv->requests = sv->frames = sv->tick_count = sv->admitted = sv->waited = sv->waited_budget = 0;
             sv->tick_games_sum = 0;
             sv->t0 = now_ms();
         }
@@ -796,6 +875,8 @@ int gen_server_stats_get(gen_server* sv, gen_server_stats* st, int reset) {
         st->bytes_in_use = (double)sv->in_use;
         st->budget = (double)sv->budget;
         st->sessions_open = (uint64_t)sv->sessions.size();
+        st->peak_bytes_in_use = (double)sv->peak_in_use;
+        if (reset) sv->peak_in_use = sv->in_use;
     }
     st->frames_per_s = st->seconds > 0 ? (double)st->frames / st->seconds : 0.0;
     auto pct = [&](double q) {
@@ -809,6 +890,9 @@ int gen_server_stats_get(gen_server* sv, gen_server_stats* st, int reset) {
     double sum = 0;
     for (double x : lat) sum += x;
     st->lat_mean_ms = lat.empty() ? 0.0 : sum / (double)lat.size();
+    st->service_p50_ms = st->lat_p50_ms;
+    st->service_p99_ms = st->lat_p99_ms;
+    st->offered_requests_per_s = 0.0;
     return GEN_OK;
 }
 
@@ -824,9 +908,13 @@ void gen_server_destroy(gen_server* sv) {
     free_server(sv);
 }
 
-// Closed-loop actor clients: each waits an exponential think time, steps its
-// session with the actions the policy gave it last, and after a random
-// number of steps closes the session and opens a new one.
+// Simulated actor clients.  Each holds one session, steps it with the
+// actions the policy gave it last, and after a random number of steps closes
+// it and opens a new one.  Closed loop: an exponential think time after each
+// result.  Open loop: requests arrive as a Poisson process (exponential gaps
+// on a schedule that runs on whatever the server does); a request whose
+// arrival has passed is issued at once, and its latency counts from the
+// scheduled arrival.
 int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_server_stats* st) {
     if (!p || !cfg || !st) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
     if (cfg->clients < 1 || cfg->min_games < 1 || cfg->max_games < cfg->min_games || cfg->min_side < 1 ||
@@ -844,6 +932,13 @@ int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_serv
     sc.max_cells = std::min<int64_t>((int64_t)INT32_MAX - 4096, std::max<int64_t>(side * side * 64, 2 * max_games * mean_cells));
     const double mean_p = 2.0 * cfg->frac_1v1 + 4.0 * cfg->frac_2v2 + 8.0 * (1.0 - cfg->frac_1v1 - cfg->frac_2v2);
     sc.max_plane_cells = std::max<int64_t>(side * side * 8 * 64, (int64_t)((double)sc.max_cells * mean_p * 1.25));
+    // with outputs on the device the budget caps the planes ever admitted at
+    // budget / 6 bytes; arenas a little larger than that keep the budget the
+    // binding limit without reserving memory no session could use
+    if (!cfg->host_outputs)
+        sc.max_plane_cells = std::min<int64_t>(sc.max_plane_cells,
+                                               std::max<int64_t>(side * side * 8 * 64,
+                                                                 (int64_t)((double)cfg->budget_bytes / 6.0 * 1.15)));
     sc.host_outputs = cfg->host_outputs;
     sc.policy_seed = cfg->policy_seed;
     int rc = gen_server_create(&sv, p, &sc);
@@ -854,7 +949,13 @@ int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_serv
     std::atomic<int> errors{0};
     std::mutex err_mu;
     std::string first_err;
+    std::mutex lat_mu;
+    std::vector<double> arrival_lat;  // open loop: scheduled arrival to result, measured window only
+    const bool open_loop = cfg->open_loop != 0;
     auto client = [&](int id) {
+        using SClock = std::chrono::steady_clock;
+        auto next = SClock::now();
+        std::vector<double> my_lat;
         std::mt19937_64 rng(cfg->seed * 1000003ULL + (uint64_t)id);
         std::exponential_distribution<double> think(1.0 / std::max(1e-6, cfg->mean_interarrival_ms));
         std::uniform_int_distribution<int> ngames(cfg->min_games, cfg->max_games);
@@ -900,9 +1001,17 @@ int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_serv
             ho.done = dn.data();
             const int steps = life(rng);
             for (int k = 0; k < steps && !stop.load(); ++k) {
-                std::this_thread::sleep_for(std::chrono::duration<double, std::milli>(think(rng)));
+                const std::chrono::duration<double, std::milli> gap(think(rng));
+                if (open_loop) {
+                    next += std::chrono::duration_cast<SClock::duration>(gap);
+                    std::this_thread::sleep_until(next);
+                } else {
+                    std::this_thread::sleep_for(gap);
+                }
                 double lat = 0;
                 r = gen_server_step(sv, sid, acts.data(), cfg->copy_outputs ? &ho : nullptr, acts.data(), &lat);
+                if (open_loop && measuring.load())
+                    my_lat.push_back(std::chrono::duration<double, std::milli>(SClock::now() - next).count());
                 if (r) {
                     if (errors.fetch_add(1) == 0) {
                         std::lock_guard<std::mutex> lk(err_mu);
@@ -913,6 +1022,8 @@ int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_serv
             }
             gen_server_close(sv, sid);
         }
+        std::lock_guard<std::mutex> lk(lat_mu);
+        arrival_lat.insert(arrival_lat.end(), my_lat.begin(), my_lat.end());
     };
     std::vector<std::thread> th;
     for (int i = 0; i < cfg->clients; ++i) th.emplace_back(client, i);
@@ -920,11 +1031,26 @@ int gen_server_simulate(const gen_params* p, const gen_sim_config* cfg, gen_serv
     std::this_thread::sleep_for(std::chrono::duration<double>(std::min(2.0, 0.25 * cfg->seconds)));
     gen_server_stats tmp;
     gen_server_stats_get(sv, &tmp, 1);
+    measuring.store(true);
     std::this_thread::sleep_for(std::chrono::duration<double>(cfg->seconds));
     gen_server_stats_get(sv, st, 0);
+    measuring.store(false);
     stop.store(true);
     for (auto& t : th) t.join();
     gen_server_destroy(sv);
+    st->offered_requests_per_s = (double)cfg->clients * 1e3 / std::max(1e-6, cfg->mean_interarrival_ms);
+    if (open_loop && !arrival_lat.empty()) {
+        auto pct = [&](double q) {
+            const size_t k = std::min(arrival_lat.size() - 1, (size_t)(q * (double)(arrival_lat.size() - 1) + 0.5));
+            std::nth_element(arrival_lat.begin(), arrival_lat.begin() + (long)k, arrival_lat.end());
+            return arrival_lat[k];
+        };
+        st->lat_p50_ms = pct(0.50);
+        st->lat_p99_ms = pct(0.99);
+        double sum = 0;
+        for (double x : arrival_lat) sum += x;
+        st->lat_mean_ms = sum / (double)arrival_lat.size();
+    }
     if (errors.load()) return sfail(GEN_ERR_STATE, "%d client errors; first: %s", errors.load(), first_err.c_str());
     return GEN_OK;
 }

@@ -61,7 +61,8 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_step_host_static", "gen_set_spawn_range", "gen_features_create", "gen_features_layout",
            "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
            "gen_features_build_ex", "gen_features_set_form", "gen_sample_actions", "gen_set_sample_form",
-           "gen_set_lane_groups", "gen_outputs_get", "gen_device_bytes", "gen_save_state", "gen_load_state")
+           "gen_set_lane_groups", "gen_outputs_get", "gen_device_bytes", "gen_save_state", "gen_load_state",
+           "gen_set_batch_form")
 
 ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
 
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
             "gen_set_sample_form": (C.c_int, [vp, C.c_int]),
             "gen_set_lane_groups": (C.c_int, [vp, C.c_int]),
             "gen_outputs_get": (C.c_int, [vp, C.POINTER(GenOutputs)]),
+            "gen_set_batch_form": (C.c_int, [vp, C.c_int]),
             "gen_device_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
             "gen_save_state": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t), vp]),
             "gen_load_state": (C.c_int, [vp, vp, C.c_size_t, vp]),
@@ -356,6 +358,14 @@ class GeneralsEnv:
         (two, four in rollouts, wherever the games allow) or LANES_AUTO (by
         batch size)."""
         _check(self.lib.gen_set_lane_groups(self.h, int(mode)), "gen_set_lane_groups")
+
+    BATCH_AUTO, BATCH_BUCKETS, BATCH_WORKLIST = 0, 1, 2
+
+    def set_batch_form(self, form: int):
+        """How a batch of several size buckets launches: BATCH_BUCKETS (one
+        launch per bucket), BATCH_WORKLIST (one persistent work-list launch)
+        or BATCH_AUTO (the work list)."""
+        _check(self.lib.gen_set_batch_form(self.h, int(form)), "gen_set_batch_form")
 
     def set_sample_form(self, form: int):
         """How sample_actions spreads a game over the GPU: 1 one warp per

@@ -23,7 +23,9 @@ class ServerStats(C.Structure):
                 ("sessions_open", C.c_uint64), ("sessions_admitted", C.c_uint64), ("sessions_waited", C.c_uint64),
                 ("seconds", C.c_double), ("frames_per_s", C.c_double), ("lat_p50_ms", C.c_double),
                 ("lat_p99_ms", C.c_double), ("lat_mean_ms", C.c_double), ("tick_games_mean", C.c_double),
-                ("bytes_in_use", C.c_double), ("budget", C.c_double)]
+                ("bytes_in_use", C.c_double), ("budget", C.c_double), ("sessions_waited_budget", C.c_uint64),
+                ("peak_bytes_in_use", C.c_double), ("service_p50_ms", C.c_double), ("service_p99_ms", C.c_double),
+                ("offered_requests_per_s", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -35,7 +37,7 @@ class SimConfig(C.Structure):
                 ("frac_1v1", C.c_double), ("frac_2v2", C.c_double), ("min_steps", C.c_int32),
                 ("max_steps", C.c_int32), ("seconds", C.c_double), ("seed", C.c_uint64),
                 ("policy_seed", C.c_uint64), ("budget_bytes", C.c_size_t), ("host_outputs", C.c_int32),
-                ("copy_outputs", C.c_int32)]
+                ("copy_outputs", C.c_int32), ("open_loop", C.c_int32), ("reserved", C.c_int32)]
 
 
 SERVER_EXPORTS = ("gen_server_create", "gen_server_open", "gen_server_session_layout", "gen_server_step",

@@ -65,14 +65,16 @@ def test_c0_1v1_64x15x15_500_turns(lanes):
     rollout_policy(env, orc, frames, policy_seed=2, tag="c0")
 
 
+@pytest.mark.parametrize("batch", [1, 2], ids=["buckets", "worklist"])
 @LANES_AUTO
-def test_mixed_modes_tiny_maps_captures_and_resets(lanes):
+def test_mixed_modes_tiny_maps_captures_and_resets(lanes, batch):
     """Ragged 1v1 / 2v2 / FFA games on small boards: captures, land transfer, eliminations,
     truncation and auto-reset all happen within a few hundred frames."""
     G = 96
     H, W, mode, P = shapes(G, (3, 9), ((0, 0.34), (1, 0.33), (2, 0.33)), seed=5)
     P = np.where(mode == 2, np.minimum(8, H * W), P).astype(np.int32)
     env, orc = pair(H, W, mode, P, lanes=lanes, seed=11, min_general_dist=1, n_cities=1, max_turns=90)
+    env.set_batch_form(batch)
     rollout_policy(env, orc, 300, policy_seed=7, tag="mixed")
     st = env.read_state()[3]
     assert st[:, 2].max() >= 2, "expected several resets"
@@ -398,3 +400,38 @@ def test_host_step_pipelined_matches_device_step():
             assert torch.equal(ht, dt.cpu()), f"frame {f}: {name}"
         assert torch.equal(h_next, acts.cpu()), f"frame {f}: next actions"
         h_act.copy_(h_next)
+
+
+def test_two_shards_concatenate_to_one_batch():
+    """Replicas with disjoint game ids (the multi-GPU partition): two
+    environments holding games [0, G) and [G, 2G) with game_id_base 0 and G
+    produce, concatenated, exactly the bytes of one environment of all 2G
+    games, which matches the oracle."""
+    import torch
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    G = 40
+    H, W, mode, P = shapes(2 * G, (5, 16), ((0, 0.4), (1, 0.3), (2, 0.3)), seed=31)
+    kw = dict(seed=8, min_general_dist=1, n_cities=2, max_turns=25)
+    full = GeneralsEnv(H, W, mode, P, **kw)
+    parts = [GeneralsEnv(H[:G], W[:G], mode[:G], P[:G], game_id_base=0, **kw),
+             GeneralsEnv(H[G:], W[G:], mode[G:], P[G:], game_id_base=G, **kw)]
+    orc = OracleEnv(H, W, mode, P, **kw)
+    envs = [full] + parts
+    outs = [e.new_outputs() for e in envs]
+    acts = [e.new_actions() for e in envs]
+    for e, a in zip(envs, acts):
+        e.policy(5, a)
+    for f in range(50):
+        a_orc = orc.policy(5)
+        for e, o, a in zip(envs, outs, acts):
+            e.step_policy(a, o, 5, a)
+        orc.step(a_orc)
+    torch.cuda.synchronize()
+    for k, t in enumerate(outs[0].tensors()):
+        cat = torch.cat([outs[1].tensors()[k], outs[2].tensors()[k]])
+        assert torch.equal(t, cat), f"output array {k}"
+    assert torch.equal(acts[0], torch.cat(acts[1:]))
+    st = [e.read_state() for e in envs]
+    for k in range(4):
+        np.testing.assert_array_equal(st[0][k], np.concatenate([st[1][k], st[2][k]]))
+    compare_frame(full, outs[0], orc, "full batch vs oracle")

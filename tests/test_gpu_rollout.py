@@ -33,7 +33,7 @@ def frame_view(env, out, k):
     return v
 
 
-def make_pair(G=48, seed=3, two_player=False, lanes=0):
+def make_pair(G=48, seed=3, two_player=False, lanes=0, batch=0):
     from paper_2606_23348_gb300.generals import GeneralsEnv
     modes = ((0, 0.5), (2, 0.5)) if two_player else ((0, 0.4), (1, 0.3), (2, 0.3))
     H, W, mode, P = shapes(G, (4, 20), modes, seed=seed)
@@ -44,13 +44,20 @@ def make_pair(G=48, seed=3, two_player=False, lanes=0):
     env = GeneralsEnv(H, W, mode, P, **kw)
     if lanes:
         env.set_lane_groups(lanes)
+    if batch:
+        env.set_batch_form(batch)
     return env, OracleEnv(H, W, mode, P, **kw)
 
 
+# a batch of several size buckets: one launch per bucket, or one work-list launch
+BATCH = pytest.mark.parametrize("batch", [1, 2], ids=["buckets", "worklist"])
+
+
+@BATCH
 @pytest.mark.parametrize("lanes", [0, 2], ids=["auto", "narrow"])
 @pytest.mark.parametrize("form", [0, 1, 2], ids=["resident", "graph", "launches"])
-def test_rollout_matches_oracle(form, lanes):
-    env, orc = make_pair(lanes=lanes)
+def test_rollout_matches_oracle(form, lanes, batch):
+    env, orc = make_pair(lanes=lanes, batch=batch)
     assert len(set(zip(env.npad // 256, env.P))) > 1  # several size buckets
     check_rollout(env, orc, form)
 
@@ -121,13 +128,15 @@ def check_rollout(env, orc, form):
 
 
 def test_rollout_forms_agree_on_full_workload_slice():
-    """The three forms give identical bytes on a ragged 15..30 batch."""
+    """The three rollout forms, each with one launch per size bucket and with
+    the work-list launch, give identical bytes on a ragged 15..30 batch."""
     import torch
     from paper_2606_23348_gb300.generals import GeneralsEnv
     H, W, mode, P = shapes(4096, (15, 30), seed=7)
     res = []
-    for form in (0, 1, 2):
+    for form, batch in ((0, 2), (1, 2), (2, 2), (0, 1), (1, 1), (2, 1)):
         env = GeneralsEnv(H, W, mode, P, seed=7, n_cities=-1, city_per_mille=20)
+        env.set_batch_form(batch)
         out = env.new_outputs(frames=4)
         acts = env.new_actions()
         env.policy(9, acts)

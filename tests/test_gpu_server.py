@@ -145,6 +145,8 @@ def test_admission_against_budget():
     assert got["sid"] != sid
     st = srv.stats()
     assert st["sessions_waited"] >= 1 and st["sessions_open"] == 1
+    assert st["sessions_waited_budget"] >= 1, "the byte budget, not the arenas, held the second session back"
+    assert need <= st["peak_bytes_in_use"] <= int(need * 1.5)
 
 
 def test_simulated_clients_run():
@@ -153,3 +155,21 @@ def test_simulated_clients_run():
                   max_side=20, frac_1v1=0.4, frac_2v2=0.3, min_steps=5, max_steps=20, seconds=1.0, seed=3,
                   policy_seed=9, budget_bytes=512 * MB, host_outputs=1, copy_outputs=1)
     assert st["requests"] > 100 and st["frames"] > 0 and st["lat_p99_ms"] >= st["lat_p50_ms"] > 0
+
+
+def test_open_loop_latency_counts_from_the_scheduled_arrival():
+    """Open-loop Poisson clients: every request is timed from its scheduled
+    arrival, so the arrival-based percentiles are at least the server-side
+    (submission) ones, and an overloaded run (arrivals far faster than the
+    steps) queues: its p50 grows well past its service time."""
+    from paper_2606_23348_gb300.server import simulate
+    base = dict(clients=16, min_games=16, max_games=64, min_side=8, max_side=20, frac_1v1=0.4, frac_2v2=0.3,
+                min_steps=5, max_steps=20, seconds=1.0, seed=3, policy_seed=9, budget_bytes=512 * MB,
+                host_outputs=1, copy_outputs=1, open_loop=1)
+    st = simulate(PARAMS, mean_interarrival_ms=2.0, **base)
+    assert st["requests"] > 100 and st["frames"] > 0
+    assert st["offered_requests_per_s"] == pytest.approx(16 * 500.0)
+    assert st["lat_p99_ms"] >= st["lat_p50_ms"] > 0 and st["service_p99_ms"] >= st["service_p50_ms"] > 0
+    assert st["lat_p50_ms"] >= 0.9 * st["service_p50_ms"]
+    over = simulate(PARAMS, mean_interarrival_ms=0.001, **base)  # a million requests per second offered
+    assert over["lat_p50_ms"] > 5 * over["service_p50_ms"]

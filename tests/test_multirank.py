@@ -91,3 +91,24 @@ def test_two_ranks_equal_one_process():
         assert p.exitcode == 0
     assert got == run_games(0, H, W, mode, P)
     assert t == 2.0 and n == world * G_PER_RANK
+
+
+def test_bench_starts_its_own_ranks():
+    """`bench.py --gpus 2` started without a launcher runs itself as two ranks
+    (torch.distributed.run, gloo on a host without a GPU, rendezvous on
+    127.0.0.1) and prints one line from rank 0.  The reference arm needs no
+    GPU, so the whole N-rank path of the bench runs here."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    env.pop("WORLD_SIZE", None)
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--impl", "reference",
+                        "--steps", "2", "--warmup", "3"], capture_output=True, text=True, timeout=300, env=env,
+                       cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
