@@ -117,6 +117,7 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -317,7 +318,7 @@ def run_ours(args, rank, world, local):
     env.policy(POLICY_SEED, acts)
     # pre-roll to mid-game (players own territory, auto-resets under way),
     # then the untimed warm-up steps
-    for _ in range(STEP_PREROLL + args.warmup):
+    for _ in range(args.preroll + args.warmup):
         env.step_policy(acts, out, POLICY_SEED, acts)
     torch.cuda.synchronize()
 
@@ -415,7 +416,8 @@ def run_ours(args, rank, world, local):
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int16",
             "data": "synthetic (seeded counter-hash maps, random legal policy, auto-reset)",
-            "config": {"workload": WORKLOAD, "games_per_gpu": G, "board": "24x24", "mode": "1v1",
+            "config": {"workload": WORKLOAD, "games_per_gpu": G, "preroll_frames": args.preroll, "board": "24x24",
+                       "mode": "1v1",
                        "cities": 12, "mountains": 0.2, "policy": "uniform legal, split p=0.2",
                        "parallelism": f"replicas x{world} (disjoint game ids)",
                        "l2": "inputs larger than L2 (state 151 MB + outputs 529 MB per step)",
@@ -437,7 +439,8 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0) -> dict:
+def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0, batches=(1, 2),
+                   rollouts: bool = True) -> dict:
     """A ragged or mixed workload in every launch form, each with both batch
     forms (one launch per size bucket on forked streams, and one persistent
     work-list launch over every bucket): per-frame launches, the same K frames
@@ -464,6 +467,8 @@ def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0)
     out1 = env.new_outputs()
     outK = env.new_outputs(frames=K)
     for bname, batch in (("buckets", env.BATCH_BUCKETS), ("worklist", env.BATCH_WORKLIST)):
+        if batch not in batches:
+            continue
         env.set_batch_form(batch)
         for _ in range(max(3, args.warmup)):
             env.step_policy(acts, out1, POLICY_SEED, acts)
@@ -477,7 +482,7 @@ def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0)
         forms[f"plain_{bname}"] = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms,
                                    "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak,
                                    "launches_per_frame": len_buckets(env) if batch == 1 else 1}
-        for fname, form in (("graph", 1), ("resident", 0)):
+        for fname, form in ((("graph", 1), ("resident", 0)) if rollouts else ()):
             for _ in range(2):
                 env.rollout(K, POLICY_SEED, acts, outK, None, form)
             torch.cuda.synchronize()
@@ -495,7 +500,8 @@ def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0)
     buckets = len_buckets(env)
     del out1, outK, env
     torch.cuda.empty_cache()
-    best_plain = max(("plain_buckets", "plain_worklist"), key=lambda k: forms[k]["frames_per_s"])
+    best_plain = max((k for k in ("plain_buckets", "plain_worklist") if k in forms),
+                     key=lambda k: forms[k]["frames_per_s"])
     p = forms[best_plain]
     return {"workload": name, "games": G, "rollout_frames": K, "size_buckets": buckets, "autotune": tune,
             "forms": forms,
@@ -513,7 +519,8 @@ def run_rollout_workload(args, rank, world, local):
     torch.cuda.set_device(local)
     K = args.rollout
     rounds = max(1, args.steps // K)
-    rec = rollout_record(args, args.workload, K, rounds, rank)
+    rec = rollout_record(args, args.workload, K, rounds, rank, (args.batch,) if args.batch else (1, 2),
+                         not args.plain_only)
     forms = rec["forms"]
     best = max(forms, key=lambda k: forms[k]["frames_per_s"])
     if rank == 0:
@@ -541,7 +548,8 @@ SERVED_SIM = dict(clients=256, mean_interarrival_ms=2.0, min_games=64, max_games
 def _served_row(st: dict) -> dict:
     keep = ("frames_per_s", "requests", "lat_p50_ms", "lat_p99_ms", "lat_mean_ms", "service_p50_ms", "service_p99_ms",
             "offered_requests_per_s", "tick_games_mean", "sessions_admitted", "sessions_waited",
-            "sessions_waited_budget", "peak_bytes_in_use", "budget", "seconds")
+            "sessions_waited_budget", "peak_bytes_in_use", "budget", "seconds", "tick_gpu_ms_mean",
+            "tick_host_ms_mean")
     return {k: st[k] for k in keep}
 
 
@@ -552,8 +560,9 @@ def served_record(args, seconds: float, sweep: bool = False, admission: bool = F
     continuously, against an 80 GB admission budget; outputs stay on the
     device (GPU actors).  Beside it the plain bucketed step kernel on a batch
     of the same shape mix.  sweep: the same clients at 2, 4 and 8 times the
-    offered load.  admission: an 80 GB run whose sessions (FFA-8, 16,384 to
-    32,768 games each) outgrow the budget, so that admission defers."""
+    offered load.  admission: an 80 GB run whose 96 clients' sessions (FFA-8,
+    16,384 to 32,768 games each) outgrow the budget, so that admission
+    defers."""
     import torch
 
     from paper_2606_23348_gb300.generals import GeneralsEnv
@@ -571,10 +580,10 @@ def served_record(args, seconds: float, sweep: bool = False, admission: bool = F
             st = simulate(params, seconds=seconds, **{**SERVED_SIM, "mean_interarrival_ms": mean})
             rec["load_sweep"].append({"mean_interarrival_ms": mean, **_served_row(st)})
     if admission:
-        st = simulate(params, seconds=seconds, **{**SERVED_SIM, "clients": 64, "min_games": 16384,
+        st = simulate(params, seconds=seconds, **{**SERVED_SIM, "clients": 96, "min_games": 16384,
                                                   "max_games": 32768, "frac_1v1": 0.0, "frac_2v2": 0.0,
                                                   "min_steps": 10, "max_steps": 40, "open_loop": 0})
-        rec["admission_80gb"] = {"sessions": "64 clients x 16,384..32,768 FFA-8 games, sides 15..40, closed loop",
+        rec["admission_80gb"] = {"sessions": "96 clients x 16,384..32,768 FFA-8 games, sides 15..40, closed loop",
                                  **_served_row(st)}
     # the plain fixed-size kernel on a batch with the same shape distribution
     G = 256 * 544
@@ -772,7 +781,7 @@ def sampler_record(args, G: int, K: int, rank: int = 0, clk=None) -> dict:
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": samp_ms,
                          "kernel": "k_sample_cta (H x W x 9 policy sampling, a CTA per game)"},
-            "issue_roofline": issue_roofline(samp_ms, G, clk, SAMPLE_NCU, "gk_sample.cu") if clk else None}
+            "issue_roofline": None}  # needs the clocks of the timed region: the caller adds it
 
 
 def run_sampling(args, rank, world, local):
@@ -1009,9 +1018,15 @@ def main():
                     help="fewer games than the workload (profiling captures; 0 = the workload's count)")
     ap.add_argument("--rollout", type=int, default=64, help="frames per rollout (ragged / mixed workloads)")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes first")
+    ap.add_argument("--batch", type=int, default=0, choices=[0, 1, 2],
+                    help="ragged / mixed workloads: 1 per-bucket launches only, 2 work-list launch only, 0 both")
+    ap.add_argument("--plain-only", action="store_true",
+                    help="ragged / mixed workloads: per-frame launches only (no graph or resident rollouts)")
     ap.add_argument("--served-seconds", type=float, default=10.0, help="measured window of the served workload")
     ap.add_argument("--served-seconds-default", type=float, default=3.0,
                     help="measured window of the served record inside the default line")
+    ap.add_argument("--preroll", type=int, default=STEP_PREROLL,
+                    help="benchmark-policy frames before the default workload's warm-up (mid-game state)")
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload only (no ragged / mixed / served / features / sampler / self-play records)")
     args = ap.parse_args()

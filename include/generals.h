@@ -183,6 +183,7 @@ int gen_step_policy(gen_env *env, const int32_t *d_actions, const gen_outputs *o
 #define GEN_ROLLOUT_RESIDENT 0 /* one launch; each game's state stays in shared memory for all K frames */
 #define GEN_ROLLOUT_GRAPH 1    /* K step launches replayed from a captured CUDA graph */
 #define GEN_ROLLOUT_LAUNCHES 2 /* K step launches issued one by one */
+#define GEN_ROLLOUT_AUTO 3     /* the form gen_autotune picked for this environment (resident until tuned) */
 
 /* K frames of every game, the benchmark policy choosing every action (see
  * gen_step_policy).  Every array of `out` holds K consecutive frames: frame
@@ -290,16 +291,21 @@ int gen_set_spawn_range(gen_env *env, int min_dist, int max_dist);
 int gen_set_launch(gen_env *env, int warps_per_cta);
 
 /* Tuning call, no counterpart in the paper (Section IV-G runs every board
- * size in one environment; this picks how).  Pick each size bucket's launch
- * shape (games per CTA among 2, 4, 8) by
- * timing `steps` step launches of a scratch batch with the bucket's board
- * shapes (the environment's own games do not advance).  Results are cached
- * per (padded board size class, player class, SM count) for the process.
- * A one-line-per-bucket report goes to `report` when non-NULL.
- * Synchronous.  Buckets: games are grouped by padded cells (<= 256, 512,
- * 768, 1024, 1536, 2048, 3072, 4096) and players (<= 2, 4, 8); each bucket
- * launches with its own shared-memory size, largest first, on forked
- * streams. */
+ * size in one environment; this picks how).  Times, on a scratch batch of
+ * the environment's own shapes and parameters (its games do not advance;
+ * the scratch is freed before returning), and keeps for this environment:
+ *  - games per warp (gen_set_lane_groups: by batch size, one, or several);
+ *  - for batches of several size buckets, the batch form (gen_set_batch_form);
+ *  - the rollout form that GEN_ROLLOUT_AUTO runs (8-frame rollouts, per frame);
+ *  - the sampler form (gen_set_sample_form, on zero logits);
+ *  - each size bucket's games per CTA among 2, 4, 8 in the bucket form.
+ * Results are cached for the process per batch signature (bucket classes
+ * and counts, SM count).  `steps` timed calls per candidate; a
+ * one-line-per-choice report goes to `report` when non-NULL.  Synchronous.
+ * Buckets: games are grouped by padded cells (<= 256, 512, 768, 1024, 1536,
+ * 2048, 3072, 4096) and players (<= 2, 4, 8); each bucket launches with its
+ * own shared-memory size, largest first, on forked streams.  No choice
+ * changes a result. */
 int gen_autotune(gen_env *env, int steps, char *report, size_t report_cap);
 
 /* Measurement call, no counterpart in the paper: the HBM roofline
@@ -311,7 +317,7 @@ int gen_copy_peak(size_t bytes, int reps, double *gbps);
 /* ---- env server: continuous batching of many clients' steps ------------
  * The games of every client session stay on the device.  A scheduler
  * thread folds all step requests waiting at a given moment into one tick
- * (one set of size-bucketed step launches over all their games, with the
+ * (one work-list launch over all their games, every size class at once, with the
  * benchmark policy fused); up to two ticks are in flight on separate
  * streams, so requests that arrive while one runs start on the device before
  * it ends.  Sessions are admitted while the device bytes they need fit the
@@ -344,6 +350,8 @@ typedef struct gen_server_stats {
     double peak_bytes_in_use;        /* most bytes sessions held at once in the window */
     double service_p50_ms, service_p99_ms; /* submit to result, as seen by the server */
     double offered_requests_per_s;   /* simulations: the clients' request rate (open loop: arrivals) */
+    double tick_gpu_ms_mean;         /* device time of a tick, from its first copy to its last kernel */
+    double tick_host_ms_mean;        /* scheduler time spent issuing a tick */
 } gen_server_stats;
 
 /* Allocates the arenas for the configured capacities (device memory, and
@@ -512,6 +520,13 @@ int gen_features_build(gen_features *f, float *d_out, void *stream);
  * first), 0 before the episode.  GEN_ERR_BAD_ARG when d_series is given to a
  * builder created without a window. */
 int gen_features_build_ex(gen_features *f, float *d_out, int32_t *d_series, void *stream);
+
+/* Tuning call, no counterpart in the paper.  Times `steps` builds in each
+ * form (gen_features_set_form 1 and 2) into d_out and keeps the faster;
+ * *form_out (may be NULL) receives it.  The first build folds the current
+ * frame; the timed ones repeat it (a repeated build in one frame changes
+ * nothing), so d_out holds this frame's features afterwards.  Synchronous. */
+int gen_features_autotune(gen_features *f, float *d_out, int steps, int *form_out);
 
 /* Tuning call, no counterpart in the paper.  How the builder spreads a
  * game over the GPU (the bytes written are the same): 1 = one warp per game, players in turn; 2 = one CTA per game, its

@@ -77,6 +77,7 @@ struct gen_env {
     int pmax = 0;
     int npad_max = 0;
     int sample_form = 0;  // gen_sample_actions: 0 (default) and 2 a CTA per game, 1 a warp per game
+    int rollout_form = GEN_ROLLOUT_RESIDENT;  // what GEN_ROLLOUT_AUTO runs (the autotuner's pick)
     int lane_groups = 0;  // step kernels: 0 by batch size, 1 a warp per game, 2 several per warp when allowed
     int nmax = 0;
     bool uniform = false;            // every game has the same board size and mode
@@ -164,6 +165,21 @@ void drop_graph(gen_env* e) {
     if (e->graph) cudaGraphExecDestroy(e->graph);
     e->graph = nullptr;
     e->graph_key.clear();
+}
+
+// Mean device time, ms, of one call of `run` on `s` over `reps` calls after two warm-ups.
+template <class Run>
+float time_calls(Run run, int reps, cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
+    for (int k = 0; k < 2; ++k)
+        if (run() != GEN_OK) return 1e30f;
+    cudaEventRecord(a, s);
+    for (int k = 0; k < reps; ++k)
+        if (run() != GEN_OK) return 1e30f;
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms / (float)reps;
 }
 
 int check_params(const gen_params* p) {
@@ -469,8 +485,8 @@ int build_worklist(gen_env* e) {
                 items.push_back(it);
             }
         }
-        if (!e->d_items[m])
-            CUDA_TRY(dev_alloc(e, &e->d_items[m], sizeof(gk::WorkItem) * items.size()), "cudaMalloc work list");
+        if (!e->d_items[m])  // at most one item per game, whatever the lane-group widths
+            CUDA_TRY(dev_alloc(e, &e->d_items[m], sizeof(gk::WorkItem) * (size_t)e->G), "cudaMalloc work list");
         CUDA_TRY(cudaMemcpy(e->d_items[m], items.data(), sizeof(gk::WorkItem) * items.size(), cudaMemcpyHostToDevice),
                  "upload work list");
         e->wl_items[m] = (int)items.size();
@@ -713,6 +729,7 @@ int gen_rollout(gen_env* e, int K, uint64_t policy_seed, int32_t* d_actions, con
     // K frames of outputs: the environment's own buffers hold one, so every field is the caller's
     int rc = check_outputs(out);
     if (rc) return rc;
+    if (impl == GEN_ROLLOUT_AUTO) impl = e->rollout_form;
     if (impl == GEN_ROLLOUT_RESIDENT) {
         return launch_buckets(e, gk::OP_STEP,
                               [&](KArgs& a) {
@@ -1328,6 +1345,38 @@ int gen_features_build_ex(gen_features* f, float* d_out, int32_t* d_series, void
     return GEN_OK;
 }
 
+int gen_features_autotune(gen_features* f, float* d_out, int steps, int* form_out) {
+    if (!f || !d_out) return fail(GEN_ERR_BAD_ARG, "NULL argument");
+    if (steps < 1) return fail(GEN_ERR_BAD_ARG, "steps < 1");
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "autotune stream");
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    // the first build folds the current frame; the timed ones repeat it, so
+    // both forms do the same work and the memory is as one build leaves it
+    int rc = gen_features_build_ex(f, d_out, nullptr, s);
+    float best = 1e30f;
+    int best_form = f->form;
+    for (int form : {1, 2}) {
+        if (rc) break;
+        f->form = form;
+        auto build = [&]() { return gen_features_build_ex(f, d_out, nullptr, s); };
+        const float ms = time_calls(build, steps, s, a, b);
+        if (ms < best) {
+            best = ms;
+            best_form = form;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(s);
+    f->form = best_form;
+    if (rc) return rc;
+    if (form_out) *form_out = best_form;
+    return GEN_OK;
+}
+
 int gen_features_set_form(gen_features* f, int form) {
     if (!f) return fail(GEN_ERR_BAD_ARG, "features is NULL");
     if (form < 0 || form > 2) return fail(GEN_ERR_BAD_ARG, "form %d outside [0, 2]", form);
@@ -1407,6 +1456,163 @@ int gen_set_launch(gen_env* e, int warps_per_cta) {
     return GEN_OK;
 }
 
+}  // extern "C"
+
+// The environment-wide launch choices of the autotuner, per batch signature.
+struct TunedForms {
+    int lane_groups, batch_form, rollout_form, sample_form;
+};
+static std::map<std::string, TunedForms> g_forms_cache;  // under g_tune_mu
+
+// Lane-group width, batch form, rollout form (K = 8 frames) and sampler
+// form, each timed on a scratch batch of the environment's own shapes and
+// parameters (its games do not advance); cached per batch signature.
+static int tune_env_forms(gen_env* e, int steps, int sms, std::string& rep) {
+    char line[256];
+    std::string sig = std::to_string(sms) + ":" + std::to_string(e->G);
+    for (const Bucket& b : e->buckets)
+        sig += ":" + std::to_string(cell_class(b.npad_max)) + "/" + std::to_string(player_class(b.pmax)) + "x" +
+               std::to_string(b.n);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_forms_cache.find(sig);
+        if (it != g_forms_cache.end()) {
+            const TunedForms& f = it->second;
+            e->lane_groups = f.lane_groups;
+            e->batch_form = f.batch_form;
+            e->rollout_form = f.rollout_form;
+            e->sample_form = f.sample_form;
+            snprintf(line, sizeof(line), "forms (cached): lanes %d, batch %d, rollout %d, sampler %d\n", f.lane_groups,
+                     f.batch_form, f.rollout_form, f.sample_form);
+            rep += line;
+            return build_worklist(e);
+        }
+    }
+    std::vector<int32_t> hh, ww, mm, pp;
+    for (const GameInfo& gi : e->h_info) {
+        hh.push_back(gi.H);
+        ww.push_back(gi.W);
+        mm.push_back(gi.mode);
+        pp.push_back(gi.P);
+    }
+    gen_env* t = nullptr;
+    int rc = gen_create_ex(&t, &e->prm, e->G, hh.data(), ww.data(), mm.data(), pp.data());
+    if (rc) return rc;
+    constexpr int K = 8;
+    gen_outputs ko{};
+    float* logits = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    const size_t pc = (size_t)t->plane_cells, ps = (size_t)t->player_slots, G = (size_t)t->G;
+    cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&a);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&b);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.obs_army, K * pc * 2);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.obs_owner, K * pc);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.obs_terrain, K * pc);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.obs_vis, K * pc);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.mask, K * pc);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.reward, K * ps * 4);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.scoreboard, K * ps * 8);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ko.done, K * G);
+    if (ce == cudaSuccess) ce = cudaMalloc(&logits, pc * 9 * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(logits, 0, pc * 9 * sizeof(float), s);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "autotune scratch");
+    if (rc == GEN_OK) rc = ensure_internal_outputs(t);
+    if (rc == GEN_OK) rc = gen_policy(t, 1, t->d_actions, s);
+    TunedForms best{e->lane_groups, e->batch_form, e->rollout_form, e->sample_form};
+    auto step = [&]() { return gen_step_policy(t, t->d_actions, &t->d_out, 1, t->d_actions, s); };
+    if (rc == GEN_OK) {
+        // lane groups: by batch size, a warp per game, or several per warp where the games allow
+        float bt = 1e30f;
+        rep += "lanes:";
+        for (int lg : {0, 1, 2}) {
+            if ((rc = gen_set_lane_groups(t, lg)) != GEN_OK) break;
+            const float ms = time_calls(step, steps, s, a, b);
+            snprintf(line, sizeof(line), " %d=%.4fms", lg, ms);
+            rep += line;
+            if (ms < bt) {
+                bt = ms;
+                best.lane_groups = lg;
+            }
+        }
+        rep += "\n";
+    }
+    if (rc == GEN_OK) rc = gen_set_lane_groups(t, best.lane_groups);
+    if (rc == GEN_OK && t->buckets.size() > 1) {
+        float bt = 1e30f;
+        rep += "batch:";
+        for (int bf : {1, 2}) {
+            t->batch_form = bf;
+            const float ms = time_calls(step, steps, s, a, b);
+            snprintf(line, sizeof(line), " %d=%.4fms", bf, ms);
+            rep += line;
+            if (ms < bt) {
+                bt = ms;
+                best.batch_form = bf;
+            }
+        }
+        rep += "\n";
+        t->batch_form = best.batch_form;
+    }
+    if (rc == GEN_OK) {
+        float bt = 1e30f;
+        rep += "rollout (per frame, K = 8):";
+        for (int form : {GEN_ROLLOUT_RESIDENT, GEN_ROLLOUT_GRAPH, GEN_ROLLOUT_LAUNCHES}) {
+            auto roll = [&]() { return gen_rollout(t, K, 1, t->d_actions, &ko, nullptr, form, s); };
+            const float ms = time_calls(roll, std::max(1, steps / K), s, a, b) / K;
+            snprintf(line, sizeof(line), " %d=%.4fms", form, ms);
+            rep += line;
+            if (ms < bt) {
+                bt = ms;
+                best.rollout_form = form;
+            }
+        }
+        rep += "\n";
+    }
+    if (rc == GEN_OK) {
+        float bt = 1e30f;
+        rep += "sampler:";
+        for (int form : {1, 2}) {
+            t->sample_form = form;
+            auto samp = [&]() { return gen_sample_actions(t, logits, 1, t->d_actions, nullptr, s); };
+            const float ms = time_calls(samp, steps, s, a, b);
+            snprintf(line, sizeof(line), " %d=%.4fms", form, ms);
+            rep += line;
+            if (ms < bt) {
+                bt = ms;
+                best.sample_form = form;
+            }
+        }
+        rep += "\n";
+    }
+    cudaFree(ko.obs_army);
+    cudaFree(ko.obs_owner);
+    cudaFree(ko.obs_terrain);
+    cudaFree(ko.obs_vis);
+    cudaFree(ko.mask);
+    cudaFree(ko.reward);
+    cudaFree(ko.scoreboard);
+    cudaFree(ko.done);
+    cudaFree(logits);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
+    free_env(t);
+    if (rc) return rc;
+    e->lane_groups = best.lane_groups;
+    e->batch_form = best.batch_form;
+    e->rollout_form = best.rollout_form;
+    e->sample_form = best.sample_form;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_forms_cache[sig] = best;
+    }
+    return build_worklist(e);
+}
+
+extern "C" {
+
 int gen_autotune(gen_env* e, int steps, char* report, size_t report_cap) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (steps < 1) return fail(GEN_ERR_BAD_ARG, "steps < 1");
@@ -1416,6 +1622,10 @@ int gen_autotune(gen_env* e, int steps, char* report, size_t report_cap) {
     drop_graph(e);
     std::string rep;
     char line[256];
+    {
+        const int rc = tune_env_forms(e, steps, sms, rep);
+        if (rc) return rc;
+    }
     for (size_t bi = 0; bi < e->buckets.size(); ++bi) {
         Bucket& b = e->buckets[bi];
         const auto cls = std::make_pair(cell_class(b.npad_max), player_class(b.pmax));

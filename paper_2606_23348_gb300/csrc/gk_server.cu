@@ -1,7 +1,7 @@
 // Env server of libgenerals: the games of many client sessions stay resident
 // on the device and are stepped by continuous batching.  Clients submit step
 // requests as they please; a scheduler thread folds every request waiting at
-// that moment into one tick (one size-bucketed set of step launches over all
+// that moment into one tick (one work-list launch over all
 // their games), keeps up to two ticks in flight on separate streams so that
 // requests arriving while a tick runs start on the device before it ends,
 // and completes each request when its tick's event fires.  New sessions are
@@ -56,6 +56,7 @@ using Clock = std::chrono::steady_clock;
 double now_ms() { return std::chrono::duration<double, std::milli>(Clock::now().time_since_epoch()).count(); }
 
 constexpr int kMaxSmemPerCta = 227 * 1024;
+constexpr int kTicks = 2;  // ticks in flight at once, each on its own stream
 constexpr double kTickDeadlineMs = 30000.0;  // a tick still running after this fails its requests
 
 // First-fit allocator of index ranges in [0, cap), with coalescing.
@@ -129,6 +130,7 @@ struct Tick {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr, done = nullptr;
+    cudaEvent_t t_start = nullptr, t_end = nullptr;  // timing: the tick's device time
     int32_t* d_list = nullptr;
     int32_t* h_list = nullptr;  // pinned
     gk::WorkItem* d_items = nullptr;  // the tick's work list (one launch over every class)
@@ -186,7 +188,7 @@ struct gen_server {
     int32_t* act_host = nullptr;
     int32_t* act_dev = nullptr;
     cudaStream_t admin = nullptr;
-    Tick ticks[2];
+    Tick ticks[kTicks];
     std::map<std::pair<int, int>, ClassShape> shapes;
     // work-list launches: per size class its geometry, items of a CTA's worth of games
     gk::BucketGeom* d_geoms = nullptr;
@@ -203,6 +205,7 @@ struct gen_server {
     std::mutex stat_mu;
     std::vector<double> lat;
     uint64_t frames = 0, requests = 0, tick_count = 0, admitted = 0, waited = 0, waited_budget = 0;
+    double tick_gpu_ms_sum = 0, tick_host_ms_sum = 0;
     size_t peak_in_use = 0;  // under mu
     double t0 = 0, tick_games_sum = 0;
     std::string fatal;
@@ -284,17 +287,16 @@ void finish_request(Request* r, int rc) {
     r->cv.notify_all();
 }
 
-// Launch one tick over every game of `reqs` (called with sv->mu held).
-int launch_tick(gen_server* sv, Tick& t) {
+// Launch one tick over every game of the sessions `ss` (busy sessions: their
+// game lists do not change).  With spawn options the per-class launches
+// need sv->mu held (class shapes are cached in a shared map); the work-list
+// launch reads nothing shared that can change and runs without it.
+int launch_tick(gen_server* sv, Tick& t, const std::vector<const Session*>& ss, const ClassShape& base) {
     int64_t count[kClasses] = {0};
-    std::vector<const Session*> ss;
-    ss.reserve(t.reqs.size());
     int64_t games = 0;
-    for (Request* r : t.reqs) {
-        const Session& s = sv->sessions[r->session];
-        ss.push_back(&s);
-        for (auto& kv : s.by_class) count[kv.first] += (int64_t)kv.second.size();
-        games += s.n;
+    for (const Session* sp : ss) {
+        for (auto& kv : sp->by_class) count[kv.first] += (int64_t)kv.second.size();
+        games += sp->n;
     }
     int64_t start[kClasses], fill[kClasses];
     int64_t k = 0;
@@ -307,6 +309,7 @@ int launch_tick(gen_server* sv, Tick& t) {
             memcpy(t.h_list + fill[kv.first], kv.second.data(), sizeof(int32_t) * kv.second.size());
             fill[kv.first] += (int64_t)kv.second.size();
         }
+    SCUDA(cudaEventRecord(t.t_start, t.stream), "tick timing");
     SCUDA(cudaMemcpyAsync(t.d_list, t.h_list, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, t.stream),
           "tick list upload");
     const bool spawn = sv->prm.max_general_dist > 0 || sv->prm.bfs_distance || sv->prm.castle_radius > 0;
@@ -326,11 +329,9 @@ int launch_tick(gen_server* sv, Tick& t) {
         SCUDA(cudaMemcpyAsync(t.d_items, t.h_items, sizeof(gk::WorkItem) * (size_t)n_items, cudaMemcpyHostToDevice,
                               t.stream),
               "tick work-list upload");
-        ClassShape cs;
-        int rc = class_shape(sv, 256, 2, &cs);
-        if (rc) return rc;
-        KArgs a = server_args(sv, gk::OP_STEP, cs);  // geometry comes with each item
+        KArgs a = server_args(sv, gk::OP_STEP, base);  // geometry comes with each item
         gk::WArgs w;
+        int rc;
         w.items = t.d_items;
         w.n_items = n_items;
         w.geoms = sv->d_geoms;
@@ -338,7 +339,8 @@ int launch_tick(gen_server* sv, Tick& t) {
         w.counter = t.d_counter;
         rc = gk::launch_worklist(a, w, sv->wl_smem, sv->wl_ctas, t.stream);
         if (rc) return sfail(GEN_ERR_CUDA, "tick launch: %s", cudaGetErrorString((cudaError_t)rc));
-        SCUDA(cudaEventRecord(t.done, t.stream), "tick event");
+        SCUDA(cudaEventRecord(t.t_end, t.stream), "tick timing");
+    SCUDA(cudaEventRecord(t.done, t.stream), "tick event");
         t.busy = true;
         t.games = games;
         t.t_launch = now_ms();
@@ -366,6 +368,7 @@ int launch_tick(gen_server* sv, Tick& t) {
         }
         ++i;
     }
+    SCUDA(cudaEventRecord(t.t_end, t.stream), "tick timing");
     SCUDA(cudaEventRecord(t.done, t.stream), "tick event");
     t.busy = true;
     t.games = games;
@@ -373,11 +376,18 @@ int launch_tick(gen_server* sv, Tick& t) {
     return GEN_OK;
 }
 
+int busy_ticks(const gen_server* sv) {
+    int n = 0;
+    for (const Tick& t : sv->ticks) n += t.busy ? 1 : 0;
+    return n;
+}
+
 void scheduler(gen_server* sv) {
     cudaSetDevice(sv->device);
+    std::vector<std::pair<Request*, int>> finished;
     std::unique_lock<std::mutex> lk(sv->mu);
     while (true) {
-        const bool any_busy = sv->ticks[0].busy || sv->ticks[1].busy;
+        const bool any_busy = busy_ticks(sv) > 0;
         if (sv->stop && sv->queue.empty() && !any_busy) break;
         // complete finished ticks (poll with a deadline)
         for (Tick& t : sv->ticks) {
@@ -392,26 +402,53 @@ void scheduler(gen_server* sv) {
                 rc = sfail(GEN_ERR_CUDA, "tick failed: %s", cudaGetErrorString(q));
                 sv->fatal = s_err;
             }
+            float gpu_ms = 0.f;
+            if (rc == GEN_OK) cudaEventElapsedTime(&gpu_ms, t.t_start, t.t_end);
             {
                 std::lock_guard<std::mutex> sl(sv->stat_mu);
+                sv->tick_gpu_ms_sum += gpu_ms;
                 sv->tick_count += 1;
                 sv->tick_games_sum += (double)t.games;
                 if (rc == GEN_OK) sv->frames += (uint64_t)t.games;
             }
             for (Request* r : t.reqs) {
                 sv->sessions[r->session].busy = false;
-                finish_request(r, rc);
+                finished.emplace_back(r, rc);
             }
             t.reqs.clear();
             t.busy = false;
         }
+        if (!finished.empty()) {  // wake the clients without holding the server lock
+            lk.unlock();
+            for (auto& fr : finished) finish_request(fr.first, fr.second);
+            finished.clear();
+            lk.lock();
+        }
         // start a tick with every waiting request
         if (!sv->queue.empty()) {
-            Tick* free_t = !sv->ticks[0].busy ? &sv->ticks[0] : (!sv->ticks[1].busy ? &sv->ticks[1] : nullptr);
+            Tick* free_t = nullptr;
+            for (Tick& t : sv->ticks)
+                if (!t.busy && !free_t) free_t = &t;
             if (free_t && sv->fatal.empty()) {
                 free_t->reqs.assign(sv->queue.begin(), sv->queue.end());
                 sv->queue.clear();
-                const int rc = launch_tick(sv, *free_t);
+                std::vector<const Session*> ss;
+                ss.reserve(free_t->reqs.size());
+                for (Request* r : free_t->reqs) ss.push_back(&sv->sessions.find(r->session)->second);
+                ClassShape base;
+                int rc = class_shape(sv, 256, 2, &base);
+                const double h0 = now_ms();
+                if (rc == GEN_OK) {
+                    free_t->busy = true;  // taken: only this thread starts or completes ticks
+                    const bool spawn = sv->prm.max_general_dist > 0 || sv->prm.bfs_distance || sv->prm.castle_radius > 0;
+                    if (!spawn) lk.unlock();
+                    rc = launch_tick(sv, *free_t, ss, base);
+                    if (!spawn) lk.lock();
+                }
+                {
+                    std::lock_guard<std::mutex> sl(sv->stat_mu);
+                    sv->tick_host_ms_sum += now_ms() - h0;
+                }
                 if (rc) {
                     sv->fatal = s_err;
                     for (Request* r : free_t->reqs) {
@@ -432,7 +469,7 @@ void scheduler(gen_server* sv) {
             }
         }
         // sleep until a request arrives or a running tick may have finished
-        const bool busy_now = sv->ticks[0].busy || sv->ticks[1].busy;
+        const bool busy_now = busy_ticks(sv) > 0;
         sv->cv_req.wait_for(lk, std::chrono::microseconds(busy_now ? 20 : 2000));
     }
 }
@@ -444,6 +481,8 @@ void free_server(gen_server* sv) {
         for (auto e : t.join) cudaEventDestroy(e);
         if (t.fork) cudaEventDestroy(t.fork);
         if (t.done) cudaEventDestroy(t.done);
+        if (t.t_start) cudaEventDestroy(t.t_start);
+        if (t.t_end) cudaEventDestroy(t.t_end);
         if (t.stream) cudaStreamDestroy(t.stream);
         cudaFree(t.d_list);
         cudaFreeHost(t.h_list);
@@ -567,6 +606,8 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking);
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&t.t_start);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&t.t_end);
         if (ce == cudaSuccess) ce = cudaMalloc(&t.d_list, sizeof(int32_t) * G);
         if (ce == cudaSuccess) ce = cudaHostAlloc(&t.h_list, sizeof(int32_t) * G, cudaHostAllocPortable);
         if (ce == cudaSuccess) ce = cudaMalloc(&t.d_items, sizeof(gk::WorkItem) * G);
@@ -863,10 +904,13 @@ int gen_server_stats_get(gen_server* sv, gen_server_stats* st, int reset) {
         st->sessions_waited_budget = sv->waited_budget;
         st->seconds = (now_ms() - sv->t0) * 1e-3;
         st->tick_games_mean = sv->tick_count ? sv->tick_games_sum / (double)sv->tick_count : 0.0;
+        st->tick_gpu_ms_mean = sv->tick_count ? sv->tick_gpu_ms_sum / (double)sv->tick_count : 0.0;
+        st->tick_host_ms_mean = sv->tick_count ? sv->tick_host_ms_sum / (double)sv->tick_count : 0.0;
         if (reset) {
             sv->lat.clear();
             sv->requests = sv->frames = sv->tick_count = sv->admitted = sv->waited = sv->waited_budget = 0;
             sv->tick_games_sum = 0;
+            sv->tick_gpu_ms_sum = sv->tick_host_ms_sum = 0;
             sv->t0 = now_ms();
         }
     }

@@ -62,9 +62,9 @@ EXPORTS = ("gen_default_params", "gen_create", "gen_create_ex", "gen_layout", "g
            "gen_features_build", "gen_features_destroy", "gen_features_create_ex", "gen_features_series_layout",
            "gen_features_build_ex", "gen_features_set_form", "gen_sample_actions", "gen_set_sample_form",
            "gen_set_lane_groups", "gen_outputs_get", "gen_device_bytes", "gen_save_state", "gen_load_state",
-           "gen_set_batch_form")
+           "gen_set_batch_form", "gen_features_autotune")
 
-ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES = 0, 1, 2
+ROLLOUT_RESIDENT, ROLLOUT_GRAPH, ROLLOUT_LAUNCHES, ROLLOUT_AUTO = 0, 1, 2, 3
 
 
 def load_library(path: str = LIB_PATH):
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH):
             "gen_set_lane_groups": (C.c_int, [vp, C.c_int]),
             "gen_outputs_get": (C.c_int, [vp, C.POINTER(GenOutputs)]),
             "gen_set_batch_form": (C.c_int, [vp, C.c_int]),
+            "gen_features_autotune": (C.c_int, [vp, vp, C.c_int, C.POINTER(i32)]),
             "gen_device_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
             "gen_save_state": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t), vp]),
             "gen_load_state": (C.c_int, [vp, vp, C.c_size_t, vp]),
@@ -476,6 +477,13 @@ class Features:
         return out
 
     FORM_AUTO, FORM_WARP, FORM_CTA = 0, 1, 2
+
+    def autotune(self, out, steps: int = 5) -> int:
+        """Time both forms building into `out` and keep the faster; returns it."""
+        f = C.c_int32()
+        _check(self.lib.gen_features_autotune(self.h, C.c_void_p(out.data_ptr()), int(steps), C.byref(f)),
+               "gen_features_autotune")
+        return int(f.value)
 
     def set_form(self, form: int):
         """Spread of a game over the GPU: FORM_WARP (one warp per game),

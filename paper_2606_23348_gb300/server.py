@@ -25,7 +25,8 @@ class ServerStats(C.Structure):
                 ("lat_p99_ms", C.c_double), ("lat_mean_ms", C.c_double), ("tick_games_mean", C.c_double),
                 ("bytes_in_use", C.c_double), ("budget", C.c_double), ("sessions_waited_budget", C.c_uint64),
                 ("peak_bytes_in_use", C.c_double), ("service_p50_ms", C.c_double), ("service_p99_ms", C.c_double),
-                ("offered_requests_per_s", C.c_double)]
+                ("offered_requests_per_s", C.c_double), ("tick_gpu_ms_mean", C.c_double),
+                ("tick_host_ms_mean", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -164,6 +164,40 @@ def test_autotune_keeps_results():
     compare_frame(env, out, orc, "after autotune")
 
 
+def test_tuned_and_default_shapes_give_identical_bytes():
+    """Every choice the autotuner makes (games per warp, batch form, the
+    rollout form AUTO runs, sampler form, feature-builder form, games per
+    CTA) leaves the results as they were: a tuned and an untuned environment
+    of the same games agree byte for byte on rollouts, sampled actions and
+    the feature tensor."""
+    import torch
+    from paper_2606_23348_gb300.generals import ROLLOUT_AUTO, ROLLOUT_RESIDENT
+    tuned, _ = make_pair(G=64, seed=23)
+    plain, _ = make_pair(G=64, seed=23)
+    rep = tuned.autotune(steps=2)
+    assert "lanes:" in rep and "batch:" in rep and "rollout" in rep and "sampler:" in rep
+    fa, fb = tuned.features(7, 16), plain.features(7, 16)
+    xa, xb = fa.new_output(), fb.new_output()
+    fa.autotune(xa, steps=2)  # folds the first frame, as this build does on the other side
+    fb.build(xb)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    logits = torch.randn(int(tuned.layout.plane_cells) * 9, generator=g, device="cuda")
+    res = []
+    for env, fbld, x, form in ((tuned, fa, xa, ROLLOUT_AUTO), (plain, fb, xb, ROLLOUT_RESIDENT)):
+        out = env.new_outputs(frames=6)
+        acts = env.new_actions()
+        env.policy(4, acts)
+        env.rollout(6, 4, acts, out, None, form)
+        env.rollout(6, 4, acts, out, None, form)
+        sampled = env.sample_actions(logits, 9)
+        fbld.build(x)
+        torch.cuda.synchronize()
+        res.append([t.cpu().numpy().copy() for t in out.tensors()] + [acts.cpu().numpy(), sampled.cpu().numpy(),
+                                                                      x.cpu().numpy()])
+    for i, (u, v) in enumerate(zip(*res)):
+        np.testing.assert_array_equal(u, v, err_msg=f"array {i}")
+
+
 def _check_sampled(env, out, K, H, W, mode, P, gen, blocks, n, policy_seed, log=None):
     """Replay sampled blocks of games in the oracle and compare every frame of the rollout buffer."""
     import torch
