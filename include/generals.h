@@ -318,9 +318,9 @@ int gen_copy_peak(size_t bytes, int reps, double *gbps);
  * The games of every client session stay on the device.  A scheduler
  * thread folds all step requests waiting at a given moment into one tick
  * (one work-list launch over all their games, every size class at once, with the
- * benchmark policy fused); up to two ticks are in flight on separate
- * streams, so requests that arrive while one runs start on the device before
- * it ends.  Sessions are admitted while the device bytes they need fit the
+ * benchmark policy fused); up to two ticks are in flight, one behind the
+ * other on the device, so requests that arrive while one runs start the
+ * moment it ends.  Sessions are admitted while the device bytes they need fit the
  * budget; otherwise gen_server_open waits for others to close.  Each game is
  * keyed by the global game id its session was opened with, so its results
  * do not depend on the other sessions.  Section IV rules throughout.  The

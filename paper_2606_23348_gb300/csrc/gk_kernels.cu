@@ -118,10 +118,22 @@ struct Smem {
     uint32_t* colL;    // last column
     uint32_t* vis;     // [pmax][stride]
     uint32_t* tmp;
-    uint8_t* cnt;      // [pmax][chunks]: legal (cell, direction) pairs of the player in the chunk
+    // legal moves per (player, 16-cell chunk), one region in one of two forms:
+    // launches of at most two players keep each chunk's 64-bit mask (bit
+    // 4j + d: cell j towards d), wider ones only its count of legal pairs
+    // (a byte), which keeps 8-player carves small; the policy then rebuilds
+    // the selected chunk's mask from the board
+    uint64_t* legal;   // [pmax][chunks] when masks
+    uint8_t* cnt;      // [pmax][chunks] otherwise (same bytes)
     int32_t* misc;     // [0..7] general cells, [8..15] land, [16..23] army
     int stride;
+    bool masks;
 };
+
+// bytes of the legal-move region of a warp's carve
+__host__ __device__ __forceinline__ int legal_region_bytes(int npad_max, int pmax) {
+    return pmax <= 2 ? 8 * pmax * (npad_max >> 4) : ((pmax * (npad_max >> 4) + 15) & ~15);
+}
 
 // A warp's shared-memory geometry packed in one word: padded cells of the
 // largest board (13 bits), bitset stride in words (8 bits), players (4 bits).
@@ -130,9 +142,8 @@ __host__ __device__ __forceinline__ uint32_t pack_geom(int npad_max, int nw_stri
 }
 __device__ __forceinline__ uint32_t geom_of(const KArgs& a) { return pack_geom(a.npad_max, a.nw_stride, a.pmax); }
 
-__device__ __forceinline__ Smem carve_geom(char* base, uint32_t geom) {
+__device__ __forceinline__ Smem carve_dims(char* base, const int np, const int st, const int pm) {
     Smem s;
-    const int np = (int)(geom & 0x1FFFu), st = (int)((geom >> 13) & 0xFFu), pm = (int)(geom >> 21);
     s.army = reinterpret_cast<int16_t*>(base);
     s.owner = reinterpret_cast<int8_t*>(base + 2 * np);
     s.terrain = reinterpret_cast<uint8_t*>(base + 3 * np);
@@ -149,13 +160,21 @@ __device__ __forceinline__ Smem carve_geom(char* base, uint32_t geom) {
     w += pm * st;
     s.tmp = w;
     w += st;
+    s.legal = reinterpret_cast<uint64_t*>(w);  // 8-byte aligned: every region above is
     s.cnt = reinterpret_cast<uint8_t*>(w);
-    w += ((pm * (np >> 4) + 15) & ~15) >> 2;  // whole 16-byte units
+    w += legal_region_bytes(np, pm) >> 2;  // whole 16-byte units
     s.misc = reinterpret_cast<int32_t*>(w);
     s.stride = st;
+    s.masks = pm <= 2;
     return s;
 }
-__device__ __forceinline__ Smem carve(char* base, const KArgs& a) { return carve_geom(base, geom_of(a)); }
+__device__ __forceinline__ Smem carve_geom(char* base, uint32_t geom) {
+    return carve_dims(base, (int)(geom & 0x1FFFu), (int)((geom >> 13) & 0xFFu), (int)(geom >> 21));
+}
+// the launch's own geometry, straight from the kernel parameters
+__device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
+    return carve_dims(base, a.npad_max, a.nw_stride, a.pmax);
+}
 
 struct Game {
     int H, W, N, Npad, nch, P, mode, nw;
@@ -1017,9 +1036,16 @@ __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32
             om[k] = dpb & (spread4((mv >> (4 * k)) & 15u) * 0xFFu);
         }
         if (COUNT) {
-            // legal (cell, direction) pairs of the chunk: the low nibble of each mask byte
-            s.cnt[p * nch + ch] = (uint8_t)(__popc(om[0] & 0x0F0F0F0Fu) + __popc(om[1] & 0x0F0F0F0Fu) +
-                                            __popc(om[2] & 0x0F0F0F0Fu) + __popc(om[3] & 0x0F0F0F0Fu));
+            if (LW < 32 || s.masks) {
+                // the chunk's legal moves as 64 bits: 4 per cell in (cell, direction) order
+                const uint32_t lo = nibbles16(om[0]) | (nibbles16(om[1]) << 16);
+                const uint32_t hi = nibbles16(om[2]) | (nibbles16(om[3]) << 16);
+                s.legal[p * nch + ch] = ((uint64_t)hi << 32) | lo;
+            } else {
+                // legal (cell, direction) pairs of the chunk: the low nibble of each mask byte
+                s.cnt[p * nch + ch] = (uint8_t)(__popc(om[0] & 0x0F0F0F0Fu) + __popc(om[1] & 0x0F0F0F0Fu) +
+                                                __popc(om[2] & 0x0F0F0F0Fu) + __popc(om[3] & 0x0F0F0F0Fu));
+            }
         }
         if (WRITE) {
             const uint32_t vis16 = (s.vis[p * st + wi] >> sh) & 0xFFFFu;
@@ -1080,6 +1106,7 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
                                uint32_t frame, uint64_t gid, const Grp<LW>& t) {
     int32_t mine_action = 0;
     const int nch = g.nch;
+    const bool masks = LW < 32 || s.masks;
     const int cpl = (nch + LW - 1) / LW;  // consecutive chunks per lane
     const int c_lo = t.lane * cpl;
     const int c_hi = min(c_lo + cpl, nch);
@@ -1093,8 +1120,13 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
     for (int p0 = 0; p0 < g.P; p0 += 2) {
         uint32_t mine = 0;
         for (int c = c_lo; c < c_hi; ++c) {
-            mine += s.cnt[p0 * nch + c];
-            if (p0 + 1 < g.P) mine += (uint32_t)s.cnt[(p0 + 1) * nch + c] << 16;
+            if (masks) {
+                mine += __popcll(s.legal[p0 * nch + c]);
+                if (p0 + 1 < g.P) mine += (uint32_t)__popcll(s.legal[(p0 + 1) * nch + c]) << 16;
+            } else {
+                mine += s.cnt[p0 * nch + c];
+                if (p0 + 1 < g.P) mine += (uint32_t)s.cnt[(p0 + 1) * nch + c] << 16;
+            }
         }
         const uint32_t incl2 = warp_incl_scan(mine, t);
         const uint32_t total2 = t.shfl(incl2, LW - 1);
@@ -1112,12 +1144,13 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
                 if (t.lane == L) {
                     uint32_t jj = j - (incl - ((mine >> (16 * q)) & 0xFFFFu));
                     for (int c = c_lo; c < c_hi; ++c) {
-                        const uint32_t n = s.cnt[p * nch + c];
+                        const uint64_t mk = masks ? s.legal[p * nch + c] : 0ull;
+                        const uint32_t n = masks ? (uint32_t)__popcll(mk) : (uint32_t)s.cnt[p * nch + c];
                         if (jj >= n) {
                             jj -= n;
                             continue;
                         }
-                        const uint64_t m = chunk_legal64(s, p, c);
+                        const uint64_t m = masks ? mk : chunk_legal64(s, p, c);
                         uint32_t x = (uint32_t)m;
                         int bit = 0;
                         const uint32_t nlo = __popc(x);
@@ -1219,6 +1252,8 @@ namespace {
 
 
 template <bool MULTI, bool SPAWN, int LW, bool UNI>
+// geom: the packed carve geometry of the game's warp region, or 0 for the
+// launch's own (kernel parameters); only the cold out-of-line paths use it.
 __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* warp_base, const uint32_t geom,
                                          const int gidx, const Grp<LW>& t) {
     Game g = game_of<UNI>(a, gidx);
@@ -1259,15 +1294,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
         if constexpr (SPAWN)
-            generate_spawn(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+            generate_spawn(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         else
-            generate<LW, UNI>(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+            generate<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
     } else if (a.op == OP_DERIVE) {
-        derive_passable_at<LW, UNI>(a, gidx, warp_base, geom, t.lane + t.shift);
+        derive_passable_at<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of(a), t.lane + t.shift);
         wrote_state = true;
     }
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
@@ -1326,9 +1361,9 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
                 if (a.auto_reset) {
                     epoch += 1;
                     if constexpr (SPAWN)
-                        generate_spawn(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+                        generate_spawn(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     else
-                        generate<LW, UNI>(a, gidx, warp_base, geom, game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+                        generate<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, t);
@@ -1421,13 +1456,13 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) 
         if (item >= a.n_items) return;
         const int gidx = a.list ? a.list[item] : item;
         if (gidx < 0 || gidx >= a.n_games) return;
-        run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, geom_of(a), gidx, t);
+        run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, 0u, gidx, t);
     } else {
         for (int item = blockIdx.x * gpc + grp; item < a.n_items; item += gridDim.x * gpc) {
             const int gidx = a.list ? a.list[item] : item;
             if (gidx < 0 || gidx >= a.n_games) continue;
             t.sync();
-            run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, geom_of(a), gidx, t);
+            run_game<MULTI, SPAWN, LW, UNI>(a, s, warp_base, 0u, gidx, t);
         }
     }
 }
@@ -1552,8 +1587,7 @@ int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
     int nw = (npad_max + 31) / 32;
     nw = (nw + 1) & ~1;  // even: the carve stays a multiple of 16 bytes
     if (nw_stride) *nw_stride = nw;
-    const int cnt_bytes = (pmax * (npad_max >> 4) + 15) & ~15;
-    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + cnt_bytes + 4 * 24;
+    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + legal_region_bytes(npad_max, pmax) + 4 * 24;
 }
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {

@@ -2,9 +2,10 @@
 // on the device and are stepped by continuous batching.  Clients submit step
 // requests as they please; a scheduler thread folds every request waiting at
 // that moment into one tick (one work-list launch over all
-// their games), keeps up to two ticks in flight on separate streams so that
-// requests arriving while a tick runs start on the device before it ends,
-// and completes each request when its tick's event fires.  New sessions are
+// their games), keeps up to two ticks in flight on one stream so that
+// requests arriving while a tick runs are launched behind it and start on
+// the device the moment it ends, and completes each request when its tick's
+// event fires.  New sessions are
 // admitted against a byte budget of device memory as earlier ones close.
 //
 // Every game keys its maps and policy draws by the global game id its
@@ -126,7 +127,7 @@ struct ClassShape {
 };
 
 struct Tick {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the server's tick stream (shared by every tick)
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr, done = nullptr;
@@ -189,6 +190,10 @@ struct gen_server {
     int32_t* act_dev = nullptr;
     cudaStream_t admin = nullptr;
     Tick ticks[kTicks];
+    // every tick runs on this one stream: a tick launched while another runs
+    // waits behind it, so the device goes from one to the next without a gap
+    // and two ticks never split its SMs
+    cudaStream_t tick_stream = nullptr;
     std::map<std::pair<int, int>, ClassShape> shapes;
     // work-list launches: per size class its geometry, items of a CTA's worth of games
     gk::BucketGeom* d_geoms = nullptr;
@@ -483,7 +488,7 @@ void free_server(gen_server* sv) {
         if (t.done) cudaEventDestroy(t.done);
         if (t.t_start) cudaEventDestroy(t.t_start);
         if (t.t_end) cudaEventDestroy(t.t_end);
-        if (t.stream) cudaStreamDestroy(t.stream);
+
         cudaFree(t.d_list);
         cudaFreeHost(t.h_list);
         cudaFree(t.d_items);
@@ -492,6 +497,7 @@ void free_server(gen_server* sv) {
     }
     cudaFree(sv->d_geoms);
     if (sv->admin) cudaStreamDestroy(sv->admin);
+    if (sv->tick_stream) cudaStreamDestroy(sv->tick_stream);
     cudaFree(sv->d_info);
     cudaFree(sv->d_scal);
     cudaFree(sv->d_army);
@@ -602,8 +608,9 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         sv->act_dev = (int32_t*)dp;
     }
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&sv->admin, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&sv->tick_stream, cudaStreamNonBlocking);
     for (Tick& t : sv->ticks) {
-        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking);
+        t.stream = sv->tick_stream;
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
         if (ce == cudaSuccess) ce = cudaEventCreate(&t.t_start);
