@@ -454,7 +454,8 @@ int gen_set_lane_groups(gen_env *env, int mode);
  * work-list launch per frame (per rollout in the resident form): CTAs take
  * items -- up to a CTA's worth of one bucket's games, largest boards first --
  * from an atomic counter and carve their shared memory per item; 0 (default)
- * = 2.  Batches with spawn options always take form 1.  The work list's
+ * = 2 for batches of more than four buckets, else 1.  Batches with spawn
+ * options always take form 1.  The work list's
  * counter belongs to the environment: order its calls on one stream.
  * GEN_ERR_BAD_ARG for NULL env or a form outside 0..2. */
 int gen_set_batch_form(gen_env *env, int form);

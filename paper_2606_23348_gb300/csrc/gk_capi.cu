@@ -283,10 +283,16 @@ int launch_one(const Bucket& b, const KArgs& a, void* stream, const char* what) 
 // Every game, one launch per size bucket; buckets after the first run on
 // side streams forked from and joined back into `stream`.
 // The work-list form serves batches of several buckets without spawn
-// options (their generator runs in its own kernel).
+// options (their generator runs in its own kernel).  By default it takes
+// batches of more than four buckets: there the per-bucket launches are many
+// and small (mixed 32,768 games, 15 buckets: 136 against 131 M frames/s per
+// frame, resident 173 against 167 M), while a few large buckets overlap
+// well on the forked streams (ragged 131,072 games, 4 buckets: 428 against
+// 419 M, resident 627 against 606 M).
 bool use_worklist(const gen_env* e) {
     const bool spawn = e->prm.max_general_dist > 0 || e->prm.bfs_distance || e->prm.castle_radius > 0;
-    return e->buckets.size() > 1 && e->d_items[0] && !spawn && e->batch_form != 1;
+    if (e->buckets.size() < 2 || !e->d_items[0] || spawn || e->batch_form == 1) return false;
+    return e->batch_form == 2 || e->buckets.size() > 4;
 }
 
 template <class Fill>
@@ -453,9 +459,9 @@ int build_worklist(gen_env* e) {
     std::vector<gk::BucketGeom> geoms(nb);
     for (size_t i = 0; i < nb; ++i) {
         const Bucket& b = e->buckets[i];
-        geoms[i].geom = gk::bucket_geom(b.npad_max, b.nw_stride, b.pmax);
-        geoms[i].group_smem = b.warp_smem;
         geoms[i].lw = (b.pmax <= 2 && b.npad_max <= 1024 && e->lane_groups != 1) ? 16 : 32;
+        geoms[i].group_smem = gk::warp_smem_bytes(b.npad_max, b.pmax, nullptr, geoms[i].lw < 32);
+        geoms[i].geom = gk::bucket_geom(b.npad_max, b.nw_stride, b.pmax, geoms[i].lw < 32);
         geoms[i].pad = 0;
     }
     if (!e->d_geoms) {
@@ -472,10 +478,10 @@ int build_worklist(gen_env* e) {
         for (size_t i = 0; i < nb; ++i) {
             const Bucket& b = e->buckets[i];
             const int groups = 8 * (32 / geoms[i].lw);
-            const int per = std::max(1, std::min(groups, smem / b.warp_smem));
-            if (per * b.warp_smem > smem)
-                return fail(GEN_ERR_BAD_ARG, "a %d-cell board needs %d bytes of shared memory per game", b.npad_max,
-                            b.warp_smem);
+            const int gs = geoms[i].group_smem;
+            const int per = std::max(1, std::min(groups, smem / gs));
+            if (per * gs > smem)
+                return fail(GEN_ERR_BAD_ARG, "a %d-cell board needs %d bytes of shared memory per game", b.npad_max, gs);
             for (int k = 0; k < b.n; k += per) {
                 gk::WorkItem it;
                 it.first = b.offset + k;

@@ -86,7 +86,7 @@ struct KArgs {
     int32_t npad_max;   // cells
     int32_t nw_stride;  // 32-bit words per bitset
     int32_t pmax;
-    int32_t warp_smem;  // bytes per warp
+    int32_t warp_smem;  // bytes per warp (a warp per game; launches of narrower groups recompute it)
     // spawn options of the map generator (all zero: the plain generator)
     int32_t spawn_dmax;     // cap on a general's distance to every earlier one (0: none)
     int32_t spawn_bfs;      // 1: spacing in BFS steps around mountains
@@ -165,9 +165,10 @@ struct SArgs {
 // players of any game.  Returns a cudaError_t.
 int launch_sample(const SArgs& a, int pmax, int form, void* stream);
 
-// Bytes of shared memory one warp needs for games up to npad_max cells and
-// pmax players; also returns the bitset stride in words.
-int warp_smem_bytes(int npad_max, int pmax, int* nw_stride);
+// Bytes of shared memory one lane group needs for games up to npad_max
+// cells and pmax players; also returns the bitset stride in words.  narrow:
+// a group narrower than a warp (its legal moves kept as per-chunk masks).
+int warp_smem_bytes(int npad_max, int pmax, int* nw_stride, bool narrow = false);
 
 // CTAs of the step kernel that fit on the whole GPU at once (raises the
 // kernel's shared-memory limit as a side effect).  Returns a cudaError_t.
@@ -195,7 +196,7 @@ struct WArgs {
     int32_t* counter;  // next item; zeroed by launch_worklist before the kernel
 };
 // Packed geometry word of a bucket (as the kernels unpack it).
-uint32_t bucket_geom(int npad_max, int nw_stride, int pmax);
+uint32_t bucket_geom(int npad_max, int nw_stride, int pmax, bool narrow);
 // Dynamic shared memory per CTA and CTAs of the whole GPU for the work-list
 // kernel (`multi`: multi-frame form).  Returns a cudaError_t.
 int worklist_shape(bool multi, int* cta_smem, int* ctas);

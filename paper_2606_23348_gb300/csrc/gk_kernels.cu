@@ -119,30 +119,35 @@ struct Smem {
     uint32_t* vis;     // [pmax][stride]
     uint32_t* tmp;
     // legal moves per (player, 16-cell chunk), one region in one of two forms:
-    // launches of at most two players keep each chunk's 64-bit mask (bit
-    // 4j + d: cell j towards d), wider ones only its count of legal pairs
-    // (a byte), which keeps 8-player carves small; the policy then rebuilds
-    // the selected chunk's mask from the board
-    uint64_t* legal;   // [pmax][chunks] when masks
-    uint8_t* cnt;      // [pmax][chunks] otherwise (same bytes)
+    // groups narrower than a warp (two-player games, issue-bound) keep each
+    // chunk's 64-bit mask (bit 4j + d: cell j towards d); a warp per game
+    // keeps only its count of legal pairs (a byte), which keeps 8-player
+    // carves small, and the policy rebuilds the selected chunk's mask from
+    // the board
+    uint64_t* legal;   // [pmax][chunks], narrow groups
+    uint8_t* cnt;      // [pmax][chunks], a warp per game (same bytes)
     int32_t* misc;     // [0..7] general cells, [8..15] land, [16..23] army
     int stride;
-    bool masks;
 };
 
-// bytes of the legal-move region of a warp's carve
-__host__ __device__ __forceinline__ int legal_region_bytes(int npad_max, int pmax) {
-    return pmax <= 2 ? 8 * pmax * (npad_max >> 4) : ((pmax * (npad_max >> 4) + 15) & ~15);
+// bytes of the legal-move region of a carve: masks for narrow groups, counts for a warp per game
+__host__ __device__ __forceinline__ int legal_region_bytes(int npad_max, int pmax, bool narrow) {
+    return narrow ? 8 * pmax * (npad_max >> 4) : ((pmax * (npad_max >> 4) + 15) & ~15);
 }
 
-// A warp's shared-memory geometry packed in one word: padded cells of the
-// largest board (13 bits), bitset stride in words (8 bits), players (4 bits).
-__host__ __device__ __forceinline__ uint32_t pack_geom(int npad_max, int nw_stride, int pmax) {
-    return (uint32_t)npad_max | ((uint32_t)nw_stride << 13) | ((uint32_t)pmax << 21);
+// A group's shared-memory geometry packed in one word: padded cells of the
+// largest board (13 bits), bitset stride in words (8 bits), players (4 bits),
+// and whether the group is narrower than a warp (bit 25: the mask form of
+// the legal-move region).
+__host__ __device__ __forceinline__ uint32_t pack_geom(int npad_max, int nw_stride, int pmax, bool narrow) {
+    return (uint32_t)npad_max | ((uint32_t)nw_stride << 13) | ((uint32_t)pmax << 21) | (narrow ? 1u << 25 : 0u);
 }
-__device__ __forceinline__ uint32_t geom_of(const KArgs& a) { return pack_geom(a.npad_max, a.nw_stride, a.pmax); }
+template <int LW>
+__device__ __forceinline__ uint32_t geom_of(const KArgs& a) {
+    return pack_geom(a.npad_max, a.nw_stride, a.pmax, LW < 32);
+}
 
-__device__ __forceinline__ Smem carve_dims(char* base, const int np, const int st, const int pm) {
+__device__ __forceinline__ Smem carve_dims(char* base, const int np, const int st, const int pm, const bool narrow) {
     Smem s;
     s.army = reinterpret_cast<int16_t*>(base);
     s.owner = reinterpret_cast<int8_t*>(base + 2 * np);
@@ -162,18 +167,19 @@ __device__ __forceinline__ Smem carve_dims(char* base, const int np, const int s
     w += st;
     s.legal = reinterpret_cast<uint64_t*>(w);  // 8-byte aligned: every region above is
     s.cnt = reinterpret_cast<uint8_t*>(w);
-    w += legal_region_bytes(np, pm) >> 2;  // whole 16-byte units
+    w += legal_region_bytes(np, pm, narrow) >> 2;  // whole 16-byte units
     s.misc = reinterpret_cast<int32_t*>(w);
     s.stride = st;
-    s.masks = pm <= 2;
     return s;
 }
 __device__ __forceinline__ Smem carve_geom(char* base, uint32_t geom) {
-    return carve_dims(base, (int)(geom & 0x1FFFu), (int)((geom >> 13) & 0xFFu), (int)(geom >> 21));
+    return carve_dims(base, (int)(geom & 0x1FFFu), (int)((geom >> 13) & 0xFFu), (int)((geom >> 21) & 0xFu),
+                      ((geom >> 25) & 1u) != 0u);
 }
 // the launch's own geometry, straight from the kernel parameters
+template <int LW>
 __device__ __forceinline__ Smem carve(char* base, const KArgs& a) {
-    return carve_dims(base, a.npad_max, a.nw_stride, a.pmax);
+    return carve_dims(base, a.npad_max, a.nw_stride, a.pmax, LW < 32);
 }
 
 struct Game {
@@ -1036,7 +1042,7 @@ __device__ void output_pass(const KArgs& a, const Game& g, const Smem& s, uint32
             om[k] = dpb & (spread4((mv >> (4 * k)) & 15u) * 0xFFu);
         }
         if (COUNT) {
-            if (LW < 32 || s.masks) {
+            if (LW < 32) {
                 // the chunk's legal moves as 64 bits: 4 per cell in (cell, direction) order
                 const uint32_t lo = nibbles16(om[0]) | (nibbles16(om[1]) << 16);
                 const uint32_t hi = nibbles16(om[2]) | (nibbles16(om[3]) << 16);
@@ -1106,7 +1112,7 @@ __device__ int32_t policy_pass(const KArgs& a, const Game& g, const Smem& s, uin
                                uint32_t frame, uint64_t gid, const Grp<LW>& t) {
     int32_t mine_action = 0;
     const int nch = g.nch;
-    const bool masks = LW < 32 || s.masks;
+    constexpr bool masks = LW < 32;
     const int cpl = (nch + LW - 1) / LW;  // consecutive chunks per lane
     const int c_lo = t.lane * cpl;
     const int c_hi = min(c_lo + cpl, nch);
@@ -1294,15 +1300,15 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
     if (a.op == OP_CREATE || a.op == OP_RESET) {
         if (a.op == OP_RESET) epoch += 1;
         if constexpr (SPAWN)
-            generate_spawn(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+            generate_spawn(a, gidx, warp_base, geom ? geom : geom_of<LW>(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         else
-            generate<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+            generate<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of<LW>(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
         turn = 0;
         alive = all_alive;
         finished = 0;
         wrote_state = true;
     } else if (a.op == OP_DERIVE) {
-        derive_passable_at<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of(a), t.lane + t.shift);
+        derive_passable_at<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of<LW>(a), t.lane + t.shift);
         wrote_state = true;
     }
     const int frames = (MULTI && a.op == OP_STEP) ? a.frames : 1;
@@ -1361,9 +1367,9 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
                 if (a.auto_reset) {
                     epoch += 1;
                     if constexpr (SPAWN)
-                        generate_spawn(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+                        generate_spawn(a, gidx, warp_base, geom ? geom : geom_of<LW>(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     else
-                        generate<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
+                        generate<LW, UNI>(a, gidx, warp_base, geom ? geom : geom_of<LW>(a), game_id_of<UNI>(a, gidx), epoch, t.lane + t.shift);
                     turn = 0;
                     alive = all_alive;
                     cell_pass(g, s, false, false, t);
@@ -1450,7 +1456,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) 
     const int grp = (threadIdx.x >> 5) * kGroups + wl / LW;  // group in the CTA
     const int gpc = (blockDim.x >> 5) * kGroups;                                // groups per CTA
     char* warp_base = smem_raw + grp * a.warp_smem;
-    const Smem s = carve(warp_base, a);
+    const Smem s = carve<LW>(warp_base, a);
     if constexpr (!MULTI) {  // the grid covers every item
         const int item = blockIdx.x * gpc + grp;
         if (item >= a.n_items) return;
@@ -1541,7 +1547,9 @@ int allow_max_smem() {
     return limit.raise(fns, 14, 227 * 1024);
 }
 
-uint32_t bucket_geom(int npad_max, int nw_stride, int pmax) { return pack_geom(npad_max, nw_stride, pmax); }
+uint32_t bucket_geom(int npad_max, int nw_stride, int pmax, bool narrow) {
+    return pack_geom(npad_max, nw_stride, pmax, narrow);
+}
 
 int worklist_shape(bool multi, int* cta_smem, int* ctas) {
     // four CTAs of 8 warps per SM per frame (the register budget's limit),
@@ -1583,11 +1591,11 @@ int launch_worklist(const KArgs& a, const WArgs& w, int cta_smem, int ctas, void
     return (int)cudaGetLastError();
 }
 
-int warp_smem_bytes(int npad_max, int pmax, int* nw_stride) {
+int warp_smem_bytes(int npad_max, int pmax, int* nw_stride, bool narrow) {
     int nw = (npad_max + 31) / 32;
     nw = (nw + 1) & ~1;  // even: the carve stays a multiple of 16 bytes
     if (nw_stride) *nw_stride = nw;
-    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + legal_region_bytes(npad_max, pmax) + 4 * 24;
+    return 4 * npad_max + 4 * nw * (2 * pmax + 4) + legal_region_bytes(npad_max, pmax, narrow) + 4 * 24;
 }
 
 int max_resident_ctas(int warps_per_cta, int smem_bytes, int* out) {
@@ -1724,11 +1732,19 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
     const bool large = a.n_items >= (multi ? 24 : 12) * sms;
     const bool small = !spawn && a.pmax <= kPairMaxPlayers && (a.lane_groups == 2 || (a.lane_groups == 0 && large));
     const int wcap = warps_per_cta > 0 ? warps_per_cta : 1;  // the fixed shape must fit too
+    // narrow groups keep their legal moves as chunk masks: a larger carve
+    const int ws_narrow = small ? warp_smem_bytes(a.npad_max, a.pmax, nullptr, true) : a.warp_smem;
     int per_warp = 1;
-    if (small && multi && a.npad_max <= kQuadMaxCells && 4 * wcap * a.warp_smem <= 227 * 1024)
+    if (small && multi && a.npad_max <= kQuadMaxCells && 4 * wcap * ws_narrow <= 227 * 1024)
         per_warp = 4;
-    else if (small && a.npad_max <= kPairMaxCells && 2 * wcap * a.warp_smem <= 227 * 1024)
+    else if (small && a.npad_max <= kPairMaxCells && 2 * wcap * ws_narrow <= 227 * 1024)
         per_warp = 2;
+    if (per_warp > 1) {
+        KArgs n = a;
+        n.warp_smem = ws_narrow;
+        return per_warp == 4 ? launch_plain<8>(n, multi, warps_per_cta, max_ctas, sms, st)
+                             : launch_plain<16>(n, multi, warps_per_cta, max_ctas, sms, st);
+    }
     if (spawn) {  // one game per warp, shapes read per game
         const void* f = multi ? (const void*)k_generals<true, true, 32, false> : (const void*)k_generals<false, true, 32, false>;
         const int warps = pick_warps(f, warps_per_cta, 1, a.warp_smem, a.n_items, sms);
@@ -1741,8 +1757,6 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
             k_generals<false, true, 32, false><<<blocks, 32 * warps, smem, st>>>(a);
         return (int)cudaGetLastError();
     }
-    if (per_warp == 4) return launch_plain<8>(a, multi, warps_per_cta, max_ctas, sms, st);
-    if (per_warp == 2) return launch_plain<16>(a, multi, warps_per_cta, max_ctas, sms, st);
     return launch_plain<32>(a, multi, warps_per_cta, max_ctas, sms, st);
 }
 

@@ -637,10 +637,10 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         for (int c = 0; c < kClasses && ce == cudaSuccess; ++c) {
             int st = 0;
             const int npad = class_edge(c), P = class_players(c);
-            const int bytes = gk::warp_smem_bytes(npad, P, &st);
-            geoms[c].geom = gk::bucket_geom(npad, st, P);
-            geoms[c].group_smem = bytes;
             geoms[c].lw = (P <= 2 && npad <= 1024) ? 16 : 32;
+            const int bytes = gk::warp_smem_bytes(npad, P, &st, geoms[c].lw < 32);
+            geoms[c].geom = gk::bucket_geom(npad, st, P, geoms[c].lw < 32);
+            geoms[c].group_smem = bytes;
             geoms[c].pad = 0;
             sv->class_per_item[c] = std::min(8 * (32 / geoms[c].lw), sv->wl_smem / bytes);
         }

@@ -365,7 +365,7 @@ class GeneralsEnv:
     def set_batch_form(self, form: int):
         """How a batch of several size buckets launches: BATCH_BUCKETS (one
         launch per bucket), BATCH_WORKLIST (one persistent work-list launch)
-        or BATCH_AUTO (the work list)."""
+        or BATCH_AUTO (the work list for batches of more than four buckets)."""
         _check(self.lib.gen_set_batch_form(self.h, int(form)), "gen_set_batch_form")
 
     def set_sample_form(self, form: int):
