@@ -37,17 +37,26 @@ UNIT = "frames/s"
 POLICY_SEED = 2
 MAP_SEED = 1
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel
-# from one ncu capture, valid only for the kernel source with this hash.
-# DRAM bytes (read + write) of one launch from ncu, captured on a smaller case
-# of the same kernel with inputs larger than L2 and scaled by the games it
-# processes (traffic grows in proportion); valid only for the kernel source
-# it was taken on.
-NCU_TRAFFIC = {"kernel_sha1": "df64a6d61122", "bytes_per_launch": 2 * 325966336.0,
-               "warp_inst_per_launch": 2 * 58977272.0, "captured": "32,768 games (x2)", "games": 65536}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# from one ncu capture, valid only for the kernel source with this hash: the
+# step kernel on the default workload's own 65,536 games (a one-pass capture
+# of one launch); the sampler on 16,384 games, scaled by the games it
+# processes (traffic grows in proportion).  Writes still dirty in the L2
+# when a launch ends are not in its DRAM count.
+NCU_TRAFFIC = {"kernel_sha1": "9c26d56607a0", "bytes_per_launch": 153821952.0 + 556117248.0,
+               "warp_inst_per_launch": 118072429.0, "captured": "65,536 games (the bench's own launch)",
+               "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
-SAMPLE_NCU = {"kernel_sha1": "1229b630d960", "bytes_per_launch": 4 * 137880064.0,
-              "warp_inst_per_launch": 4 * 52898856.0, "captured": "16,384 games (x4)", "games": 65536}
+SAMPLE_NCU = {"kernel_sha1": "1229b630d960", "bytes_per_launch": 4 * (133582848.0 + 4239616.0),
+              "warp_inst_per_launch": 4 * 52820402.0, "captured": "16,384 games (x4)", "games": 65536}
+# DRAM bytes of one frame of the ragged and mixed workloads, each in the form
+# that the default batch rule picks (per-bucket launches for the four ragged
+# buckets, summed; one work-list launch for the fifteen mixed buckets)
+ROLLOUT_NCU = {"kernel_sha1": "9c26d56607a0",
+               "1v1-131072-ragged15to30": {"form": "plain_buckets", "bytes_per_frame":
+                                           (30465536.0 + 145797888.0 + 139028480.0 + 5468672.0)
+                                           + (51076864.0 + 456136960.0 + 427234304.0 + 3328.0)},
+               "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128563712.0 + 867591680.0}}
 FEATURE_NCU_TRAFFIC = {"kernel_sha1": "0becd141ea17", "bytes_per_launch": 8 * 1911037952.0,
                        "captured": "8,192 games (x8)", "games": 65536}
 
@@ -503,10 +512,13 @@ def rollout_record(args, name: str, K: int = 64, rounds: int = 1, rank: int = 0,
     best_plain = max((k for k in ("plain_buckets", "plain_worklist") if k in forms),
                      key=lambda k: forms[k]["frames_per_s"])
     p = forms[best_plain]
+    cap = ROLLOUT_NCU.get(name) if ROLLOUT_NCU["kernel_sha1"] == kernel_sha1() else None
+    traffic = cap["bytes_per_frame"] if cap and cap["form"] == best_plain and G == int(workload(name)[0].shape[0]) \
+        else None
     return {"workload": name, "games": G, "rollout_frames": K, "size_buckets": buckets, "autotune": tune,
             "forms": forms,
             "roofline": {"bound": "hbm", "achieved": nbytes / (p["ms_per_frame"] * 1e-3) / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": p["hbm_frac"], "traffic": None,
+                         "unit": "GB/s", "frac": p["hbm_frac"], "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_frame": nbytes, "form": best_plain,
                          "kernel": "k_worklist" if best_plain == "plain_worklist" else "k_generals per bucket"}}
