@@ -229,8 +229,9 @@ int gen_step_host(gen_env *env, const int32_t *h_actions, const gen_outputs *h_o
  *    each rounded up to 256 bytes) exceeds 32 MiB is rejected with
  *    GEN_ERR_BAD_ARG; use gen_step_host for it.
  *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture.
+ *    per device, with that device current, and again after the device's
+ *    context has been recreated, as by cudaDeviceReset); make that first
+ *    call before any stream capture.
  *  - Every call, from any environment, shares the one array: calls whose
  *    device work overlaps (other threads, other streams) race and must be
  *    serialised by the caller.  Each call overwrites every staged byte it
