@@ -778,6 +778,9 @@ def sampler_record(args, G: int, K: int, rank: int = 0, clk=None) -> dict:
     # over the start and the end of the timed region
     owned = 0.5 * (owned0 + owned_player_cells(env))
     nbytes = 36.0 * owned + 4.0 * 576 * G + 4.0 * 2 * G
+    # the same at DRAM-sector granularity: a cell's 36 logit bytes start at a
+    # multiple of 4 bytes and always span two 32-byte sectors
+    sector_bytes = 64.0 * owned + 4.0 * 576 * G + 4.0 * 2 * G
     peak, peak_kind = peaks()
     achieved = nbytes / (samp_ms * 1e-3) / 1e9
     del env, out, logits
@@ -792,6 +795,8 @@ def sampler_record(args, G: int, K: int, rank: int = 0, clk=None) -> dict:
                                      and G == SAMPLE_NCU["games"] else None),
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": nbytes, "launch_ms": samp_ms,
+                         "sector_bytes_per_launch": sector_bytes,
+                         "frac_of_sector_bytes": sector_bytes / (samp_ms * 1e-3) / 1e9 / peak,
                          "kernel": "k_sample_cta (H x W x 9 policy sampling, a CTA per game)"},
             "issue_roofline": None}  # needs the clocks of the timed region: the caller adds it
 
