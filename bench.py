@@ -197,8 +197,11 @@ def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
         backend = "nccl" if _cuda() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)  # each rank's collectives on its own GPU
         dist.init_process_group(backend)
     return rank, world, local
 
