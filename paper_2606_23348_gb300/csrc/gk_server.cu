@@ -57,7 +57,7 @@ using Clock = std::chrono::steady_clock;
 double now_ms() { return std::chrono::duration<double, std::milli>(Clock::now().time_since_epoch()).count(); }
 
 constexpr int kMaxSmemPerCta = 227 * 1024;
-constexpr int kTicks = 2;  // ticks in flight at once, each on its own stream
+constexpr int kTicks = 2;  // ticks in flight at once, one behind the other on the tick stream
 constexpr double kTickDeadlineMs = 30000.0;  // a tick still running after this fails its requests
 
 // First-fit allocator of index ranges in [0, cap), with coalescing.
