@@ -462,9 +462,12 @@ int gen_set_lane_groups(gen_env *env, int mode);
 int gen_set_batch_form(gen_env *env, int form);
 
 /* Tuning call, no counterpart in the paper.  How gen_sample_actions
- * spreads a game over the GPU (the results are the same): 1 = one warp per game, players in turn; 2 = one CTA per game with a
- * warp per player (as many as fit in shared memory beside the board);
- * 0 (default) = 2.  GEN_ERR_BAD_ARG for NULL env or a form outside 0..2. */
+ * spreads a game over the GPU (the results are the same): 1 = one warp per
+ * game, players in turn; 2 = one CTA per game with a warp per player (as
+ * many as fit in shared memory beside the board); 3 = one CTA per player
+ * with a thread per (own cell, entry) pair; 0 (default) = 3 while games x
+ * the most players per game is at most 8 x the SM count, else 2.
+ * GEN_ERR_BAD_ARG for NULL env or a form outside 0..3. */
 int gen_set_sample_form(gen_env *env, int form);
 
 /* ---- feature tensor (App. A, table of observation channels) -------------

@@ -76,7 +76,7 @@ struct gen_env {
     int player_slots = 0;
     int pmax = 0;
     int npad_max = 0;
-    int sample_form = 0;  // gen_sample_actions: 0 (default) and 2 a CTA per game, 1 a warp per game
+    int sample_form = 0;  // gen_sample_actions: 1 a warp per game, 2 a CTA per game, 3 a CTA per player, 0 by batch size
     int rollout_form = GEN_ROLLOUT_RESIDENT;  // what GEN_ROLLOUT_AUTO runs (the autotuner's pick)
     int lane_groups = 0;  // step kernels: 0 by batch size, 1 a warp per game, 2 several per warp when allowed
     int nmax = 0;
@@ -1439,7 +1439,7 @@ int gen_set_batch_form(gen_env* e, int form) {
 
 int gen_set_sample_form(gen_env* e, int form) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
-    if (form < 0 || form > 2) return fail(GEN_ERR_BAD_ARG, "form %d outside [0, 2]", form);
+    if (form < 0 || form > 3) return fail(GEN_ERR_BAD_ARG, "form %d outside [0, 3]", form);
     e->sample_form = form;
     return GEN_OK;
 }
@@ -1579,7 +1579,7 @@ static int tune_env_forms(gen_env* e, int steps, int sms, std::string& rep) {
     if (rc == GEN_OK) {
         float bt = 1e30f;
         rep += "sampler:";
-        for (int form : {1, 2}) {
+        for (int form : {1, 2, 3}) {
             t->sample_form = form;
             auto samp = [&]() { return gen_sample_actions(t, logits, 1, t->d_actions, nullptr, s); };
             const float ms = time_calls(samp, steps, s, a, b);

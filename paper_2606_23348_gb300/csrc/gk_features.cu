@@ -28,7 +28,6 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
-#include <mutex>
 
 #include <algorithm>
 #include <cstdint>
@@ -45,7 +44,16 @@ constexpr int kWarps = 8;
 // bitsets, scoreboard; a multiple of 16 bytes
 __host__ __device__ __forceinline__ int warp_bytes(int npad_max) {
     const int nw_max = (npad_max + 31) >> 5;
-    return (4 * npad_max + 8 * nw_max + 64 + 15) & ~15;
+    return (4 * npad_max + 8 * nw_max + 64 + 8 * kMaxSide + 15) & ~15;
+}
+
+// the coordinate rows' values (Q32) by column and by row: column / (W - 1)
+// and row / (H - 1), 0 when the side is 1; computed once per game
+__device__ __forceinline__ void coord_table(float* s_coord, int H, int W, int tid, int nthreads) {
+    for (int i = tid; i < 2 * kMaxSide; i += nthreads) {
+        const int v = i < kMaxSide ? i : i - kMaxSide, side = i < kMaxSide ? W : H;
+        s_coord[i] = side > 1 && v < side ? (float)v / (float)(side - 1) : 0.0f;
+    }
 }
 
 __device__ __forceinline__ uint32_t valid_word(int N, int w) {
@@ -201,8 +209,11 @@ struct PlayerFrame {
     int nvalid;       // ring slots holding frames of this episode
 };
 
-__device__ __forceinline__ PlayerFrame player_frame(const FArgs& f, const GameInfo& gi, const GameScalars& sc,
-                                                    const int32_t* s_score, int p, int R) {
+// LOAD_HDR: the player's memory header is read from global memory here (the
+// warp form), else `h` holds it (the CTA form stages the headers)
+template <bool LOAD_HDR>
+__device__ __forceinline__ PlayerFrame player_frame_t(const FArgs& f, const GameInfo& gi, const GameScalars& sc,
+                                                      const int32_t* s_score, int p, int R, uint4 h) {
     PlayerFrame x;
     x.p = p;
     x.tp = gi.mode == 1 ? (p >> 1) : p;
@@ -221,7 +232,7 @@ __device__ __forceinline__ PlayerFrame player_frame(const FArgs& f, const GameIn
     x.f_opp_land = (float)opp_land;
     x.f_opp_army = (float)opp_army;
     // memory header: clear on a new epoch, fold once per frame
-    const uint4 h = f.hdr[x.slot];
+    if (LOAD_HDR) h = f.hdr[x.slot];
     x.cleared = h.x != sc.epoch + 1u;
     x.fold = x.cleared || h.y != sc.frame;
     x.n_fold = (x.cleared ? 0u : h.z) + (x.fold ? 1u : 0u);
@@ -251,12 +262,18 @@ __device__ __forceinline__ void player_tokens(const FArgs& f, const PlayerFrame&
     }
 }
 
-// cells c .. c+3 of one player: read and fold the memory, write the 24 + 2K rows
-__device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, const PlayerFrame& x, int turn,
-                                          float f_turn, float f_phase, const int16_t* s_army, const int8_t* s_owner,
-                                          const int8_t* s_terrain, const uint32_t* s_vis, int c) {
+// cells c .. c+3 of one player: read and fold the memory, write the 24 + 2K
+// rows.  mem(mb, lea, let) supplies the memory of the four cells (zeros when
+// cleared) and ring_pair(back, own, enemy) the army planes `back` frames ago
+// (zeros where the episode has none): global loads for the warp form, a
+// shared-memory staging for the CTA form.
+template <class Mem, class Ring>
+__device__ __forceinline__ void cell_quad_from(const FArgs& f, const GameInfo& gi, const PlayerFrame& x, int turn,
+                                               float f_turn, float f_phase, const int16_t* s_army,
+                                               const int8_t* s_owner, const int8_t* s_terrain, const uint32_t* s_vis,
+                                               const float* s_coord, int c, Mem mem, Ring ring_pair) {
     const int H = gi.H, W = gi.W, N = gi.N, Npad = gi.Npad, mode = gi.mode, p = x.p, tp = x.tp;
-    const int C = 24 + 2 * f.hist, K = f.hist, R = f.hist + 1;
+    const int C = 24 + 2 * f.hist, K = f.hist;
     const int64_t q0 = gi.plane_off + (int64_t)p * Npad;  // this player's plane
     float* out = f.out + q0 * C;
     const int64_t pc = q0 + c;
@@ -264,11 +281,7 @@ __device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, co
     uint32_t mb = 0u;
     uint2 lea = make_uint2(0u, 0u);
     int4 let = make_int4(0, 0, 0, 0);
-    if (!x.cleared) {
-        mb = __ldcs(reinterpret_cast<const unsigned int*>(f.mem_bits + pc));
-        lea = __ldcs(reinterpret_cast<const uint2*>(f.mem_army + pc));
-        let = __ldcs(reinterpret_cast<const int4*>(f.mem_turn + pc));
-    }
+    mem(mb, lea, let);
     // board of cells c..c+3
     const uint2 a2 = *reinterpret_cast<const uint2*>(s_army + c);
     const uint32_t ow = *reinterpret_cast<const uint32_t*>(s_owner + c);
@@ -346,8 +359,8 @@ __device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, co
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool in = (fl >> (8 * i)) & kFIn;
-            cx[i] = in && W > 1 ? (float)col / (float)(W - 1) : 0.0f;
-            cy[i] = in && H > 1 ? (float)r / (float)(H - 1) : 0.0f;
+            cx[i] = in ? s_coord[col] : 0.0f;
+            cy[i] = in ? s_coord[kMaxSide + min(r, H - 1)] : 0.0f;
             if (++col == W) {
                 col = 0;
                 ++r;
@@ -357,16 +370,7 @@ __device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, co
         st4(row += Npad, cy[0], cy[1], cy[2], cy[3]);
     }
     // deltas (Q33): plane 0 is this frame, plane k >= 1 the ring slot k back;
-    // each pair is loaded two iterations ahead of the stores that use it
-    auto ring_pair = [&](int back, uint2& o, uint2& e) {  // own / enemy planes `back` frames ago
-        o = make_uint2(0u, 0u);
-        e = o;
-        if (back < x.nvalid) {
-            const int sl = (x.head - back + R) % R;
-            o = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
-            e = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
-        }
-    };
+    // each pair is fetched two iterations ahead of the stores that use it
     uint2 po = own, pe = ene, o1, e1, o2, e2;
     ring_pair(1, o1, e1);
     ring_pair(2, o2, e2);
@@ -385,7 +389,34 @@ __device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, co
     }
 }
 
+// the warp form's cells: memory and ring planes loaded from global memory
+__device__ __forceinline__ void cell_quad(const FArgs& f, const GameInfo& gi, const PlayerFrame& x, int turn,
+                                          float f_turn, float f_phase, const int16_t* s_army, const int8_t* s_owner,
+                                          const int8_t* s_terrain, const uint32_t* s_vis, const float* s_coord,
+                                          int c) {
+    const int R = f.hist + 1;
+    const int64_t pc = gi.plane_off + (int64_t)x.p * gi.Npad + c;
+    auto mem = [&](uint32_t& mb, uint2& lea, int4& let) {
+        if (!x.cleared) {
+            mb = __ldcs(reinterpret_cast<const unsigned int*>(f.mem_bits + pc));
+            lea = __ldcs(reinterpret_cast<const uint2*>(f.mem_army + pc));
+            let = __ldcs(reinterpret_cast<const int4*>(f.mem_turn + pc));
+        }
+    };
+    auto ring_pair = [&](int back, uint2& o, uint2& e) {  // own / enemy planes `back` frames ago
+        o = make_uint2(0u, 0u);
+        e = o;
+        if (back < x.nvalid) {
+            const int sl = (x.head - back + R) % R;
+            o = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl) * f.plane_cells + pc));
+            e = __ldcs(reinterpret_cast<const uint2*>(f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc));
+        }
+    };
+    cell_quad_from(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis, s_coord, c, mem, ring_pair);
+}
+
 __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
+    chain_entry();
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gidx = blockIdx.x * kWarps + wid;
@@ -399,6 +430,7 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     uint32_t* s_team = reinterpret_cast<uint32_t*>(base + 4 * f.npad_max);
     uint32_t* s_vis = s_team + nw_max;
     int32_t* s_score = reinterpret_cast<int32_t*>(s_vis + nw_max);  // land[8], army[8]
+    float* s_coord = reinterpret_cast<float*>(s_score + 16);         // [2 * kMaxSide]
 
     const GameInfo gi = f.info[gidx];
     const int N = gi.N, Npad = gi.Npad, P = gi.P;
@@ -418,6 +450,7 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
             reinterpret_cast<uint4*>(s_terrain)[v] = __ldg(gt + v);
         }
     }
+    coord_table(s_coord, gi.H, gi.W, lane, 32);
     __syncwarp();
 
     // public scoreboard (Sec. IV-B): land and army per player
@@ -431,23 +464,77 @@ __global__ void __launch_bounds__(256, 4) k_features(const FArgs f) {
     for (int p = 0; p < P; ++p) {
         const int tp = gi.mode == 1 ? (p >> 1) : p;
         vis_of(s_owner, s_team, s_vis, N, gi.W, nw, gi.mode, tp, (sc.alive >> p) & 1u, lane);
-        const PlayerFrame x = player_frame(f, gi, sc, s_score, p, R);
+        const PlayerFrame x = player_frame_t<true>(f, gi, sc, s_score, p, R, make_uint4(0u, 0u, 0u, 0u));
         if (f.window > 0) player_tokens(f, x, lane == 0, (uint32_t)lane, 32u);
         for (int c = 4 * lane; c < Npad; c += 128)
-            cell_quad(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis, c);
+            cell_quad(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis, s_coord, c);
         if (x.fold && lane == 0) f.hdr[x.slot] = make_uint4(sc.epoch + 1u, sc.frame, x.n_fold, 0u);
         __syncwarp();
     }
 }
 
 // shared memory of the one-game CTA: board, a scratch and a visibility
-// bitset per player, scoreboard; a multiple of 16 bytes
-__host__ __device__ __forceinline__ int cta_bytes(int npad_max, int pmax) {
+// bitset per player, scoreboard, players' memory headers, then per warp the
+// staging of kItemsPerBatch items; a multiple of 16 bytes
+constexpr int kItemsPerBatch = 2;
+__host__ __device__ __forceinline__ int cta_hdr_offset(int npad_max, int pmax) {  // 16-byte aligned
     const int nw_max = (npad_max + 31) >> 5;
-    return (4 * npad_max + 8 * nw_max * pmax + 64 + 15) & ~15;
+    return (4 * npad_max + 8 * nw_max * pmax + 64 + 8 * kMaxSide + 15) & ~15;
+}
+__host__ __device__ __forceinline__ int cta_head_bytes(int npad_max, int pmax) {
+    return cta_hdr_offset(npad_max, pmax) + 16 * kMaxPlayers;
+}
+// one item's staging, lane-major: memory bits (4 B), last enemy army (8 B) and
+// turn (16 B) of the lane's four cells, then K (own, enemy) ring plane pairs
+// (8 + 8 B)
+__host__ __device__ __forceinline__ int item_stage_bytes(int hist) { return 32 * (28 + 16 * hist); }
+__host__ __device__ __forceinline__ int cta_bytes(int npad_max, int pmax, int hist, int warps) {
+    return cta_head_bytes(npad_max, pmax) + warps * kItemsPerBatch * item_stage_bytes(hist);
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+                 : "memory");
+}
+
+// the part of a player's memory header that decides what is read
+struct HdrState {
+    bool cleared;
+    int head, nvalid;
+};
+__device__ __forceinline__ HdrState hdr_state(const uint4 h, const GameScalars& sc, int R) {
+    HdrState y;
+    y.cleared = h.x != sc.epoch + 1u;
+    const bool fold = y.cleared || h.y != sc.frame;
+    const uint32_t n_fold = (y.cleared ? 0u : h.z) + (fold ? 1u : 0u);
+    y.head = (int)((n_fold - 1u) % (uint32_t)R);
+    y.nvalid = (int)min(n_fold, (uint32_t)R);
+    return y;
+}
+
+// issue the copies of one item's memory and older ring planes into `st`
+// (this lane's share; completed by cp.async.wait_all)
+__device__ __forceinline__ void stage_item(const FArgs& f, const HdrState& y, int64_t pc, char* st, int lane) {
+    const int K = f.hist, R = f.hist + 1;
+    if (!y.cleared) {
+        cp_async4(st + 4 * lane, f.mem_bits + pc);
+        cp_async8(st + 128 + 8 * lane, f.mem_army + pc);
+        cp_async16(st + 384 + 16 * lane, f.mem_turn + pc);
+    }
+    for (int back = 1; back <= K && back < y.nvalid; ++back) {
+        const int sl = (y.head - back + R) % R;
+        char* d = st + 896 + 512 * (back - 1);
+        cp_async8(d + 8 * lane, f.ring + (int64_t)(2 * sl) * f.plane_cells + pc);
+        cp_async8(d + 256 + 8 * lane, f.ring + (int64_t)(2 * sl + 1) * f.plane_cells + pc);
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_features_cta(const FArgs f, int pmax) {
+    chain_entry();
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int gidx = blockIdx.x;  // the grid is one CTA per game
@@ -459,13 +546,18 @@ __global__ void __launch_bounds__(1024) k_features_cta(const FArgs f, int pmax) 
     uint32_t* s_vis = reinterpret_cast<uint32_t*>(smem + 4 * f.npad_max);  // [pmax][nw_max]
     uint32_t* s_team = s_vis + pmax * nw_max;                               // [pmax][nw_max] scratch
     int32_t* s_score = reinterpret_cast<int32_t*>(s_team + pmax * nw_max);  // land[8], army[8]
+    float* s_coord = reinterpret_cast<float*>(s_score + 16);                // [2 * kMaxSide]
+    uint4* s_hdr = reinterpret_cast<uint4*>(smem + cta_hdr_offset(f.npad_max, pmax));  // [kMaxPlayers]
+    char* s_stage = smem + cta_head_bytes(f.npad_max, pmax) + (size_t)wid * kItemsPerBatch * item_stage_bytes(f.hist);
 
     const GameInfo gi = f.info[gidx];
     const int N = gi.N, Npad = gi.Npad, P = gi.P;
     const int nw = (Npad + 31) >> 5;
     const GameScalars sc = f.scal[gidx];
     const int R = f.hist + 1;
-    {  // board to shared memory, every 16-byte copy in flight at once
+    const int chunks = (Npad + 127) >> 7;  // 128 cells: four per lane
+    const int items = P * chunks;
+    {  // board to shared memory, every 16-byte copy in flight at once; the players' headers
         const uint4* ga = reinterpret_cast<const uint4*>(f.army + gi.cell_off);
         const uint4* go = reinterpret_cast<const uint4*>(f.owner + gi.cell_off);
         const uint4* gt = reinterpret_cast<const uint4*>(f.terrain + gi.cell_off);
@@ -475,9 +567,28 @@ __global__ void __launch_bounds__(1024) k_features_cta(const FArgs f, int pmax) 
             cp_async16(reinterpret_cast<uint4*>(s_owner) + v, go + v);
             cp_async16(reinterpret_cast<uint4*>(s_terrain) + v, gt + v);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
     }
+    coord_table(s_coord, gi.H, gi.W, threadIdx.x, blockDim.x);
+    uint4 my_hdr = make_uint4(0u, 0u, 0u, 0u);
+    if ((int)threadIdx.x < P) {  // read before the last barrier, written after it
+        my_hdr = f.hdr[gi.player_off + threadIdx.x];
+        s_hdr[threadIdx.x] = my_hdr;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
+    // this warp's items are wid, wid + nwarps, ...; batch b holds the
+    // kItemsPerBatch of them from the (b * kItemsPerBatch)-th on
+    auto stage_batch = [&](int b) {
+        for (int j = 0; j < kItemsPerBatch; ++j) {
+            const int item = wid + nwarps * (b * kItemsPerBatch + j);
+            if (item >= items) break;
+            const int p = item / chunks, c = 128 * (item - p * chunks) + 4 * lane;
+            if (c < Npad)
+                stage_item(f, hdr_state(s_hdr[p], sc, R), gi.plane_off + (int64_t)p * Npad + c,
+                           s_stage + j * item_stage_bytes(f.hist), lane);
+        }
+    };
+    stage_batch(0);  // in flight while the scoreboard and visibility are built
     // scoreboard and visibility (Sec. IV-B): warp q takes player q
     for (int q = wid; q < P; q += nwarps) {
         score_of(s_army, s_owner, N, q, s_score, lane);
@@ -489,19 +600,44 @@ __global__ void __launch_bounds__(1024) k_features_cta(const FArgs f, int pmax) 
     const int turn = (int)sc.turn;
     const float f_turn = (float)turn;
     const float f_phase = (float)(turn % 50) / 50.0f;
-    const int chunks = (Npad + 127) >> 7;  // 128 cells: four per lane
-    uint4 my_hdr = make_uint4(0u, 0u, 0u, 0u);
-    if ((int)threadIdx.x < P) my_hdr = f.hdr[gi.player_off + threadIdx.x];  // read before the barrier below
-    for (int item = wid; item < P * chunks; item += nwarps) {
-        const int p = item / chunks, k = item - p * chunks;
-        const PlayerFrame x = player_frame(f, gi, sc, s_score, p, R);
-        // the player's tokens are shared by its chunk items
-        if (f.window > 0) {
-            const int per = min(chunks, nwarps);
-            if (k < per) player_tokens(f, x, k == 0 && lane == 0, (uint32_t)(32 * k + lane), (uint32_t)(32 * per));
+    const int K = f.hist;
+    const int mine = items > wid ? (items - wid + nwarps - 1) / nwarps : 0;
+    for (int b = 0; kItemsPerBatch * b < mine; ++b) {
+        if (b > 0) stage_batch(b);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int j = 0; j < kItemsPerBatch; ++j) {
+            const int item = wid + nwarps * (b * kItemsPerBatch + j);
+            if (item >= items) break;
+            const int p = item / chunks, k = item - p * chunks;
+            const PlayerFrame x = player_frame_t<false>(f, gi, sc, s_score, p, R, s_hdr[p]);
+            // the player's tokens are shared by its chunk items
+            if (f.window > 0) {
+                const int per = min(chunks, nwarps);
+                if (k < per) player_tokens(f, x, k == 0 && lane == 0, (uint32_t)(32 * k + lane), (uint32_t)(32 * per));
+            }
+            const int c = 128 * k + 4 * lane;
+            if (c >= Npad) continue;
+            const char* st = s_stage + j * item_stage_bytes(f.hist);
+            auto mem = [&](uint32_t& mb, uint2& lea, int4& let) {
+                if (!x.cleared) {
+                    mb = *reinterpret_cast<const uint32_t*>(st + 4 * lane);
+                    lea = *reinterpret_cast<const uint2*>(st + 128 + 8 * lane);
+                    let = *reinterpret_cast<const int4*>(st + 384 + 16 * lane);
+                }
+            };
+            auto ring_pair = [&](int back, uint2& o, uint2& e) {
+                o = make_uint2(0u, 0u);
+                e = o;
+                if (back <= K && back < x.nvalid) {
+                    const char* d = st + 896 + 512 * (back - 1);
+                    o = *reinterpret_cast<const uint2*>(d + 8 * lane);
+                    e = *reinterpret_cast<const uint2*>(d + 256 + 8 * lane);
+                }
+            };
+            cell_quad_from(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis + p * nw_max, s_coord, c,
+                           mem, ring_pair);
         }
-        const int c = 128 * k + 4 * lane;
-        if (c < Npad) cell_quad(f, gi, x, turn, f_turn, f_phase, s_army, s_owner, s_terrain, s_vis + p * nw_max, c);
+        __syncwarp();  // this warp's staging is reused by its next batch
     }
     __syncthreads();  // every warp has read the headers
     if ((int)threadIdx.x < P) {
@@ -527,33 +663,18 @@ int launch_features(const FArgs& f, int pmax, int form, void* stream) {
     }
     if (form == 0) form = f.n_games < 16 * sms ? 2 : 1;  // measured crossover: 2,048 games CTA, 4,096 warp
     if (form == 2) {
+        // a warp per kItemsPerBatch (player, chunk) items, as many as the
+        // staging leaves room for in shared memory
         const int chunks = (f.npad_max + 127) >> 7;
-        int warps = std::max(1, std::min(32, pmax * chunks));  // one (player, chunk) item each
-        const int smem = cta_bytes(f.npad_max, pmax);
+        const int per_warp = kItemsPerBatch * item_stage_bytes(f.hist);
+        const int fit = (227 * 1024 - cta_head_bytes(f.npad_max, pmax)) / per_warp;
+        const int warps = std::max(1, std::min(std::min(32, fit), (pmax * chunks + kItemsPerBatch - 1) / kItemsPerBatch));
+        const int smem = cta_bytes(f.npad_max, pmax, f.hist, warps);
         static SmemLimit limit;
         const void* fn = (const void*)k_features_cta;
-        int e = limit.raise(&fn, 1, smem);
+        const int e = limit.raise(&fn, 1, smem);
         if (e != 0) return e;
-        // a grid of at most 1.5 waves runs faster with half the warps (two
-        // items each) and so one wave (measured: 512 games 37 -> 31 us,
-        // 1,024 games 57 against 61 us the other way round)
-        int per_sm = 0;
-        {
-            static std::mutex mu;
-            static int key_warps = -1, key_smem = -1, cached = 0;
-            std::lock_guard<std::mutex> lk(mu);
-            if (key_warps != warps || key_smem != smem) {
-                if ((e = (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, k_features_cta, 32 * warps,
-                                                                            smem)) != 0)
-                    return e;
-                key_warps = warps;
-                key_smem = smem;
-            }
-            per_sm = cached;
-        }
-        if (warps > 1 && 2 * (int64_t)f.n_games <= 3 * (int64_t)per_sm * sms) warps = (warps + 1) / 2;
-        k_features_cta<<<f.n_games, 32 * warps, smem, (cudaStream_t)stream>>>(f, pmax);
-        return (int)cudaGetLastError();
+        return launch_chained(k_features_cta, dim3(f.n_games), dim3(32 * warps), smem, (cudaStream_t)stream, f, pmax);
     }
     const int smem = kWarps * warp_bytes(f.npad_max);
     static SmemLimit limit;
@@ -561,8 +682,7 @@ int launch_features(const FArgs& f, int pmax, int form, void* stream) {
     const int e = limit.raise(&fn, 1, smem);
     if (e != 0) return e;
     const int blocks = (f.n_games + kWarps - 1) / kWarps;
-    k_features<<<blocks, 32 * kWarps, smem, (cudaStream_t)stream>>>(f);
-    return (int)cudaGetLastError();
+    return launch_chained(k_features, dim3(blocks), dim3(32 * kWarps), smem, (cudaStream_t)stream, f);
 }
 
 }  // namespace gk

@@ -1449,6 +1449,7 @@ __device__ __forceinline__ void run_game(const KArgs& a, const Smem& s, char* wa
 // best with 85 (3 CTAs).
 template <bool MULTI, bool SPAWN, int LW, bool UNI>
 __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) {
+    chain_entry();
     extern __shared__ __align__(16) char smem_raw[];
     constexpr int kGroups = 32 / LW;  // games per warp
     const int wl = threadIdx.x & 31;
@@ -1481,6 +1482,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_generals(const KArgs a) 
 // so that the next item may carve the same bytes differently.
 template <bool MULTI>
 __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_worklist(const KArgs a, const WArgs w) {
+    chain_entry();
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_item;
     const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
@@ -1584,11 +1586,8 @@ int launch_worklist(const KArgs& a, const WArgs& w, int cta_smem, int ctas, void
     const bool multi = a.frames > 1 || a.action_log;
     const int grid = ctas < w.n_items ? ctas : w.n_items;
     if (grid <= 0) return 0;
-    if (multi)
-        k_worklist<true><<<grid, 256, cta_smem, st>>>(a, w);
-    else
-        k_worklist<false><<<grid, 256, cta_smem, st>>>(a, w);
-    return (int)cudaGetLastError();
+    if (multi) return launch_chained(k_worklist<true>, dim3(grid), dim3(256), cta_smem, st, a, w);
+    return launch_chained(k_worklist<false>, dim3(grid), dim3(256), cta_smem, st, a, w);
 }
 
 int warp_smem_bytes(int npad_max, int pmax, int* nw_stride, bool narrow) {
@@ -1694,15 +1693,10 @@ int launch_plain(const KArgs& a, bool multi, int fixed_warps, int max_ctas, int 
     // multi-frame launches: a grid of many waves, groups stride over any items beyond it
     if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
     const dim3 grid(blocks), block(32 * warps);
-    if (multi && a.uniform)
-        k_generals<true, false, LW, true><<<grid, block, smem, st>>>(a);
-    else if (multi)
-        k_generals<true, false, LW, false><<<grid, block, smem, st>>>(a);
-    else if (a.uniform)
-        k_generals<false, false, LW, true><<<grid, block, smem, st>>>(a);
-    else
-        k_generals<false, false, LW, false><<<grid, block, smem, st>>>(a);
-    return (int)cudaGetLastError();
+    if (multi && a.uniform) return launch_chained(k_generals<true, false, LW, true>, grid, block, smem, st, a);
+    if (multi) return launch_chained(k_generals<true, false, LW, false>, grid, block, smem, st, a);
+    if (a.uniform) return launch_chained(k_generals<false, false, LW, true>, grid, block, smem, st, a);
+    return launch_chained(k_generals<false, false, LW, false>, grid, block, smem, st, a);
 }
 
 int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
@@ -1751,11 +1745,8 @@ int launch_step(const KArgs& a, int warps_per_cta, int max_ctas, void* stream) {
         const int smem = a.warp_smem * warps;
         int blocks = (a.n_items + warps - 1) / warps;
         if (multi && max_ctas > 0 && blocks > 64 * max_ctas) blocks = 64 * max_ctas;
-        if (multi)
-            k_generals<true, true, 32, false><<<blocks, 32 * warps, smem, st>>>(a);
-        else
-            k_generals<false, true, 32, false><<<blocks, 32 * warps, smem, st>>>(a);
-        return (int)cudaGetLastError();
+        if (multi) return launch_chained(k_generals<true, true, 32, false>, dim3(blocks), dim3(32 * warps), smem, st, a);
+        return launch_chained(k_generals<false, true, 32, false>, dim3(blocks), dim3(32 * warps), smem, st, a);
     }
     return launch_plain<32>(a, multi, warps_per_cta, max_ctas, sms, st);
 }

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "gk_internal.h"
@@ -267,6 +268,7 @@ __device__ __forceinline__ int32_t sample_player(const SArgs& a, const GameInfo&
             run += __shfl_sync(kAll, incl, 31);
         }
     }
+    if (jr < 0) return 0;  // S = 0: only when every legal logit is -inf (outside the documented domain)
     const int i = 32 * jr + lane;
     const uint64_t wi = i < n ? s_w[i] : 0u;
     const uint64_t incl = warp_incl64(wi, lane);
@@ -285,6 +287,7 @@ __device__ __forceinline__ int32_t sample_player(const SArgs& a, const GameInfo&
 
 // one warp per game, players in turn
 __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta) {
+    chain_entry();
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gidx = blockIdx.x * warps_per_cta + wid;
@@ -313,6 +316,7 @@ __global__ void __launch_bounds__(256) k_sample(const SArgs a, int warps_per_cta
 // one CTA per game (small batches): warp q takes players q, q + warps, ...
 // and mask rows q, q + warps, ... over its own region of shared memory
 __global__ void __launch_bounds__(256) k_sample_cta(const SArgs a) {
+    chain_entry();
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int gidx = blockIdx.x;  // the grid is one CTA per game
@@ -336,13 +340,230 @@ __global__ void __launch_bounds__(256) k_sample_cta(const SArgs a) {
     }
 }
 
+// ---- entry-parallel form (small batches) --------------------------------
+// One CTA of kWideThreads threads per (game, player): the player's own cells
+// are listed in index order by contiguous ranges of cells per thread and a
+// block scan; then every (own cell, entry) pair gets a thread of its own,
+// entry e of the list being entry e mod 9 of own cell e / 9 -- index order.
+// Pass 1 loads each legal entry's logit once (the first kWideRegRounds
+// rounds of the block stay in registers) and takes the block maximum; pass 2
+// forms the integer weights and each warp's sum per round; one warp then
+// sums them (S), draws r and finds the (round, warp) where the running sum
+// first exceeds r; that warp scans its own 32 weights for the entry.  A
+// game's chain is a few dependent steps instead of a warp's walk over its
+// own cells, which is what sets the time when a launch fills less than a
+// wave.
+constexpr int kWideThreads = 128;
+constexpr int kWideWarps = kWideThreads / 32;
+constexpr int kWideRegRounds = 4;
+constexpr float kNegInf = -__builtin_huge_valf();
+
+__host__ __device__ __forceinline__ int wide_rounds(int npad_max) {
+    return (9 * npad_max + kWideThreads - 1) / kWideThreads;
+}
+// board (4 B per cell), own-cell list and legal bits (2 + 2 B per cell),
+// per-round warp sums (4 B each), block scratch, one mask staging row per warp
+__host__ __device__ __forceinline__ int wide_bytes(int npad_max) {
+    const int rw = (4 * wide_rounds(npad_max) * kWideWarps + 15) & ~15;
+    return 8 * npad_max + rw + 64 + 288 * kWideWarps;
+}
+
+__global__ void __launch_bounds__(kWideThreads) k_sample_wide(const SArgs a, int pmax) {
+    chain_entry();
+    extern __shared__ __align__(16) char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int gidx = blockIdx.x / pmax, p = blockIdx.x - gidx * pmax;
+    const GameInfo gi = a.info[gidx];
+    if (p >= gi.P) return;
+    const GameScalars sc = a.scal[gidx];
+    const int np = a.npad_max, N = gi.N, Npad = gi.Npad;
+    uint16_t* s_list = reinterpret_cast<uint16_t*>(smem + 4 * np);
+    uint16_t* s_legal = reinterpret_cast<uint16_t*>(smem + 6 * np);
+    uint32_t* s_ws = reinterpret_cast<uint32_t*>(smem + 8 * np);  // [round][warp]
+    const int rw = (4 * wide_rounds(np) * kWideWarps + 15) & ~15;
+    uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + 8 * np + rw);  // 16 words
+    uint8_t* s_mask = reinterpret_cast<uint8_t*>(smem + 8 * np + rw + 64) + 288 * wid;
+    stage_board(a, gi, smem, np, tid, kWideThreads);
+    __syncthreads();
+    const int16_t* s_army = reinterpret_cast<const int16_t*>(smem);
+    const int8_t* s_owner = reinterpret_cast<const int8_t*>(smem + 2 * np);
+    const uint8_t* s_terrain = reinterpret_cast<const uint8_t*>(smem + 3 * np);
+    const bool moves = ((sc.alive >> p) & 1u) && !sc.finished;
+    if (a.mask9) {  // player p's plane: rows of 32 cells, one warp each
+        for (int r0 = 32 * wid; r0 < Npad; r0 += 32 * kWideWarps) {
+            const int cells = min(32, Npad - r0), c = r0 + lane;
+            const uint32_t bits =
+                c < N && s_owner[c] == p ? legal9(true, s_army[c], s_terrain[c], moves) : 0u;
+            if (lane < cells)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) s_mask[9 * lane + k] = (uint8_t)((bits >> k) & 1u);
+            __syncwarp();
+            const int64_t base = (gi.plane_off + (int64_t)p * Npad) * 9;
+            if (lane < ((9 * cells) >> 4))
+                reinterpret_cast<uint4*>(a.mask9 + base + 9 * r0)[lane] = reinterpret_cast<const uint4*>(s_mask)[lane];
+            __syncwarp();
+        }
+    }
+    if (!a.logits) return;
+    // the player's cells in index order: a contiguous range of cells per thread
+    const int cpt = (N + kWideThreads - 1) / kWideThreads;
+    const int c0 = min(N, tid * cpt), c1 = min(N, c0 + cpt);
+    int cnt = 0;
+    for (int c = c0; c < c1; ++c) cnt += s_owner[c] == p;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_misc[wid] = (uint32_t)incl;
+    __syncthreads();
+    int before = incl - cnt, n = 0;
+#pragma unroll
+    for (int q = 0; q < kWideWarps; ++q) {
+        const int t = (int)s_misc[q];
+        if (q < wid) before += t;
+        n += t;
+    }
+    for (int c = c0, i = before; c < c1; ++c)
+        if (s_owner[c] == p) {
+            s_list[i] = (uint16_t)c;
+            s_legal[i] = (uint16_t)legal9(true, s_army[c], s_terrain[c], moves);
+            ++i;
+        }
+    __syncthreads();  // the list is complete; s_misc free again
+    if (n == 0) {
+        if (tid == 0 && a.actions) a.actions[gi.player_off + p] = 0;
+        return;
+    }
+    const float* lg = a.logits + (gi.plane_off + (int64_t)p * Npad) * 9;
+    const int ne = 9 * n, rounds = (ne + kWideThreads - 1) / kWideThreads;
+    // entry e of the list: its logit if legal, else -inf
+    auto logit_of = [&](int e) -> float {
+        if (e >= ne) return kNegInf;
+        const int i = e / 9, k = e - 9 * i;
+        if (!((s_legal[i] >> k) & 1u)) return kNegInf;
+        return __ldcg(lg + 9 * (int)s_list[i] + k);
+    };
+    // pass 1: the maximum legal logit
+    float v[kWideRegRounds];
+    float m = kNegInf;
+#pragma unroll
+    for (int j = 0; j < kWideRegRounds; ++j) {
+        v[j] = j < rounds ? logit_of(tid + kWideThreads * j) : kNegInf;
+        m = fmaxf(m, v[j]);
+    }
+    for (int j = kWideRegRounds; j < rounds; ++j) m = fmaxf(m, logit_of(tid + kWideThreads * j));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
+    if (lane == 0) s_misc[wid] = __float_as_uint(m);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kWideWarps; ++q) m = fmaxf(m, __uint_as_float(s_misc[q]));
+    // pass 2: integer weights (0 for illegal entries) and each warp's sum per round
+    auto weight_of = [&](float x) -> uint32_t { return x == kNegInf ? 0u : weight_shift(x, m); };
+    uint32_t w[kWideRegRounds];
+#pragma unroll
+    for (int j = 0; j < kWideRegRounds; ++j) {
+        w[j] = weight_of(v[j]);
+        if (j < rounds) {
+            const uint32_t ws = __reduce_add_sync(kAll, w[j]);  // at most 32 * 2^24
+            if (lane == 0) s_ws[j * kWideWarps + wid] = ws;
+        }
+    }
+    for (int j = kWideRegRounds; j < rounds; ++j) {
+        const uint32_t ws = __reduce_add_sync(kAll, weight_of(logit_of(tid + kWideThreads * j)));
+        if (lane == 0) s_ws[j * kWideWarps + wid] = ws;
+    }
+    __syncthreads();
+    // one warp: S, r, then the (round, warp) slot where the running sum first exceeds r
+    if (wid == 0) {
+        const int slots = rounds * kWideWarps;
+        uint64_t S = 0;
+        for (int t = lane; t < slots; t += 32) S += s_ws[t];
+        S = warp_sum64(S);
+        const uint64_t d = stream_out(hkey(a.seed, gi.game_id, sc.frame, (uint64_t)p), 7);
+        const uint64_t r = __umul64hi(d, S);
+        uint64_t run = 0;
+        int found = -1;
+        for (int t0 = 0; t0 < slots && found < 0; t0 += 32) {
+            const uint64_t x = t0 + lane < slots ? s_ws[t0 + lane] : 0u;
+            const uint64_t inc = warp_incl64(x, lane);
+            const unsigned hit = __ballot_sync(kAll, run + inc > r);
+            if (hit) {
+                const int L = __ffs(hit) - 1;
+                found = t0 + L;
+                run += __shfl_sync(kAll, inc - x, L);
+            } else {
+                run += __shfl_sync(kAll, inc, 31);
+            }
+        }
+        if (lane == 0) {
+            s_misc[8] = (uint32_t)found;
+            s_misc[10] = (uint32_t)run;
+            s_misc[11] = (uint32_t)(run >> 32);
+            s_misc[12] = (uint32_t)r;
+            s_misc[13] = (uint32_t)(r >> 32);
+        }
+    }
+    __syncthreads();
+    const int found = (int)s_misc[8];
+    if (found < 0) {  // S = 0: only when every legal logit is -inf (outside the documented domain)
+        if (tid == 0 && a.actions) a.actions[gi.player_off + p] = 0;
+        return;
+    }
+    const int jf = found / kWideWarps;
+    if (wid != found - jf * kWideWarps) return;
+    const uint64_t run = s_misc[10] | ((uint64_t)s_misc[11] << 32);
+    const uint64_t r = s_misc[12] | ((uint64_t)s_misc[13] << 32);
+    uint32_t wj = 0u;
+#pragma unroll
+    for (int j = 0; j < kWideRegRounds; ++j)
+        if (j == jf) wj = w[j];
+    if (jf >= kWideRegRounds) wj = weight_of(logit_of(tid + kWideThreads * jf));
+    uint32_t inc = wj;  // at most 32 * 2^24: no overflow
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kAll, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const unsigned hit = __ballot_sync(kAll, run + inc > r);
+    if (lane == __ffs(hit) - 1 && a.actions) {
+        const int e = tid + kWideThreads * jf, i = e / 9;
+        a.actions[gi.player_off + p] = 9 * (int)s_list[i] + (e - 9 * i);
+    }
+}
+
 }  // namespace
 
 int launch_sample(const SArgs& a, int pmax, int form, void* stream) {
     if (a.n_games <= 0) return 0;
-    // a CTA per game by default: measured faster at every batch from 512 to
-    // 65,536 games of 24x24 but one (more warps per SM, players side by side)
-    if (form == 0) form = 2;
+    // by default a CTA per player with a thread per entry while the players
+    // fill at most about one wave of those CTAs, else a CTA per game
+    // (measured on 24x24 1v1 at mid-game: 512 games 6.1 against 7.8 us,
+    // 1,024 games 9.8 against 8.8 us; from 2,048 games on the CTA per game
+    // is the fastest form)
+    if (form == 0) {
+        static std::atomic<int> sm_count{0};  // of the first device used: only the form depends on it
+        int sms = sm_count.load(std::memory_order_relaxed);
+        if (sms == 0) {
+            int dev = 0, n = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+            sms = n > 0 ? n : 1;
+            sm_count.store(sms, std::memory_order_relaxed);
+        }
+        form = (int64_t)a.n_games * pmax <= 8 * (int64_t)sms ? 3 : 2;
+    }
+    if (form == 3) {
+        const int smem = wide_bytes(a.npad_max);
+        static SmemLimit limit;
+        const void* fn = (const void*)k_sample_wide;
+        const int e = limit.raise(&fn, 1, smem);
+        if (e != 0) return e;
+        return launch_chained(k_sample_wide, dim3((unsigned)((int64_t)a.n_games * pmax)), dim3(kWideThreads), smem,
+                              (cudaStream_t)stream, a, pmax);
+    }
     if (form == 2) {
         // a warp per player, as many as fit next to the board (at least one)
         const int fit = (227 * 1024 - 4 * a.npad_max) / sample_player_bytes(a.npad_max);
@@ -352,8 +573,7 @@ int launch_sample(const SArgs& a, int pmax, int form, void* stream) {
         const void* fn = (const void*)k_sample_cta;
         const int e = limit.raise(&fn, 1, smem);
         if (e != 0) return e;
-        k_sample_cta<<<a.n_games, 32 * warps, smem, (cudaStream_t)stream>>>(a);
-        return (int)cudaGetLastError();
+        return launch_chained(k_sample_cta, dim3(a.n_games), dim3(32 * warps), smem, (cudaStream_t)stream, a);
     }
     const int per_warp = sample_warp_bytes(a.npad_max);
     const int wpc = std::max(1, std::min(kWarps, (200 * 1024) / per_warp));
@@ -363,8 +583,7 @@ int launch_sample(const SArgs& a, int pmax, int form, void* stream) {
     const int e = limit.raise(&fn, 1, smem);
     if (e != 0) return e;
     const int blocks = (a.n_games + wpc - 1) / wpc;
-    k_sample<<<blocks, 32 * wpc, smem, (cudaStream_t)stream>>>(a, wpc);
-    return (int)cudaGetLastError();
+    return launch_chained(k_sample, dim3(blocks), dim3(32 * wpc), smem, (cudaStream_t)stream, a, wpc);
 }
 
 }  // namespace gk

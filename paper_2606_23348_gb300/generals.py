@@ -370,7 +370,8 @@ class GeneralsEnv:
 
     def set_sample_form(self, form: int):
         """How sample_actions spreads a game over the GPU: 1 one warp per
-        game, 2 one CTA per game with a warp per player, 0 the default (2)."""
+        game, 2 one CTA per game with a warp per player, 3 one CTA per player
+        with a thread per (own cell, entry), 0 the default (by batch size)."""
         _check(self.lib.gen_set_sample_form(self.h, int(form)), "gen_set_sample_form")
 
     def sample_actions(self, logits, seed: int, actions=None, mask9=None):

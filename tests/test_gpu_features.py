@@ -119,12 +119,25 @@ def test_features_mixed_modes_with_resets(form):
     lockstep(env, orc, fb, ofb, 80, 6, "mixed")
 
 
+@FORMS
 @pytest.mark.parametrize("hist,window", [(1, 512), (16, 1)])
-def test_features_history_lengths(hist, window):
+def test_features_history_lengths(hist, window, form):
     H, W, mode, P, gen, _ = workload("1v1-64x15x15")
-    env, orc, fb, ofb = pair(H[:16], W[:16], mode[:16], P[:16], hist=hist, window=window, seed=1, **gen)
+    env, orc, fb, ofb = pair(H[:16], W[:16], mode[:16], P[:16], hist=hist, window=window, form=form, seed=1, **gen)
     assert fb.channels == 24 + 2 * hist
     lockstep(env, orc, fb, ofb, 30, 3, f"hist {hist}", every=3)
+
+
+@FORMS
+@pytest.mark.parametrize("hist", [7, 16])
+def test_features_large_boards_and_odd_player_counts(form, hist):
+    """64x64 FFA-8 (256 (player, 128-cell) items: several batches per warp in
+    the CTA form, the most staging shared memory allows at hist 16), FFA-3 on
+    40x37 and 3x5 (an odd player count: unaligned bitset regions), and a 1x2
+    board, with truncation resets; every frame compared."""
+    H, W, mode, P = (np.array(v, np.int32) for v in ([64, 40, 3, 1], [64, 37, 5, 2], [2, 2, 2, 0], [8, 3, 3, 2]))
+    env, orc, fb, ofb = pair(H, W, mode, P, hist=hist, window=16, form=form, seed=6, n_cities=3, max_turns=12)
+    lockstep(env, orc, fb, ofb, 30, 5, f"large hist {hist}", every=2)
 
 
 @FORMS

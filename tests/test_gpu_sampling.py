@@ -61,8 +61,9 @@ def pair(H, W, mode, P, **kw):
     return GeneralsEnv(H, W, mode, P, **kw), OracleEnv(H, W, mode, P, **kw)
 
 
-# both spreads of a game over the GPU: one warp per game, one CTA per game
-FORMS = pytest.mark.parametrize("form", [1, 2], ids=["warp", "cta"])
+# the spreads of a game over the GPU: one warp per game, one CTA per game,
+# one CTA per player with a thread per (own cell, entry)
+FORMS = pytest.mark.parametrize("form", [1, 2, 3], ids=["warp", "cta", "wide"])
 
 
 @FORMS
@@ -121,6 +122,42 @@ def test_sampling_edge_shapes(H, W, mode, P, form):
     check_sample(env, orc, logits, 9, f"edge {H}x{W}")
 
 
+@FORMS
+def test_sampling_large_territories(form):
+    """Planted boards where one player owns most of a large board (hundreds of
+    own cells, thousands of legal entries: several rounds of every form's
+    passes, beyond what any form keeps in registers) and the others hold a
+    few cells each; 1v1, 2v2 and FFA-8, armies 0..30, some cells with a
+    single unit (only the pass entry legal)."""
+    import torch
+    shp = [(32, 32, 0, 2), (40, 37, 1, 4), (20, 24, 2, 8), (64, 64, 0, 2)]
+    H, W, mode, P = (np.array([x[i] for x in shp], np.int32) for i in range(4))
+    env, orc = pair(H, W, mode, P, seed=2, n_cities=0)
+    env.set_sample_form(form)
+    rng = np.random.default_rng(17)
+    n = int(env.layout.state_cells)
+    army, owner, terrain = np.zeros(n, np.int16), np.full(n, -1, np.int8), np.zeros(n, np.int8)
+    sc = np.zeros((env.G, 8), np.uint32)
+    for g in range(env.G):
+        N, Pg, o = int(env.N[g]), int(P[g]), int(env.state_off[g])
+        t = np.where(rng.random(N) < 0.08, 1, 0).astype(np.int8)  # mountains
+        ow = np.where(rng.random(N) < 0.75, 0, rng.integers(-1, Pg, N)).astype(np.int8)
+        ow[t == 1] = -1
+        a = np.where(ow >= 0, rng.integers(0, 31, N), 0).astype(np.int16)
+        a[(ow >= 0) & (rng.random(N) < 0.2)] = 1
+        free = np.flatnonzero(t == 0)
+        for q, c in enumerate(rng.choice(free, Pg, replace=False)):  # one general per player
+            ow[c], t[c], a[c] = q, 3, 5
+        army[o:o + N], owner[o:o + N], terrain[o:o + N] = a, ow, t
+        sc[g, 0], sc[g, 1], sc[g, 3] = 60, 4, (1 << Pg) - 1
+        orc.set_game(g, a, ow, t, turn=60, frame=4)
+    env.write_state(army, owner, terrain, sc)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    for s in range(3):
+        logits = torch.randn(int(env.layout.plane_cells) * 9, generator=gen, device="cuda") * (1.0 + 4 * s)
+        check_sample(env, orc, logits, 40 + s, f"territories seed {s}")
+
+
 def test_expand_mask_only_and_errors():
     import torch
     from paper_2606_23348_gb300.generals import GeneralsError
@@ -132,13 +169,13 @@ def test_expand_mask_only_and_errors():
     env.sample_actions(logits, 1, None, m9b)
     torch.cuda.synchronize()
     assert torch.equal(m9, m9b)
-    for form in (1, 2):  # the mask of either spread, and the actions with it
+    for form in (1, 2, 3):  # the mask of every spread, and the actions with it
         env.set_sample_form(form)
         m9c, a1 = torch.empty_like(m9), env.sample_actions(logits, 1)
         a2 = env.sample_actions(logits, 1, None, m9c)
         torch.cuda.synchronize()
         assert torch.equal(m9, m9c) and torch.equal(a1, a2)
-    for form in (-1, 3):
+    for form in (-1, 4):
         with pytest.raises(GeneralsError):
             env.set_sample_form(form)
     assert env.lib.gen_sample_actions(env.h, None, 0, None, None, None) != 0  # nothing to compute
