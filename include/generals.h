@@ -534,10 +534,11 @@ int gen_features_build_ex(gen_features *f, float *d_out, int32_t *d_series, void
 int gen_features_autotune(gen_features *f, float *d_out, int steps, int *form_out);
 
 /* Tuning call, no counterpart in the paper.  How the builder spreads a
- * game over the GPU (the bytes written are the same): 1 = one warp per game, players in turn; 2 = one CTA per game, its
- * warps sharing the (player, 128-cell chunk) items, for batches too small to
- * fill the GPU one warp per game; 0 (default) = 2 while the batch has fewer
- * games than 16 x the SM count, else 1.  GEN_ERR_BAD_ARG outside 0..2. */
+ * game over the GPU (the bytes written are the same): 1 = one warp per
+ * game, players in turn; 2 = one CTA per (game, player), its warps sharing
+ * the player's 128-cell chunks, for batches too small to fill the GPU one
+ * warp per game; 0 (default) = 2 while games x the most players per game is
+ * at most 88 x the SM count, else 1.  GEN_ERR_BAD_ARG outside 0..2. */
 int gen_features_set_form(gen_features *f, int form);
 
 /* Free a builder's memory (App. A feature memory). */

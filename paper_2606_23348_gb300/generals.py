@@ -488,7 +488,8 @@ class Features:
 
     def set_form(self, form: int):
         """Spread of a game over the GPU: FORM_WARP (one warp per game),
-        FORM_CTA (one CTA per game, for small batches) or FORM_AUTO."""
+        FORM_CTA (one CTA per game and player, for small batches) or
+        FORM_AUTO."""
         _check(self.lib.gen_features_set_form(self.h, int(form)), "gen_features_set_form")
 
     def player_series(self, series, g: int, p: int):
