@@ -43,21 +43,21 @@ MAP_SEED = 1
 # of one launch); the sampler on 16,384 games, scaled by the games it
 # processes (traffic grows in proportion).  Writes still dirty in the L2
 # when a launch ends are not in its DRAM count.
-NCU_TRAFFIC = {"kernel_sha1": "9c26d56607a0", "bytes_per_launch": 153821952.0 + 556117248.0,
-               "warp_inst_per_launch": 118072429.0, "captured": "65,536 games (the bench's own launch)",
+NCU_TRAFFIC = {"kernel_sha1": "965c260a0292", "bytes_per_launch": 153821184.0 + 555878912.0,
+               "warp_inst_per_launch": 118105197.0, "captured": "65,536 games (the bench's own launch)",
                "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
-SAMPLE_NCU = {"kernel_sha1": "1229b630d960", "bytes_per_launch": 4 * (133582848.0 + 4239616.0),
-              "warp_inst_per_launch": 4 * 52820402.0, "captured": "16,384 games (x4)", "games": 65536}
+SAMPLE_NCU = {"kernel_sha1": "e9c5772d6a07", "bytes_per_launch": 4 * (133579520.0 + 3933952.0),
+              "warp_inst_per_launch": 4 * 52885938.0, "captured": "16,384 games (x4)", "games": 65536}
 # DRAM bytes of one frame of the ragged and mixed workloads, each in the form
 # that the default batch rule picks (per-bucket launches for the four ragged
 # buckets, summed; one work-list launch for the fifteen mixed buckets)
-ROLLOUT_NCU = {"kernel_sha1": "9c26d56607a0",
+ROLLOUT_NCU = {"kernel_sha1": "965c260a0292",
                "1v1-131072-ragged15to30": {"form": "plain_buckets", "bytes_per_frame":
-                                           (30465536.0 + 145797888.0 + 139028480.0 + 5468672.0)
-                                           + (51076864.0 + 456136960.0 + 427234304.0 + 3328.0)},
-               "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128563712.0 + 867591680.0}}
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "0becd141ea17", "bytes_per_launch": 8 * 1911037952.0,
+                                           (30472448.0 + 145816832.0 + 139028224.0 + 5467648.0)
+                                           + (51024128.0 + 455904000.0 + 426976000.0 + 4096.0)},
+               "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128558080.0 + 867632128.0}}
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "dd4db543f9ed", "bytes_per_launch": 8 * (356423168.0 + 1554848768.0),
                        "captured": "8,192 games (x8)", "games": 65536}
 
 
@@ -974,6 +974,105 @@ def run_batch_sweep(args, rank, world, local):
             "rows": rows, "gpu_launches": None, "clocks": clk.summary()}), flush=True)
 
 
+def _graph_us(fn, T: int, stream) -> float:
+    """Device time per call of `fn`, T calls captured as one CUDA graph and
+    replayed (best of three), so that host launch cost does not enter."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(T):
+            fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e3 / T)
+    del g
+    return best
+
+
+def run_forms_sweep(args, rank, world, local):
+    """Per-launch device time of every sampler form (warp per game, CTA per
+    game, CTA per player) and both feature-builder forms (warp per game, CTA
+    per player) on the default game shape (1v1 24x24) from 512 to 65,536
+    games, at mid-game (256 frames of the benchmark policy), each form
+    replayed as a CUDA graph of launches; and, at the self-play batch (512
+    games), the sampler, step and feature launches alone and as a frame.
+    Feature builds are timed as (step + build) - step, every build the first
+    of its frame (the memory fold, the history ring full)."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv
+    from paper_2606_23348_gb300.workloads import shard, workload
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    rows = []
+    frame = {}
+    with ClockSampler(local) as clk:
+        for G in (512, 1024, 2048, 4096, 8192, 16384, 65536):
+            T = 64 if G <= 8192 else 16
+            H, W, mode, P, gen, _ = workload(WORKLOAD, G=G)
+            env = GeneralsEnv(H, W, mode, P, seed=MAP_SEED, game_id_base=shard(G, rank), **gen)
+            fb = env.features(7, 512)
+            out, acts = env.new_outputs(), env.new_actions()
+            x, tok = fb.new_output(), fb.new_series()
+            env.policy(POLICY_SEED, acts)
+            for f in range(STEP_PREROLL):
+                env.step_policy(acts, out, POLICY_SEED, acts)
+                if f >= STEP_PREROLL - 16:  # the feature history ring full
+                    fb.build(x, tok)
+            gen_ = torch.Generator(device="cuda").manual_seed(99 + rank)
+            logits = torch.randn(int(env.layout.plane_cells) * 9, generator=gen_, device="cuda") * 2.0
+            sampled = env.new_actions()
+            fb.build(x, tok)
+            torch.cuda.synchronize()
+            row = {"games": G, "sampler_us": {}, "features_us": {}}
+            for form, name in ((1, "warp_per_game"), (2, "cta_per_game"), (3, "cta_per_player")):
+                env.set_sample_form(form)
+                row["sampler_us"][name] = _graph_us(lambda: env.sample_actions(logits, POLICY_SEED, sampled), T,
+                                                    stream)
+            # a build folds the frame into the players' memory once per frame:
+            # timed as (step + build) - step, so that every build is a frame's first
+            step_us = _graph_us(lambda: env.step_policy(acts, out, POLICY_SEED, acts), T, stream)
+            for form, name in ((1, "warp_per_game"), (2, "cta_per_player")):
+                fb.set_form(form)
+                row["features_us"][name] = _graph_us(lambda: (env.step_policy(acts, out, POLICY_SEED, acts),
+                                                              fb.build(x, tok)), T, stream) - step_us
+            env.set_sample_form(0)
+            fb.set_form(0)
+            if G == 512:
+                frame = {"sample_us": _graph_us(lambda: env.sample_actions(logits, POLICY_SEED, sampled), T, stream),
+                         "step_us": _graph_us(lambda: env.step(sampled, out), T, stream)}
+                frame["features_us"] = _graph_us(lambda: (env.step(sampled, out), fb.build(x, tok)), T,
+                                                 stream) - frame["step_us"]
+                frame["frame_us"] = _graph_us(lambda: (env.sample_actions(logits, POLICY_SEED, sampled),
+                                                       env.step(sampled, out), fb.build(x, tok)), T, stream)
+            rows.append(row)
+            del fb, env, out, x, tok, logits
+            torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "us per launch by form and batch size (sampler, feature builder)", "value": None,
+            "unit": "us", "n_gpus": world, "higher_is_better": False, "vs_baseline": None,
+            "dtype": "f32 logits and features, int16 state",
+            "data": "synthetic (seeded counter-hash maps, N(0, 2) logits, 256 policy frames)",
+            "config": {"workload": "forms-512to65536x24x24", "hist": 7, "temporal_window": 512,
+                       "timing": "CUDA graph of 64 launches (16 from 16,384 games), best of 3; features as "
+                                 "(step + build) - step"},
+            "rows": rows, "selfplay_512_frame_parts": frame, "gpu_launches": None,
+            "clocks": clk.summary()}), flush=True)
+
+
 def run_generator(args, rank, world, local):
     """Map generation throughput: gen_reset of every game of the default
     workload's shapes, for each generator option set."""
@@ -1077,6 +1176,8 @@ def main():
             run_selfplay(args, rank, world, local)
         elif args.workload == "sweep-1024to65536x24x24":
             run_batch_sweep(args, rank, world, local)
+        elif args.workload == "forms-512to65536x24x24":
+            run_forms_sweep(args, rank, world, local)
         else:
             run_rollout_workload(args, rank, world, local)
     if world > 1:

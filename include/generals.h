@@ -538,7 +538,7 @@ int gen_features_autotune(gen_features *f, float *d_out, int steps, int *form_ou
  * game, players in turn; 2 = one CTA per (game, player), its warps sharing
  * the player's 128-cell chunks, for batches too small to fill the GPU one
  * warp per game; 0 (default) = 2 while games x the most players per game is
- * at most 88 x the SM count, else 1.  GEN_ERR_BAD_ARG outside 0..2. */
+ * at most 56 x the SM count, else 1.  GEN_ERR_BAD_ARG outside 0..2. */
 int gen_features_set_form(gen_features *f, int form);
 
 /* Free a builder's memory (App. A feature memory). */

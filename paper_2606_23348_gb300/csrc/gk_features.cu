@@ -680,10 +680,11 @@ int launch_features(const FArgs& f, int pmax, int form, void* stream) {
         sms = n > 0 ? n : 1;
         sm_count.store(sms, std::memory_order_relaxed);
     }
-    // the CTA form while the batch has at most 88 x the SM count players
-    // (measured on 24x24 1v1, per build: 512 games 20.5 against 67.6 us,
-    // 6,144 games 252 against 278 us, 8,192 games 336 against 316 us)
-    if (form == 0) form = (int64_t)f.n_games * pmax <= 88 * (int64_t)sms ? 2 : 1;
+    // the CTA form while the batch has at most 56 x the SM count players
+    // (measured on 24x24 1v1, each build the first of its frame: 512 games
+    // 28.5 against 69.3 us, 4,096 games 184.8 against 186.4 us, 8,192 games
+    // 360 against 335 us)
+    if (form == 0) form = (int64_t)f.n_games * pmax <= 56 * (int64_t)sms ? 2 : 1;
     if (form == 2) {
         // a CTA per (game, player) with a warp per kItemsPerBatch chunks, as
         // many as the staging leaves room for in shared memory
