@@ -57,7 +57,7 @@ ROLLOUT_NCU = {"kernel_sha1": "965c260a0292",
                                            (30472448.0 + 145816832.0 + 139028224.0 + 5467648.0)
                                            + (51024128.0 + 455904000.0 + 426976000.0 + 4096.0)},
                "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128558080.0 + 867632128.0}}
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "dd4db543f9ed", "bytes_per_launch": 8 * (356423168.0 + 1554848768.0),
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "7604d33a04ea", "bytes_per_launch": 8 * (356319488.0 + 1554689024.0),
                        "captured": "8,192 games (x8)", "games": 65536}
 
 
