@@ -431,7 +431,7 @@ int gen_server_simulate(const gen_params *p, const gen_sim_config *cfg, gen_serv
  * the step that will consume it, p); a player without a legal entry gets 0
  * (pass).  The same logits and seed give the same actions on every device.
  * d_actions: player_slots int32 (the layout gen_step reads).  d_mask9
- * (optional, 4-byte aligned): the expanded legal mask, 9 * Npad_g bytes per
+ * (optional, 16-byte aligned): the expanded legal mask, 9 * Npad_g bytes per
  * player plane at q * 9, 1 = legal.  With d_logits and d_actions NULL only
  * the mask is written.  Asynchronous on `stream`; order it after the step
  * that produced the state.  GEN_ERR_BAD_ARG for NULL env, inconsistent

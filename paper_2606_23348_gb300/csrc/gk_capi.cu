@@ -202,6 +202,8 @@ int check_outputs(const gen_outputs* o) {
     for (int i = 0; i < 8; ++i) {
         if (!ptrs[i]) return fail(GEN_ERR_BAD_ARG, "output field %d is NULL", i);
         if (i < 5 && !aligned16(ptrs[i])) return fail(GEN_ERR_BAD_ARG, "output plane %d not 16-byte aligned", i);
+        if ((i == 5 || i == 6) && (reinterpret_cast<uintptr_t>(ptrs[i]) & 3u))  // float / int32 stores
+            return fail(GEN_ERR_BAD_ARG, "output field %d not 4-byte aligned", i);
     }
     return GEN_OK;
 }
@@ -1402,8 +1404,8 @@ int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t
     if (!d_logits && d_actions) return fail(GEN_ERR_BAD_ARG, "actions need logits");
     if (d_logits && !d_actions) return fail(GEN_ERR_BAD_ARG, "logits need an actions buffer");
     if (!d_logits && !d_mask9) return fail(GEN_ERR_BAD_ARG, "nothing to compute");
-    if ((reinterpret_cast<uintptr_t>(d_logits) & 15u) || (reinterpret_cast<uintptr_t>(d_mask9) & 3u))
-        return fail(GEN_ERR_BAD_ARG, "logits must be 16-byte and mask9 4-byte aligned");
+    if (!aligned16(d_logits) || !aligned16(d_mask9))  // the mask rows are written 16 bytes at a time
+        return fail(GEN_ERR_BAD_ARG, "logits and mask9 must be 16-byte aligned");
     gk::SArgs a{};
     a.info = e->d_info;
     a.army = e->d_army;

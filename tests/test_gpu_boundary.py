@@ -148,3 +148,25 @@ def test_load_rejects_bad_blobs():
     after = env.read_state()
     for x, y in zip(before, after):
         np.testing.assert_array_equal(x, y)  # a refused blob changes nothing
+
+
+def test_misaligned_outputs_are_refused_on_the_host():
+    """Output planes are written 16 bytes at a time and the reward and
+    scoreboard one 4-byte word at a time: pointers that break either are
+    refused before any launch, and the environment stays usable."""
+    import torch
+
+    from paper_2606_23348_gb300.generals import GeneralsEnv, GeneralsError
+    H, W, mode, P = _batch(seed=24, G=8)
+    env = GeneralsEnv(H, W, mode, P, seed=1, **KW)
+    acts = env.new_actions()
+    spare = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    for field, offset in (("obs_army", 8), ("mask", 4), ("reward", 2), ("scoreboard", 1)):
+        out = env.new_outputs()
+        setattr(out.struct, field, spare.data_ptr() + offset)
+        with pytest.raises(GeneralsError, match="aligned"):
+            env.step(acts, out)
+    out = env.new_outputs()
+    env.step(acts, out)  # still usable
+    torch.cuda.synchronize()
+    assert env.read_state()[3][:, 7].max() == 0

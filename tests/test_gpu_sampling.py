@@ -181,6 +181,9 @@ def test_expand_mask_only_and_errors():
     assert env.lib.gen_sample_actions(env.h, None, 0, None, None, None) != 0  # nothing to compute
     with pytest.raises(GeneralsError):
         env.sample_actions(logits[1:], 1)  # misaligned logits
+    m9x = torch.empty(int(env.layout.plane_cells) * 9 + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(GeneralsError):
+        env.sample_actions(logits, 1, None, m9x[4:])  # a mask 4 but not 16 bytes aligned: refused on the host
 
 
 def test_sampling_full_size_24x24_65536_sampled():
