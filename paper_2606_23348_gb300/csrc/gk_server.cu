@@ -806,7 +806,10 @@ int gen_server_step(gen_server* sv, int session, const int32_t* h_actions, const
                     int32_t* h_next_actions, double* latency_ms) {
     if (!sv || !h_actions) return sfail(GEN_ERR_BAD_ARG, "NULL argument");
     const double t_submit = now_ms();
-    Session s;
+    struct {
+        int64_t g0, p0, s0, planes, slots;
+        int n;
+    } s;  // the session's ranges only: its game tables stay where they are
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         auto it = sv->sessions.find(session);
@@ -814,7 +817,8 @@ int gen_server_step(gen_server* sv, int session, const int32_t* h_actions, const
         if (it->second.busy) return sfail(GEN_ERR_STATE, "session %d already has a step in flight", session);
         if (!sv->fatal.empty()) return sfail(GEN_ERR_STATE, "server failed: %s", sv->fatal.c_str());
         it->second.busy = true;
-        s = it->second;
+        const Session& q = it->second;
+        s = {q.g0, q.p0, q.s0, q.planes, q.slots, q.n};
     }
     // actions into the session's slots (mapped host memory)
     memcpy(sv->act_host + s.s0, h_actions, sizeof(int32_t) * (size_t)s.slots);
