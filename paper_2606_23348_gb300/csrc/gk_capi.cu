@@ -46,6 +46,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr int kMaxSmemPerCta = 227 * 1024;
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
 // A group of games of similar size launched together with its own
 // shared-memory carve and launch shape.
@@ -700,6 +701,7 @@ int gen_step_policy(gen_env* e, const int32_t* d_actions, const gen_outputs* out
                     int32_t* d_next_actions, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
+    if (!aligned4(d_actions) || !aligned4(d_next_actions)) return fail(GEN_ERR_BAD_ARG, "actions not 4-byte aligned");
     gen_outputs res;
     int rc = resolve_outputs(e, out_arg, &res);
     if (rc) return rc;
@@ -721,6 +723,7 @@ int gen_step(gen_env* e, const int32_t* d_actions, const gen_outputs* out, void*
 int gen_policy(gen_env* e, uint64_t policy_seed, int32_t* d_actions, void* stream) {
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
+    if (!aligned4(d_actions)) return fail(GEN_ERR_BAD_ARG, "actions not 4-byte aligned");
     return launch_buckets(e, gk::OP_POLICY,
                           [&](KArgs& a) {
                               a.next_actions = d_actions;
@@ -734,6 +737,7 @@ int gen_rollout(gen_env* e, int K, uint64_t policy_seed, int32_t* d_actions, con
     if (!e) return fail(GEN_ERR_BAD_ARG, "env is NULL");
     if (K < 1) return fail(GEN_ERR_BAD_ARG, "K = %d < 1", K);
     if (!d_actions) return fail(GEN_ERR_BAD_ARG, "actions is NULL");
+    if (!aligned4(d_actions) || !aligned4(d_action_log)) return fail(GEN_ERR_BAD_ARG, "actions not 4-byte aligned");
     // K frames of outputs: the environment's own buffers hold one, so every field is the caller's
     int rc = check_outputs(out);
     if (rc) return rc;
@@ -1404,6 +1408,7 @@ int gen_sample_actions(gen_env* e, const float* d_logits, uint64_t seed, int32_t
     if (!d_logits && d_actions) return fail(GEN_ERR_BAD_ARG, "actions need logits");
     if (d_logits && !d_actions) return fail(GEN_ERR_BAD_ARG, "logits need an actions buffer");
     if (!d_logits && !d_mask9) return fail(GEN_ERR_BAD_ARG, "nothing to compute");
+    if (!aligned4(d_actions)) return fail(GEN_ERR_BAD_ARG, "actions not 4-byte aligned");
     if (!aligned16(d_logits) || !aligned16(d_mask9))  // the mask rows are written 16 bytes at a time
         return fail(GEN_ERR_BAD_ARG, "logits and mask9 must be 16-byte aligned");
     gk::SArgs a{};

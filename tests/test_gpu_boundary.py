@@ -166,7 +166,11 @@ def test_misaligned_outputs_are_refused_on_the_host():
         setattr(out.struct, field, spare.data_ptr() + offset)
         with pytest.raises(GeneralsError, match="aligned"):
             env.step(acts, out)
+    import ctypes as C
     out = env.new_outputs()
+    odd = C.c_void_p(acts.data_ptr() + 2)
+    assert env.lib.gen_step(env.h, odd, C.byref(out.struct), None) != 0  # actions read as int32
+    assert env.lib.gen_policy(env.h, 1, odd, None) != 0
     env.step(acts, out)  # still usable
     torch.cuda.synchronize()
     assert env.read_state()[3][:, 7].max() == 0
