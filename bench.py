@@ -47,8 +47,8 @@ NCU_TRAFFIC = {"kernel_sha1": "965c260a0292", "bytes_per_launch": 153821184.0 + 
                "warp_inst_per_launch": 118105197.0, "captured": "65,536 games (the bench's own launch)",
                "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
-SAMPLE_NCU = {"kernel_sha1": "e9c5772d6a07", "bytes_per_launch": 4 * (133579520.0 + 3933952.0),
-              "warp_inst_per_launch": 4 * 52885938.0, "captured": "16,384 games (x4)", "games": 65536}
+SAMPLE_NCU = {"kernel_sha1": "4dcce83afa2e", "bytes_per_launch": 4 * (133577216.0 + 3892480.0),
+              "warp_inst_per_launch": 4 * 50199088.0, "captured": "16,384 games (x4)", "games": 65536}
 # DRAM bytes of one frame of the ragged and mixed workloads, each in the form
 # that the default batch rule picks (per-bucket launches for the four ragged
 # buckets, summed; one work-list launch for the fifteen mixed buckets)

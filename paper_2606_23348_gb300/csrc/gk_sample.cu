@@ -77,6 +77,41 @@ __device__ __forceinline__ uint32_t weight_shift(float l, float m) {
     return n >= 0 ? sig << 1 : sig >> (-(n + 1));
 }
 
+// two weights at once: the same single-precision operations as
+// weight_shift, issued as packed pairs (each half an IEEE round-to-nearest
+// operation of its own, so the results are bit for bit those of two calls)
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+    return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ float lo2(uint64_t x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float hi2(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t weight_from(float t, float nf, float p) {
+    if (t < -25.0f) return 0u;
+    const int n = (int)nf;
+    const uint32_t sig = (__float_as_uint(p) & 0x7FFFFFu) | 0x800000u;
+    return n >= 0 ? sig << 1 : sig >> (-(n + 1));
+}
+__device__ __forceinline__ uint2 weight_shift2(float l0, float l1, float m) {
+    const float t0 = __fmul_rn(__fsub_rn(l0, m), 1.4426950408889634f);
+    const float t1 = __fmul_rn(__fsub_rn(l1, m), 1.4426950408889634f);
+    const float n0 = floorf(t0), n1 = floorf(t1);
+    const uint64_t f = pack2(__fsub_rn(t0, n0), __fsub_rn(t1, n1));
+    uint64_t p = pack2(1.5252733804059838e-05f, 1.5252733804059838e-05f);
+    p = fma2(p, f, pack2(0.00015403530393381606f, 0.00015403530393381606f));
+    p = fma2(p, f, pack2(0.0013333558146428441f, 0.0013333558146428441f));
+    p = fma2(p, f, pack2(0.009618129107628477f, 0.009618129107628477f));
+    p = fma2(p, f, pack2(0.055504108664821576f, 0.055504108664821576f));
+    p = fma2(p, f, pack2(0.2402265069591007f, 0.2402265069591007f));
+    p = fma2(p, f, pack2(0.6931471805599453f, 0.6931471805599453f));
+    p = fma2(p, f, pack2(1.0f, 1.0f));
+    return make_uint2(weight_from(t0, n0, lo2(p)), weight_from(t1, n1, hi2(p)));
+}
+
 // legal entries of one cell for player p as bits 0..8 (entry k of the cell)
 __device__ __forceinline__ uint32_t legal9(int own_p, int army, uint32_t terrain, bool moves) {
     if (!own_p) return 0u;
@@ -241,8 +276,12 @@ __device__ __forceinline__ int32_t sample_player(const SArgs& a, const GameInfo&
                 load9(v, lg + 9 * c);
             }
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                if ((lb >> k) & 1u) wsum += weight_shift(v[k], m);
+            for (int k = 0; k < 8; k += 2) {
+                const uint2 w2 = weight_shift2(v[k], v[k + 1], m);
+                wsum += ((lb >> k) & 1u) ? w2.x : 0u;
+                wsum += ((lb >> (k + 1)) & 1u) ? w2.y : 0u;
+            }
+            if ((lb >> 8) & 1u) wsum += weight_shift(v[8], m);
             s_w[i] = wsum;
         }
         const uint64_t rs = warp_sum64(wsum);
