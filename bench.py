@@ -47,7 +47,7 @@ NCU_TRAFFIC = {"kernel_sha1": "965c260a0292", "bytes_per_launch": 153821184.0 + 
                "warp_inst_per_launch": 118105197.0, "captured": "65,536 games (the bench's own launch)",
                "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
-SAMPLE_NCU = {"kernel_sha1": "4dcce83afa2e", "bytes_per_launch": 4 * (133577216.0 + 3892480.0),
+SAMPLE_NCU = {"kernel_sha1": "515d4f95a9c0", "bytes_per_launch": 4 * (133577216.0 + 3892480.0),
               "warp_inst_per_launch": 4 * 50199088.0, "captured": "16,384 games (x4)", "games": 65536}
 # DRAM bytes of one frame of the ragged and mixed workloads, each in the form
 # that the default batch rule picks (per-bucket launches for the four ragged
@@ -57,7 +57,7 @@ ROLLOUT_NCU = {"kernel_sha1": "965c260a0292",
                                            (30472448.0 + 145816832.0 + 139028224.0 + 5467648.0)
                                            + (51024128.0 + 455904000.0 + 426976000.0 + 4096.0)},
                "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128558080.0 + 867632128.0}}
-FEATURE_NCU_TRAFFIC = {"kernel_sha1": "7604d33a04ea", "bytes_per_launch": 8 * (356319488.0 + 1554689024.0),
+FEATURE_NCU_TRAFFIC = {"kernel_sha1": "8af7d765f60a", "bytes_per_launch": 8 * (356319488.0 + 1554689024.0),
                        "captured": "8,192 games (x8)", "games": 65536}
 
 

@@ -20,9 +20,11 @@
 // cells, four consecutive cells per lane, that reads the memory, writes the
 // 24 + 2K channels with 16-byte streaming stores and writes the folded memory
 // back.  k_features_cta, for batches too small to fill the GPU one warp per
-// game: one CTA per game, warp q builds player q's bitset, then the warps
-// share the (player, 128-cell chunk) items; every warp reads the players'
-// memory headers before a CTA barrier, after which they are written.
+// game: one CTA per (game, player); each warp stages the memory and history
+// planes of two of the player's 128-cell chunks with cp.async while one warp
+// builds the player's bitset and others the scoreboard, then writes those
+// chunks; the player's memory header is read before the CTA's last barrier
+// and written after it.
 // HBM-bound: per player and cell it moves 4 (24 + 2K) bytes of output,
 // 2 * 2K bytes of history and 15 bytes of memory.
 #include <cuda_runtime.h>

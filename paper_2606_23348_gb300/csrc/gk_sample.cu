@@ -17,15 +17,18 @@
 // single-precision operation with round-to-nearest written out explicitly
 // (no contraction), so the weights are bit-reproducible.
 //
-// One CTA per game with a warp per player (k_sample_cta, the default), or one
-// warp per game with the players in turn (k_sample).  The board is staged in
+// One CTA per game with a warp per player (k_sample_cta), one warp per game
+// with the players in turn (k_sample), or, for small batches, one CTA per
+// player with a thread per (own cell, entry) pair (k_sample_wide, described
+// where it is defined).  The board is staged in
 // shared memory (every 16-byte copy in flight at once); legal entries lie
 // only on the player's own cells, so the warp first lists those cells in
 // index order (a ballot per 32 cells, no global load) and the passes run over
 // the list, 32 own cells at a time: pass 1 derives each cell's nine legal
 // bits and takes the maximum; pass 2 (logits held in registers for the first
 // 64 own cells, read again from L1/L2 beyond) sums each cell's weights,
-// computing every exponential once, and keeps the sums per cell and per 32
+// computing every exponential once (two entries per packed FMA chain), and
+// keeps the sums per cell and per 32
 // cells; pass 3 finds the group, the cell and (nine lanes weighing the cell's
 // entries at once) the entry where the running sum first exceeds r.  Only the
 // own cells' logits are read (36 bytes each).  The expanded mask, when asked
