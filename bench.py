@@ -335,21 +335,28 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     t_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
         t_all[0].record(stream)
-        for k in range(K):
-            ev[k][0].record(stream)
+        for k in range(K):  # back to back: an event between two launches would break their chaining
             env.step_policy(acts, out, POLICY_SEED, acts)
-            ev[k][1].record(stream)
         t_all[1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
     elapsed_ms = t_all[0].elapsed_time(t_all[1])
-    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    # the roofline's launch duration: the timed region's average per launch
+    # (its launches run back to back, chained); beside it, the duration of
+    # one launch bracketed by events of its own, measured right after
+    launch_ms = elapsed_ms / K
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(min(K, 20))]
+    for a, b in ev:
+        a.record(stream)
+        env.step_policy(acts, out, POLICY_SEED, acts)
+        b.record(stream)
+    torch.cuda.synchronize()
+    isolated_launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     frames_total = sum_over_ranks(float(G * K), world)
     value = frames_total / (elapsed_ms * 1e-3)
@@ -374,6 +381,21 @@ def run_ours(args, rank, world, local):
         resident = {"frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms, "rollout_frames": Kr,
                     "own_bytes_per_frame": rb, "hbm_frac_own_bytes": rb / (ms * 1e-3) / 1e9 / peaks()[0]}
         del outK
+
+    # the configuration's full episode length: 2,000 more per-frame launches
+    # of the same environment, timed as one region
+    full = None
+    if not args.no_resident and world == 1:
+        n_full = 2000
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(n_full):
+            env.step_policy(acts, out, POLICY_SEED, acts)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms = f0.elapsed_time(f1) / n_full
+        full = {"frames": n_full, "frames_per_s": G / (ms * 1e-3), "ms_per_frame": ms,
+                "hbm_frac": algorithmic_bytes(env) / (ms * 1e-3) / 1e9 / peaks()[0]}
 
     # e2e: the same step through the host-buffer entry point, copies timed
     e2e = None
@@ -438,11 +460,13 @@ def run_ours(args, rank, world, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "own_copy_kernel_gbps": own_peak, "algorithmic_bytes_per_launch": nbytes,
-                         "launch_ms": launch_ms, "kernel": "k_generals (fused step + policy)"},
+                         "launch_ms": launch_ms, "launch_ms_source": "timed region / K (launches back to back)",
+                         "isolated_launch_ms": isolated_launch_ms, "kernel": "k_generals (fused step + policy)"},
             "issue_roofline": issue_roofline(launch_ms, G, clk),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "resident_rollout_form": resident,
+            "full_length_2000_frames": full,
             "configs": configs,
             "gpu_launches": K,
             "clocks": clk.summary(),
@@ -1131,7 +1155,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-copy-peak", action="store_true")
-    ap.add_argument("--no-resident", action="store_true", help="skip the resident-rollout figure")
+    ap.add_argument("--no-resident", action="store_true",
+                    help="skip the resident-rollout and full-length (2,000 frames) figures")
     ap.add_argument("--workload", default=WORKLOAD, help="workload name (paper_2606_23348_gb300.workloads)")
     ap.add_argument("--games", type=int, default=0,
                     help="fewer games than the workload (profiling captures; 0 = the workload's count)")
