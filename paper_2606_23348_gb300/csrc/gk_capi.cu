@@ -469,7 +469,9 @@ int build_worklist(gen_env* e) {
     }
     if (!e->d_geoms) {
         CUDA_TRY(dev_alloc(e, &e->d_geoms, sizeof(gk::BucketGeom) * nb), "cudaMalloc bucket geometry");
-        CUDA_TRY(dev_alloc(e, &e->d_counter, sizeof(int32_t)), "cudaMalloc work counter");
+        CUDA_TRY(dev_alloc(e, &e->d_counter, 2 * sizeof(int32_t)), "cudaMalloc work counters");
+        const int32_t zero[2] = {0, 0};  // afterwards each work-list launch leaves them zeroed
+        CUDA_TRY(cudaMemcpy(e->d_counter, zero, sizeof(zero), cudaMemcpyHostToDevice), "zero work counters");
     }
     CUDA_TRY(cudaMemcpy(e->d_geoms, geoms.data(), sizeof(gk::BucketGeom) * nb, cudaMemcpyHostToDevice),
              "upload bucket geometry");

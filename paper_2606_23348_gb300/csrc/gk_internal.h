@@ -221,7 +221,7 @@ struct WArgs {
     int32_t n_items;
     const BucketGeom* geoms;
     const int32_t* order;
-    int32_t* counter;  // next item; zeroed by launch_worklist before the kernel
+    int32_t* counter;  // [0] next item, [1] CTAs done; the last CTA done zeroes both (zero when allocated)
 };
 // Packed geometry word of a bucket (as the kernels unpack it).
 uint32_t bucket_geom(int npad_max, int nw_stride, int pmax, bool narrow);

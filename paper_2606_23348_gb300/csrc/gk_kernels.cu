@@ -1490,7 +1490,20 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : 4) k_worklist(const KArgs a, 
         if (threadIdx.x == 0) s_item = atomicAdd(w.counter, 1);
         __syncthreads();
         const int it = s_item;
-        if (it >= w.n_items) return;  // the same for every thread of the CTA
+        if (it >= w.n_items) {  // the same for every thread of the CTA
+            // the last CTA to run out zeroes the counters for the next launch:
+            // every CTA has drawn its last index by then, and a chained launch
+            // reads them only after this grid has completed
+            if (threadIdx.x == 0) {
+                __threadfence();  // this CTA's last draw is ordered before its exit count
+                if (atomicAdd(w.counter + 1, 1) == (int)gridDim.x - 1) {
+                    __threadfence();  // and every other CTA's before these stores
+                    w.counter[0] = 0;
+                    w.counter[1] = 0;
+                }
+            }
+            return;
+        }
         const WorkItem item = w.items[it];
         const BucketGeom bg = w.geoms[item.bucket];
         if (bg.lw == 16) {
@@ -1580,9 +1593,7 @@ int worklist_shape(bool multi, int* cta_smem, int* ctas) {
 }
 
 int launch_worklist(const KArgs& a, const WArgs& w, int cta_smem, int ctas, void* stream) {
-    const cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(w.counter, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return (int)e;
+    const cudaStream_t st = (cudaStream_t)stream;  // the counters arrive zeroed (see k_worklist)
     const bool multi = a.frames > 1 || a.action_log;
     const int grid = ctas < w.n_items ? ctas : w.n_items;
     if (grid <= 0) return 0;

@@ -619,7 +619,11 @@ int gen_server_create(gen_server** out, const gen_params* p, const gen_server_co
         if (ce == cudaSuccess) ce = cudaHostAlloc(&t.h_list, sizeof(int32_t) * G, cudaHostAllocPortable);
         if (ce == cudaSuccess) ce = cudaMalloc(&t.d_items, sizeof(gk::WorkItem) * G);
         if (ce == cudaSuccess) ce = cudaHostAlloc(&t.h_items, sizeof(gk::WorkItem) * G, cudaHostAllocPortable);
-        if (ce == cudaSuccess) ce = cudaMalloc(&t.d_counter, sizeof(int32_t));
+        if (ce == cudaSuccess) ce = cudaMalloc(&t.d_counter, 2 * sizeof(int32_t));
+        if (ce == cudaSuccess) {  // afterwards each work-list launch leaves them zeroed
+            const int32_t zero[2] = {0, 0};
+            ce = cudaMemcpy(t.d_counter, zero, sizeof(zero), cudaMemcpyHostToDevice);
+        }
         for (int i = 0; i < 24 && ce == cudaSuccess; ++i) {  // one per size class
             cudaStream_t s;
             cudaEvent_t v;
