@@ -43,7 +43,7 @@ MAP_SEED = 1
 # of one launch); the sampler on 16,384 games, scaled by the games it
 # processes (traffic grows in proportion).  Writes still dirty in the L2
 # when a launch ends are not in its DRAM count.
-NCU_TRAFFIC = {"kernel_sha1": "965c260a0292", "bytes_per_launch": 153821184.0 + 555878912.0,
+NCU_TRAFFIC = {"kernel_sha1": "8302ad1d807f", "bytes_per_launch": 153810432.0 + 555577088.0,
                "warp_inst_per_launch": 118105197.0, "captured": "65,536 games (the bench's own launch)",
                "games": 65536}
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4  # one warp instruction per scheduler and clock
@@ -52,11 +52,11 @@ SAMPLE_NCU = {"kernel_sha1": "515d4f95a9c0", "bytes_per_launch": 4 * (133577216.
 # DRAM bytes of one frame of the ragged and mixed workloads, each in the form
 # that the default batch rule picks (per-bucket launches for the four ragged
 # buckets, summed; one work-list launch for the fifteen mixed buckets)
-ROLLOUT_NCU = {"kernel_sha1": "965c260a0292",
+ROLLOUT_NCU = {"kernel_sha1": "8302ad1d807f",
                "1v1-131072-ragged15to30": {"form": "plain_buckets", "bytes_per_frame":
-                                           (30472448.0 + 145816832.0 + 139028224.0 + 5467648.0)
-                                           + (51024128.0 + 455904000.0 + 426976000.0 + 4096.0)},
-               "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128558080.0 + 867632128.0}}
+                                           (30479872.0 + 145809408.0 + 139023104.0 + 5467136.0)
+                                           + (51041792.0 + 455997184.0 + 426810112.0 + 3328.0)},
+               "mixed-32768-sides20to40": {"form": "plain_worklist", "bytes_per_frame": 128557824.0 + 867469568.0}}
 FEATURE_NCU_TRAFFIC = {"kernel_sha1": "8af7d765f60a", "bytes_per_launch": 8 * (356319488.0 + 1554689024.0),
                        "captured": "8,192 games (x8)", "games": 65536}
 
